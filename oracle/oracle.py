@@ -1,0 +1,245 @@
+"""ctypes wrapper of the FP64 CPU oracle (te_oracle.c) -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this module.  It shares nothing with the CUDA library: the two
+only see the same generated instance arrays.
+
+Functions (all FP64; paper references are to GATE, Section 3 and Appendix B):
+
+* :func:`solve` / :class:`OracleSolver` -- the ADMM iteration of Algorithm 1
+  with residual balancing (Eq. 17), the stop rule (Eq. 18) and
+  alpha-continuation (Section 3.4).
+* :func:`demand_solve` -- one per-demand x-block subproblem (Appendix B.2).
+* :func:`run_expanded` -- the same iteration with every consensus copy
+  y_{e,r} and dual u_{e,r} kept per incidence (Eqs. 5-7, 10, 13).
+* :func:`project` -- the feasibility projection (Algorithm 2).
+* :func:`gap` -- the Lagrangian duality gap of a feasible allocation.
+* :func:`optimality` -- the optimality metric of Section 4.1.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "te_oracle.c")
+_LIB = os.path.join(_HERE, "libteoracle.so")
+
+TRACE_WIDTH = 5  # r, s, beta, alpha, event bits (1 beta change, 2 alpha step, 4/8/16 stop)
+
+
+def build(force: bool = False) -> str:
+    """Compile te_oracle.c with gcc (FP64, IEEE semantics, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + res.stderr)
+    return _LIB
+
+
+class _Inst(ctypes.Structure):
+    _fields_ = [("n_edges", ctypes.c_int32), ("n_demands", ctypes.c_int32),
+                ("n_paths", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("cap", ctypes.c_void_p), ("demand", ctypes.c_void_p),
+                ("dpo", ctypes.c_void_p), ("peo", ctypes.c_void_p), ("pe", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("alpha_target", ctypes.c_double), ("alpha_start", ctypes.c_double),
+                ("alpha_step", ctypes.c_double), ("alpha_max", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("A", ctypes.c_double), ("C", ctypes.c_double),
+                ("beta0", ctypes.c_double), ("adapt_beta", ctypes.c_int32),
+                ("continuation", ctypes.c_int32), ("threads", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class _Scalars(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("alpha", ctypes.c_double), ("scale", ctypes.c_double),
+                ("iter", ctypes.c_int64), ("iter_alpha", ctypes.c_int64),
+                ("converged", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def _L() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.or_init.restype = ctypes.c_int
+        lib.or_init.argtypes = [P, P, P, P, P, P, P]
+        lib.or_run.restype = ctypes.c_int64
+        lib.or_run.argtypes = [P, P, P, P, P, P, ctypes.c_int64, P]
+        lib.or_demand_solve.restype = ctypes.c_double
+        lib.or_demand_solve.argtypes = [ctypes.c_int, P, P, ctypes.c_double, ctypes.c_double, P]
+        lib.or_run_expanded.restype = None
+        lib.or_run_expanded.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P,
+                                        ctypes.c_int64]
+        lib.or_project.restype = None
+        lib.or_project.argtypes = [P, P, ctypes.c_double]
+        lib.or_gap.restype = ctypes.c_double
+        lib.or_gap.argtypes = [P, P, P, ctypes.c_double, P, P]
+        lib.or_utility.restype = ctypes.c_double
+        lib.or_utility.argtypes = [ctypes.c_double, ctypes.c_double]
+        _lib = lib
+    return _lib
+
+
+def _c(a: np.ndarray, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class _InstanceView:
+    """Keeps contiguous copies of the arrays alive while C holds pointers."""
+
+    def __init__(self, inst):
+        self.cap = _c(inst.capacity, np.float64)
+        self.demand = _c(inst.demand, np.float64)
+        self.dpo = _c(inst.demand_path_off, np.int64)
+        self.peo = _c(inst.path_edge_off, np.int64)
+        self.pe = _c(inst.path_edges, np.int32)
+        self.s = _Inst(self.cap.shape[0], self.demand.shape[0], self.peo.shape[0] - 1, self.pe.shape[0],
+                       self.cap.ctypes.data, self.demand.ctypes.data, self.dpo.ctypes.data,
+                       self.peo.ctypes.data, self.pe.ctypes.data)
+
+
+def utility(S, alpha: float):
+    """alpha-fair utility U_alpha (Eq. 4), elementwise."""
+    S = np.asarray(S, dtype=np.float64)
+    return np.vectorize(lambda v: _L().or_utility(float(v), float(alpha)))(S)
+
+
+class OracleSolver:
+    """Stateful FP64 solver: ``run(n)`` advances up to n iterations."""
+
+    def __init__(self, inst, alpha_target: float = math.inf, gamma: float = 1e-3, A: float = 10.0,
+                 C: float = 2.0, beta0: float = 1.0, adapt_beta: bool = True, continuation: bool = True,
+                 alpha_start: float = 0.0, alpha_step: float = 1.0, alpha_max: float = 32.0,
+                 threads: int = 0, x0: Optional[np.ndarray] = None):
+        self.inst = inst
+        self.view = _InstanceView(inst)
+        self.opts = _Opts(alpha_target, alpha_start, alpha_step, alpha_max, gamma, A, C, beta0,
+                          int(adapt_beta), int(continuation), int(threads), 0)
+        self.x = np.zeros(inst.n_paths, dtype=np.float64)
+        self.u = np.zeros(inst.n_edges, dtype=np.float64)
+        self.d = np.zeros(inst.n_edges, dtype=np.float64)
+        self.sc = _Scalars()
+        x0c = None if x0 is None else _c(x0, np.float64)
+        rc = _L().or_init(ctypes.byref(self.view.s), ctypes.byref(self.opts),
+                          None if x0c is None else x0c.ctypes.data, self.x.ctypes.data,
+                          self.u.ctypes.data, self.d.ctypes.data, ctypes.byref(self.sc))
+        if rc != 0:
+            raise ValueError("oracle init failed (no positive capacity)")
+        self.trace = np.zeros((0, TRACE_WIDTH))
+
+    def run(self, max_iters: int) -> int:
+        tr = np.zeros((max(int(max_iters), 1), TRACE_WIDTH), dtype=np.float64)
+        n = _L().or_run(ctypes.byref(self.view.s), ctypes.byref(self.opts), self.x.ctypes.data,
+                        self.u.ctypes.data, self.d.ctypes.data, ctypes.byref(self.sc), int(max_iters),
+                        tr.ctypes.data)
+        self.trace = np.concatenate([self.trace, tr[:n]])
+        return int(n)
+
+    # state accessors (caller units unless stated)
+    @property
+    def scale(self) -> float:
+        return self.sc.scale
+
+    @property
+    def beta(self) -> float:
+        return self.sc.beta
+
+    @property
+    def alpha(self) -> float:
+        return self.sc.alpha
+
+    @property
+    def iters(self) -> int:
+        return int(self.sc.iter)
+
+    @property
+    def converged(self) -> bool:
+        return bool(self.sc.converged)
+
+    def allocation(self) -> np.ndarray:
+        return self.x * self.scale
+
+    def prices(self) -> np.ndarray:
+        """Capacity prices p_e = beta u_e in caller units (U' scales as scale^-alpha)."""
+        return self.sc.beta * self.u * self.scale ** (-self.sc.alpha)
+
+
+def solve(inst, max_iters: int = 10000, **kw) -> OracleSolver:
+    s = OracleSolver(inst, **kw)
+    s.run(max_iters)
+    return s
+
+
+def demand_solve(m: np.ndarray, w: np.ndarray, D: float, alpha: float):
+    """Per-demand x-block: returns (lambda, x)."""
+    m = _c(m, np.float64)
+    w = _c(w, np.float64)
+    x = np.zeros_like(m)
+    lam = _L().or_demand_solve(int(m.shape[0]), m.ctypes.data, w.ctypes.data, float(D), float(alpha),
+                               x.ctypes.data)
+    return lam, x
+
+
+def run_expanded(inst, beta: float, alpha: float, iters: int):
+    """Per-incidence ADMM from the default start: returns (x, y, u) normalised."""
+    v = _InstanceView(inst)
+    scale = float(np.max(inst.capacity))
+    npaths = np.diff(inst.demand_path_off)
+    x = np.repeat(inst.demand / scale / npaths, npaths).astype(np.float64)
+    plen = np.diff(inst.path_edge_off)
+    y = np.repeat(x, plen).astype(np.float64)
+    u = np.zeros(inst.nnz, dtype=np.float64)
+    _L().or_run_expanded(ctypes.byref(v.s), float(beta), float(alpha), scale, x.ctypes.data, y.ctypes.data,
+                         u.ctypes.data, int(iters))
+    return x, y, u
+
+
+def project(inst, x: np.ndarray, alpha: float) -> np.ndarray:
+    """Algorithm 2 on a copy of x (caller units)."""
+    v = _InstanceView(inst)
+    out = np.array(x, dtype=np.float64, copy=True)
+    _L().or_project(ctypes.byref(v.s), out.ctypes.data, float(alpha))
+    return out
+
+
+def gap(inst, x: np.ndarray, prices: np.ndarray, alpha: float):
+    """(gap, primal, dual) of a feasible x under edge prices p >= 0 (caller units)."""
+    v = _InstanceView(inst)
+    xc = _c(x, np.float64)
+    pc = _c(prices, np.float64)
+    pr = ctypes.c_double()
+    du = ctypes.c_double()
+    g = _L().or_gap(ctypes.byref(v.s), xc.ctypes.data, pc.ctypes.data, float(alpha), ctypes.byref(pr),
+                    ctypes.byref(du))
+    return float(g), float(pr.value), float(du.value)
+
+
+def demand_totals(inst, x: np.ndarray) -> np.ndarray:
+    """S_c = sum of x over each demand's paths."""
+    return np.add.reduceat(np.asarray(x, dtype=np.float64), inst.demand_path_off[:-1]) \
+        if inst.n_demands else np.zeros(0)
+
+
+def edge_loads(inst, x: np.ndarray) -> np.ndarray:
+    """L_e = sum of x over the paths through e."""
+    plen = np.diff(inst.path_edge_off)
+    return np.bincount(inst.path_edges, weights=np.repeat(np.asarray(x, dtype=np.float64), plen),
+                       minlength=inst.n_edges)
+
+
+def optimality(S: np.ndarray, opt: np.ndarray, theta: float) -> float:
+    """Section 4.1: mean over demands of min(S_d / max(OPT_d, theta), 1)."""
+    S = np.asarray(S, dtype=np.float64)
+    opt = np.asarray(opt, dtype=np.float64)
+    return float(np.mean(np.minimum(S / np.maximum(opt, theta), 1.0)))

@@ -1,0 +1,214 @@
+/*
+ * te.h -- C-ABI of the GATE traffic-engineering iteration engine (libte.so).
+ *
+ * The library solves path-based alpha-fair traffic engineering (GATE,
+ * Section 3.1): given directed edge capacities C_e, demands D_c and a set of
+ * pre-computed paths per demand, it finds path rates x_r that maximise
+ *     sum_c U_alpha(S_c),   S_c = sum_{r in P_c} x_r            (Eq. 4)
+ * subject to S_c <= D_c (Eq. 1), sum_{r ni e} x_r <= C_e (Eq. 2), x >= 0
+ * (Eq. 3); alpha = 0 is total throughput, alpha = 1 proportional fairness and
+ * alpha -> infinity max-min fairness (Table 3).  It runs the ADMM iteration of
+ * Algorithm 1 (Sections 3.2-3.4) on one CUDA device: per-demand rate updates
+ * (Eq. 14 with the sum computation of Appendix B.2), per-edge price updates
+ * (Eqs. 9, 13), residuals (Eqs. 15-16), residual balancing (Eq. 17), the stop
+ * rule (Eq. 18) and alpha-continuation (Section 3.4), followed on request by
+ * the feasibility projection of Algorithm 2 (Section 3.5).
+ *
+ * Conventions for every entry point:
+ *  - Status codes are returned; nothing is thrown across the ABI.  A failing
+ *    call leaves the handle's last consistent state and stores a message
+ *    readable with te_last_error().
+ *  - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *    global memory of the device that was current at te_create.
+ *  - A handle is used by one host thread at a time and issues all its work
+ *    on the stream given in te_options.cuda_stream (NULL: the legacy default
+ *    stream).  Calls that return values synchronise that stream.
+ *  - Units: rates, demands and capacities are in the caller's units.  The
+ *    iteration itself runs on values divided by one positive scale (the
+ *    geometric mean of the demands by default; see scale_mode), which leaves
+ *    the alpha-fair optimum unchanged; te_solve_result reports beta in those
+ *    normalised units.
+ */
+#ifndef TE_H_
+#define TE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct te_handle te_handle;
+
+typedef enum {
+    TE_OK = 0,
+    TE_EINVAL = 1,        /* invalid argument or instance (message says which) */
+    TE_ENOMEM = 2,        /* host or device allocation failed                  */
+    TE_ECUDA = 3,         /* a CUDA runtime call failed                        */
+    TE_ETIMEOUT = 4,      /* a bounded device-side wait gave up; state kept    */
+    TE_ENUMERIC = 5,      /* a residual became NaN/Inf                         */
+    TE_ENOTCONVERGED = 6, /* reserved                                          */
+    TE_EUNSUPPORTED = 7   /* instance exceeds a documented limit               */
+} te_status;
+
+/* Directed topology.  edge_src/edge_dst may be NULL (then paths are not
+ * checked for being walks). */
+typedef struct {
+    int32_t n_nodes;
+    int32_t n_edges;
+    const int32_t* edge_src; /* host [n_edges] */
+    const int32_t* edge_dst; /* host [n_edges] */
+} te_topology;
+
+/* Pre-computed path sets in CSR form (Section 3.1, "Variables"): demand c
+ * owns paths demand_path_off[c] .. demand_path_off[c+1]-1, path r traverses
+ * edges path_edges[path_edge_off[r] .. path_edge_off[r+1]-1] in order.
+ * demand_src/demand_dst may be NULL (then the walk check is skipped). */
+typedef struct {
+    int32_t n_demands;
+    int32_t pad_;
+    int64_t n_paths;
+    int64_t nnz;
+    const int32_t* demand_src;       /* host [n_demands]   */
+    const int32_t* demand_dst;       /* host [n_demands]   */
+    const int64_t* demand_path_off;  /* host [n_demands+1] */
+    const int64_t* path_edge_off;    /* host [n_paths+1]   */
+    const int32_t* path_edges;       /* host [nnz]         */
+} te_paths;
+
+/* Solver options; te_default_options() fills the paper's defaults. */
+typedef struct {
+    double alpha_target;  /* fairness level; INFINITY = max-min (default)      */
+    double alpha_start;   /* first alpha of the continuation (default 0)       */
+    double alpha_step;    /* continuation increment (default 1, Algorithm 1)   */
+    double alpha_max;     /* continuation cap (default 32)                     */
+    double gamma;         /* stop threshold on relative r and s (default 1e-3,
+                             Section 3.7); negative: never stop early          */
+    double A;             /* residual balancing ratio (default 10, Eq. 17)     */
+    double C;             /* residual balancing factor (default 2, Eq. 17)     */
+    double beta0;         /* initial penalty in normalised units; <= 0
+                             (default) picks 1 / (mean path length * mean
+                             initial path rate), so the first utility push
+                             lambda/(beta n_r) at lambda = 1 equals the mean
+                             initial rate                                      */
+    int32_t adapt_beta;   /* 1: residual balancing on (default 1)              */
+    int32_t continuation; /* 1: stop when converged on the first iteration
+                             after an alpha increment (default 1)              */
+    int32_t scale_mode;   /* unit of the normalised problem: 0 = max_e C_e,
+                             1 = geometric mean of the demands (default), so
+                             the marginal utility S^-alpha of a typical demand
+                             stays near 1 as alpha grows                       */
+    int32_t wait_timeout_ms; /* bound on every grid-wide wait inside te_solve;
+                             0 = default (2000 ms)                             */
+    int32_t test_withhold_cta; /* test hook for the bounded-wait path: 1 + the
+                             index of a CTA that never arrives at the grid
+                             barrier, so te_solve must return TE_ETIMEOUT;
+                             0 = off (default)                                 */
+    int32_t reserved;
+    void* cuda_stream;    /* cudaStream_t to run on; NULL = default stream     */
+} te_options;
+
+/* Outcome of a te_solve call. */
+typedef struct {
+    int64_t iters;        /* iterations run by this call                       */
+    int64_t total_iters;  /* iterations since te_create / te_reset             */
+    double r;             /* last relative primal residual (Eq. 16)            */
+    double s;             /* last relative dual residual (Eq. 15)              */
+    double beta;          /* penalty after the last iteration (normalised)     */
+    double alpha;         /* fairness level after the last iteration           */
+    int32_t converged;    /* 1: the stop rule fired in this call               */
+    int32_t stop_reason;  /* 0 none, 4 target alpha reached, 8 stagnation after
+                             an increment, 16 alpha_max reached                */
+} te_solve_result;
+
+/* Fills *opt with the defaults listed above. */
+void te_default_options(te_options* opt);
+
+/* Validates the instance, builds the device layout, copies everything to
+ * the device and sets the initial state (Algorithm 1: x_r = D_c/|P_c|, all
+ * duals zero, alpha = alpha_start).  The caller keeps ownership of every
+ * input buffer (they are copied).  demands: host [n_demands], finite and
+ * > 0; capacities: host [n_edges], finite and >= 0, and > 0 on every edge
+ * used by a path (Slater's condition, Appendix C).  Limits: at most 32 paths
+ * per demand, at most 255 edges per path, E + 1 < 2^31.  On success *out
+ * receives a new handle.  Errors: TE_EINVAL (bad input; message names the
+ * first offending index), TE_EUNSUPPORTED, TE_ENOMEM, TE_ECUDA. */
+te_status te_create(const te_topology* topo, const te_paths* paths, const double* demands,
+                    const double* capacities, const te_options* opt, te_handle** out);
+
+/* Runs up to max_iters iterations of Algorithm 1 from the current state in
+ * one persistent kernel launch, stopping early when the stop rule fires
+ * (Eq. 18 with alpha-continuation).  Every step of the iteration runs on the
+ * device; the call synchronises and fills *out (may be NULL).  Errors:
+ * TE_EINVAL (max_iters < 0), TE_ETIMEOUT (a grid-wide wait exceeded its
+ * limit; the state of the last completed iteration is kept), TE_ENUMERIC,
+ * TE_ECUDA. */
+te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* out);
+
+/* Writes the current rates in the caller's path order and units to x_out
+ * [n_paths] (FP32).  project = 1 first applies the feasibility projection of
+ * Algorithm 2 (non-negativity, demand trims, capacity trims in descending
+ * score S_c^alpha * C_p) to a copy; the iterate itself is not changed.
+ * out_is_device selects whether x_out is a device or a host pointer. */
+te_status te_allocation(te_handle* h, float* x_out, int32_t project, int32_t out_is_device);
+
+/* Duality gap of the projected allocation x^ (caller units, FP64): the
+ * Lagrangian dual bound g(p) = sum_e p_e C_e + sum_c max_{0<=S<=D_c}
+ * [U_alpha(S) - pi_c S], pi_c = min_{r in P_c} sum_{e in r} p_e, at the
+ * current prices p_e = beta u_e, minus sum_c U_alpha(S_c(x^)), at the
+ * current alpha.  Any output pointer may be NULL. */
+te_status te_gap(te_handle* h, double* gap_out, double* primal_out, double* dual_out);
+
+/* Current edge prices p_e = beta u_e in the caller's units (FP64,
+ * [n_edges]); these are the capacity multipliers dual_cap_e of Eq. 9. */
+te_status te_prices(te_handle* h, double* p_out, int32_t out_is_device);
+
+/* Replaces the rates by x0 (caller order and units, [n_paths], FP32) for a
+ * warm start (Algorithm 1, optional input x^0).  keep_duals = 0 also resets
+ * the prices and alpha to their initial values. */
+te_status te_set_warm_start(te_handle* h, const float* x0, int32_t in_is_device, int32_t keep_duals);
+
+/* Replaces the demands D_c (caller order and units, [n_demands], FP64,
+ * finite and > 0) without rebuilding the instance, for re-solving as demands
+ * drift (Section 2 "Background": TE re-runs on every new demand matrix).
+ * in_is_device selects a device or host pointer.  The iterate, prices and
+ * alpha are kept (a warm start from the previous allocation); call te_reset
+ * for a cold start.  Errors: TE_EINVAL if a demand is not finite and > 0
+ * (nothing is changed then). */
+te_status te_set_demands(te_handle* h, const double* demands, int32_t in_is_device);
+
+/* Returns to the initial state of te_create. */
+te_status te_reset(te_handle* h);
+
+/* Per-iteration telemetry since the last te_create/te_reset: rows of five
+ * doubles (r, s, beta, alpha, event bits: 1 beta changed, 2 alpha
+ * incremented, 4/8/16 stop reasons).  Copies min(max_rows, available) rows
+ * to host out and returns that count in *rows. */
+te_status te_trace(te_handle* h, double* out, int64_t max_rows, int64_t* rows);
+
+/* Sizes of the device layout: n_demands, n_paths, nnz, padded id rows,
+ * slots, id width in bytes, persistent grid size, bytes the iteration kernel
+ * reads and writes per iteration (the algorithmic traffic), device memory
+ * held, and the number of kernels launched through this handle. */
+typedef struct {
+    int64_t n_demands, n_paths, nnz;
+    int64_t id_rows, slots;
+    int32_t id_bytes, grid;
+    int64_t bytes_per_iter;
+    int64_t device_bytes;
+    int64_t kernel_launches;  /* kernels this handle has launched so far */
+} te_layout_info;
+te_status te_layout(const te_handle* h, te_layout_info* info);
+
+/* Releases every resource of the handle.  NULL is ignored. */
+void te_destroy(te_handle* h);
+
+/* Message of the last failing call on h (never NULL); with h == NULL, the
+ * message of the last failing te_create in this thread. */
+const char* te_last_error(const te_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TE_H_ */

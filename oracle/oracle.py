@@ -55,7 +55,7 @@ class _Opts(ctypes.Structure):
                 ("alpha_step", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("A", ctypes.c_double), ("C", ctypes.c_double),
                 ("beta0", ctypes.c_double), ("adapt_beta", ctypes.c_int32),
-                ("continuation", ctypes.c_int32), ("threads", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("continuation", ctypes.c_int32), ("threads", ctypes.c_int32), ("scale_mode", ctypes.c_int32)]
 
 
 class _Scalars(ctypes.Structure):
@@ -119,13 +119,17 @@ class OracleSolver:
     """Stateful FP64 solver: ``run(n)`` advances up to n iterations."""
 
     def __init__(self, inst, alpha_target: float = math.inf, gamma: float = 1e-3, A: float = 10.0,
-                 C: float = 2.0, beta0: float = 1.0, adapt_beta: bool = True, continuation: bool = True,
+                 C: float = 2.0, beta0: float = 0.0, adapt_beta: bool = True, continuation: bool = True,
                  alpha_start: float = 0.0, alpha_step: float = 1.0, alpha_max: float = 32.0,
-                 threads: int = 0, x0: Optional[np.ndarray] = None):
+                 threads: int = 0, x0: Optional[np.ndarray] = None, scale_mode: int = 1):
+        """Defaults: the paper's A = 10, C = 2, gamma = 1e-3 (Section 3.7),
+        alpha from 0 in steps of 1 (Algorithm 1); the unit of the normalised
+        problem is the geometric mean of the demands (scale_mode = 1) and
+        beta0 <= 0 picks 1 / (mean path length * mean initial path rate)."""
         self.inst = inst
         self.view = _InstanceView(inst)
         self.opts = _Opts(alpha_target, alpha_start, alpha_step, alpha_max, gamma, A, C, beta0,
-                          int(adapt_beta), int(continuation), int(threads), 0)
+                          int(adapt_beta), int(continuation), int(threads), int(scale_mode))
         self.x = np.zeros(inst.n_paths, dtype=np.float64)
         self.u = np.zeros(inst.n_edges, dtype=np.float64)
         self.d = np.zeros(inst.n_edges, dtype=np.float64)
@@ -191,10 +195,11 @@ def demand_solve(m: np.ndarray, w: np.ndarray, D: float, alpha: float):
     return lam, x
 
 
-def run_expanded(inst, beta: float, alpha: float, iters: int):
-    """Per-incidence ADMM from the default start: returns (x, y, u) normalised."""
+def run_expanded(inst, beta: float, alpha: float, iters: int, scale: Optional[float] = None):
+    """Per-incidence ADMM from the default start: returns (x, y, u) normalised
+    by `scale` (default max_e C_e)."""
     v = _InstanceView(inst)
-    scale = float(np.max(inst.capacity))
+    scale = float(np.max(inst.capacity)) if scale is None else float(scale)
     npaths = np.diff(inst.demand_path_off)
     x = np.repeat(inst.demand / scale / npaths, npaths).astype(np.float64)
     plen = np.diff(inst.path_edge_off)

@@ -76,7 +76,8 @@ typedef struct {
     int32_t adapt_beta;   /* 1: residual balancing on                     */
     int32_t continuation; /* 1: stop when converged on the first iteration after an increment */
     int32_t threads;      /* OpenMP threads (0: runtime default)          */
-    int32_t pad;
+    int32_t scale_mode;   /* unit of the normalised problem: 0 = max_e C_e,
+                             1 = geometric mean of the demands            */
 } or_options;
 
 /* Scalars of the solver state (arrays are passed separately). */
@@ -223,7 +224,13 @@ static int64_t max_paths_per_demand(const or_instance* I) {
 int or_init(const or_instance* I, const or_options* o, const double* x0, double* x, double* u,
             double* d, or_scalars* sc) {
     double scale = 0.0;
-    for (int e = 0; e < I->n_edges; ++e) if (I->cap[e] > scale) scale = I->cap[e];
+    if (o->scale_mode == 1) {
+        double lg = 0.0;
+        for (int32_t c = 0; c < I->n_demands; ++c) lg += log(I->demand[c]);
+        scale = exp(lg / (double)I->n_demands);
+    } else {
+        for (int e = 0; e < I->n_edges; ++e) if (I->cap[e] > scale) scale = I->cap[e];
+    }
     if (!(scale > 0.0)) return 1;
     for (int32_t c = 0; c < I->n_demands; ++c) {
         const int64_t p0 = I->dpo[c], p1 = I->dpo[c + 1];
@@ -231,7 +238,17 @@ int or_init(const or_instance* I, const or_options* o, const double* x0, double*
             x[r] = x0 ? x0[r] / scale : (I->demand[c] / scale) / (double)(p1 - p0);
     }
     for (int e = 0; e < I->n_edges; ++e) { u[e] = 0.0; d[e] = 0.0; }
-    sc->beta = o->beta0;
+    if (o->beta0 > 0.0) {
+        sc->beta = o->beta0;
+    } else {
+        /* beta0 <= 0: the first push lambda/(beta n_r) at lambda = 1 equals
+         * the mean initial path rate: beta0 = 1 / (mean n_r * mean x^0_r) */
+        double xs = 0.0;
+        for (int64_t r = 0; r < I->n_paths; ++r) xs += x[r];
+        const double xbar = xs / (double)I->n_paths;
+        const double nbar = (double)I->nnz / (double)I->n_paths;
+        sc->beta = 1.0 / (nbar * xbar);
+    }
     sc->alpha = isfinite(o->alpha_target) && o->alpha_start > o->alpha_target ? o->alpha_target : o->alpha_start;
     sc->scale = scale;
     sc->iter = 0;

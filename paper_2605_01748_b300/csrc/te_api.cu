@@ -1,0 +1,753 @@
+// Host side of the C-ABI (include/te.h): input validation, the sliced device
+// layout, device memory, kernel launches and error reporting.
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "te.h"
+#include "te_internal.cuh"
+
+using te::kLanes;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr long long kTraceCap = 1 << 16;
+constexpr long long kItersPerLaunch = 1LL << 24;  // keeps the barrier counter below 2^32
+
+// p_out[e] = pscale * u[e]
+__global__ void k_prices(int E, const float* u, double pscale, double* p) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < E) p[e] = pscale * (double)u[e];
+}
+
+// flags demands that are not finite and positive
+__global__ void k_check_demands(int K, const double* D, int* bad) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < K && !(D[c] > 0.0 && D[c] < INFINITY)) atomicOr(bad, 1);
+}
+
+// new demands into lane order: normalised FP32 for the iteration, caller
+// units FP64 for the gap
+__global__ void k_set_demands(long long lanes, const int* lane_demand, const double* D, double inv_scale,
+                              float* Dn, double* Dc) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= lanes) return;
+    const int c = lane_demand[i];
+    if (c < 0) return;
+    Dn[i] = (float)(D[c] * inv_scale);
+    Dc[i] = D[c];
+}
+
+}  // namespace
+
+namespace te {
+cudaError_t launch_prices(int E, const float* u, double pscale, double* p_out, cudaStream_t st) {
+    k_prices<<<(E + 255) / 256, 256, 0, st>>>(E, u, pscale, p_out);
+    return cudaGetLastError();
+}
+}  // namespace te
+
+struct te_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    te::Options o{};
+    double beta0 = 1.0;
+    long long timeout_ns = 2000000000LL;
+    te::Layout L{};
+    double scale = 1.0;
+    int grid = 0;
+    long long bytes_per_iter = 0;
+    long long device_bytes = 0;
+    // owned device buffers
+    std::vector<void*> owned;
+    float* x = nullptr;       // [2][nslots*32]
+    float* u = nullptr;       // [E]
+    float* w = nullptr;       // [E]
+    float* loads = nullptr;   // [3E]
+    double* part = nullptr;   // [2*grid*4]
+    unsigned* barrier = nullptr;
+    int* status = nullptr;
+    te::Scalars* sc = nullptr;
+    double* trace = nullptr;  // [kTraceCap*5]
+    int* cta_blk = nullptr;   // [grid+1]
+    double* Dc = nullptr;     // [nblocks*32] caller-unit demands
+    float* xtmp = nullptr;    // [nslots*32]
+    float* user = nullptr;    // [P]
+    double* gacc = nullptr;   // [3]
+    double* pbuf = nullptr;   // [E]
+    double* dstage = nullptr; // [K] staging of new demands
+    int* flag = nullptr;      // [1]
+    float* lam = nullptr;     // [nblocks*32] warm-start multipliers
+    unsigned* ctr = nullptr;  // [3] work counters
+    float* Dn = nullptr;      // mutable view of L.Dn
+    long long launches = 0;   // kernels launched through this handle
+    te::ProjScratch ps{};
+    te::Scalars hsc{};        // host mirror of the scalars
+    std::string err;
+
+    te_status fail(te_status s, const std::string& m) {
+        err = m;
+        return s;
+    }
+    te_status cuda(cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return TE_OK;
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return TE_ECUDA;
+    }
+    template <typename T>
+    cudaError_t alloc(T** p, size_t bytes) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+        if (e == cudaSuccess) {
+            owned.push_back(q);
+            device_bytes += (long long)bytes;
+        }
+        *p = (T*)q;
+        return e;
+    }
+};
+
+extern "C" {
+
+void te_default_options(te_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->alpha_target = INFINITY;
+    o->alpha_start = 0.0;
+    o->alpha_step = 1.0;
+    o->alpha_max = 32.0;
+    o->gamma = 1e-3;
+    o->A = 10.0;
+    o->C = 2.0;
+    o->beta0 = 0.0;       // automatic (see te.h)
+    o->adapt_beta = 1;
+    o->continuation = 1;
+    o->scale_mode = 1;    // geometric mean of the demands
+    o->wait_timeout_ms = 0;
+    o->test_withhold_cta = 0;
+    o->cuda_stream = nullptr;
+}
+
+const char* te_last_error(const te_handle* h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void te_destroy(te_handle* h) {
+    if (!h) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (void* p : h->owned) cudaFree(p);
+    cudaSetDevice(cur);
+    delete h;
+}
+
+}  // extern "C"
+
+namespace {
+
+std::string fmt(const char* f, long long a, long long b = 0) {
+    char buf[256];
+    snprintf(buf, sizeof buf, f, a, b);
+    return buf;
+}
+
+// Checks the instance; returns an empty string when valid.
+std::string validate(const te_topology* topo, const te_paths* P, const double* D, const double* C) {
+    if (!topo || !P || !D || !C) return "null argument";
+    const int E = topo->n_edges;
+    if (E <= 0) return "n_edges must be positive";
+    if (E >= 0x7ffffffe) return "n_edges too large";
+    if (P->n_demands <= 0) return "n_demands must be positive";
+    if (P->n_paths < P->n_demands) return "fewer paths than demands";
+    if (P->nnz < P->n_paths) return "fewer incidences than paths";
+    if (!P->demand_path_off || !P->path_edge_off || !P->path_edges) return "null path arrays";
+    const int K = P->n_demands;
+    if (P->demand_path_off[0] != 0 || P->demand_path_off[K] != P->n_paths)
+        return "demand_path_off must start at 0 and end at n_paths";
+    if (P->path_edge_off[0] != 0 || P->path_edge_off[P->n_paths] != P->nnz)
+        return "path_edge_off must start at 0 and end at nnz";
+    for (int c = 0; c < K; ++c) {
+        const long long k = P->demand_path_off[c + 1] - P->demand_path_off[c];
+        if (k < 1) return fmt("demand %lld has no path", c);
+        if (k > te::kMaxPaths) return fmt("demand %lld has %lld paths (limit 32)", c, k);
+        if (!(D[c] > 0.0) || !isfinite(D[c])) return fmt("demand %lld is not finite and positive", c);
+    }
+    for (long long r = 0; r < P->n_paths; ++r) {
+        const long long n = P->path_edge_off[r + 1] - P->path_edge_off[r];
+        if (n < 1) return fmt("path %lld is empty", r);
+        if (n > te::kMaxHops) return fmt("path %lld has %lld edges (limit 255)", r, n);
+    }
+    std::vector<char> used(E, 0);
+    for (long long i = 0; i < P->nnz; ++i) {
+        const int e = P->path_edges[i];
+        if (e < 0 || e >= E) return fmt("incidence %lld names edge %lld out of range", i, e);
+        used[e] = 1;
+    }
+    for (int e = 0; e < E; ++e) {
+        if (!isfinite(C[e]) || C[e] < 0.0) return fmt("capacity of edge %lld is not finite and >= 0", e);
+        if (used[e] && !(C[e] > 0.0)) return fmt("edge %lld is on a path but has zero capacity", e);
+    }
+    if (topo->edge_src && topo->edge_dst) {
+        const int N = topo->n_nodes;
+        for (int e = 0; e < E; ++e)
+            if (topo->edge_src[e] < 0 || topo->edge_src[e] >= N || topo->edge_dst[e] < 0 || topo->edge_dst[e] >= N)
+                return fmt("edge %lld has an endpoint out of range", e);
+        if (P->demand_src && P->demand_dst) {
+            for (int c = 0; c < K; ++c) {
+                for (long long r = P->demand_path_off[c]; r < P->demand_path_off[c + 1]; ++r) {
+                    const long long i0 = P->path_edge_off[r], i1 = P->path_edge_off[r + 1];
+                    if (topo->edge_src[P->path_edges[i0]] != P->demand_src[c] ||
+                        topo->edge_dst[P->path_edges[i1 - 1]] != P->demand_dst[c])
+                        return fmt("path %lld does not join its demand's endpoints", r);
+                    for (long long i = i0; i + 1 < i1; ++i)
+                        if (topo->edge_dst[P->path_edges[i]] != topo->edge_src[P->path_edges[i + 1]])
+                            return fmt("path %lld is not a walk", r);
+                }
+            }
+        }
+    }
+    return "";
+}
+
+}  // namespace
+
+extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const double* D, const double* C,
+                               const te_options* opt_in, te_handle** out) {
+    g_create_error.clear();
+    if (!out) { g_create_error = "null output handle"; return TE_EINVAL; }
+    *out = nullptr;
+    {
+        std::string v = validate(topo, P, D, C);
+        if (!v.empty()) { g_create_error = v; return TE_EINVAL; }
+    }
+    te_options opt;
+    if (opt_in) opt = *opt_in; else te_default_options(&opt);
+    if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
+        (opt.scale_mode != 0 && opt.scale_mode != 1) ||
+        !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0) {
+        g_create_error = "invalid options";
+        return TE_EINVAL;
+    }
+    te_handle* h = new (std::nothrow) te_handle();
+    if (!h) { g_create_error = "out of host memory"; return TE_ENOMEM; }
+    auto bail = [&](te_status s) {
+        g_create_error = h->err;
+        te_destroy(h);
+        return s;
+    };
+    cudaGetDevice(&h->device);
+    h->stream = (cudaStream_t)opt.cuda_stream;
+    h->o.alpha_target = opt.alpha_target;
+    h->o.alpha_start = opt.alpha_start;
+    h->o.alpha_step = opt.alpha_step;
+    h->o.alpha_max = opt.alpha_max;
+    h->o.gamma = opt.gamma;
+    h->o.A = opt.A;
+    h->o.C = opt.C;
+    h->o.adapt_beta = opt.adapt_beta;
+    h->o.continuation = opt.continuation;
+    h->o.withhold_cta = opt.test_withhold_cta > 0 ? opt.test_withhold_cta - 1 : -1;
+    h->beta0 = opt.beta0;
+    if (opt.wait_timeout_ms > 0) h->timeout_ns = (long long)opt.wait_timeout_ms * 1000000LL;
+
+    const int E = topo->n_edges;
+    const int K = P->n_demands;
+    const long long NP = P->n_paths;
+    double scale = 0.0;
+    if (opt.scale_mode == 1) {
+        double lg = 0.0;
+        for (int c = 0; c < K; ++c) lg += log(D[c]);
+        scale = exp(lg / (double)K);
+    } else {
+        for (int e = 0; e < E; ++e) scale = std::max(scale, C[e]);
+    }
+    h->scale = scale;
+    if (!(opt.beta0 > 0.0)) {
+        // first push lambda/(beta n_r) at lambda = 1 equal to the mean initial rate
+        double dsum = 0.0;
+        for (int c = 0; c < K; ++c) dsum += D[c] / scale;
+        const double xbar = dsum / (double)NP, nbar = (double)P->nnz / (double)NP;
+        h->beta0 = 1.0 / (nbar * xbar);
+    }
+
+    // ---------------- sliced layout ----------------
+    // sort demands by (path count, lengths of the first 11 paths) so the 32
+    // demands of a block have alike path lengths and padding stays small
+    std::vector<std::pair<unsigned long long, int>> order(K);
+    int kmax = 0;
+    for (int c = 0; c < K; ++c) {
+        const long long p0 = P->demand_path_off[c], np = P->demand_path_off[c + 1] - p0;
+        kmax = std::max(kmax, (int)np);
+        unsigned long long key = (unsigned long long)np << 58;
+        for (int j = 0; j < 11 && j < np; ++j) {
+            long long len = P->path_edge_off[p0 + j + 1] - P->path_edge_off[p0 + j];
+            if (len > 31) len = 31;
+            key |= (unsigned long long)len << (53 - 5 * j);
+        }
+        order[c] = {key, c};
+    }
+    std::sort(order.begin(), order.end());
+    const int nblocks = (K + kLanes - 1) / kLanes;
+    std::vector<int> slotbase(nblocks + 1, 0);
+    for (int b = 0; b < nblocks; ++b) {
+        int kb = 0;
+        for (int t = 0; t < kLanes; ++t) {
+            const int q = b * kLanes + t;
+            if (q >= K) break;
+            const int c = order[q].second;
+            kb = std::max(kb, (int)(P->demand_path_off[c + 1] - P->demand_path_off[c]));
+        }
+        slotbase[b + 1] = slotbase[b] + kb;
+    }
+    const long long nslots = slotbase[nblocks];
+    std::vector<unsigned> rowoff(nslots + 1, 0);
+    for (int b = 0; b < nblocks; ++b) {
+        for (int j = 0; j < slotbase[b + 1] - slotbase[b]; ++j) {
+            long long H = 0;
+            for (int t = 0; t < kLanes; ++t) {
+                const int q = b * kLanes + t;
+                if (q >= K) break;
+                const int c = order[q].second;
+                const long long p0 = P->demand_path_off[c];
+                if (j < P->demand_path_off[c + 1] - p0)
+                    H = std::max<long long>(H, P->path_edge_off[p0 + j + 1] - P->path_edge_off[p0 + j]);
+            }
+            const long long s = slotbase[b] + j;
+            const long long next = (long long)rowoff[s] + H;
+            if (next > 0xffffffffLL) { h->err = "instance too large for the 32-bit row index"; return bail(TE_EUNSUPPORTED); }
+            rowoff[s + 1] = (unsigned)next;
+        }
+    }
+    const long long nrows = rowoff[nslots];
+    const int id_bytes = (E + 1 <= 65535) ? 2 : 4;
+    std::vector<unsigned char> ids((size_t)nrows * kLanes * id_bytes);
+    std::vector<long long> slot_path((size_t)nslots * kLanes, -1);
+    std::vector<int> lane_demand((size_t)nblocks * kLanes, -1);
+    std::vector<float> Dn((size_t)nblocks * kLanes, 0.f);
+    std::vector<double> Dc((size_t)nblocks * kLanes, 0.0);
+    std::vector<unsigned char> npv((size_t)nblocks * kLanes, 0);
+    if (id_bytes == 2) {
+        uint16_t* q = (uint16_t*)ids.data();
+        std::fill(q, q + (size_t)nrows * kLanes, (uint16_t)E);
+    } else {
+        int32_t* q = (int32_t*)ids.data();
+        std::fill(q, q + (size_t)nrows * kLanes, (int32_t)E);
+    }
+    for (int b = 0; b < nblocks; ++b) {
+        for (int t = 0; t < kLanes; ++t) {
+            const int q = b * kLanes + t;
+            if (q >= K) break;
+            const int c = order[q].second;
+            const size_t li = (size_t)b * kLanes + t;
+            lane_demand[li] = c;
+            Dn[li] = (float)(D[c] / scale);
+            Dc[li] = D[c];
+            const long long p0 = P->demand_path_off[c], np = P->demand_path_off[c + 1] - p0;
+            npv[li] = (unsigned char)np;
+            for (int j = 0; j < np; ++j) {
+                const long long s = slotbase[b] + j, r = p0 + j;
+                slot_path[(size_t)s * kLanes + t] = r;
+                const long long i0 = P->path_edge_off[r], n = P->path_edge_off[r + 1] - i0;
+                for (long long k = 0; k < n; ++k) {
+                    const size_t at = ((size_t)rowoff[s] + (size_t)k) * kLanes + t;
+                    if (id_bytes == 2) ((uint16_t*)ids.data())[at] = (uint16_t)P->path_edges[i0 + k];
+                    else ((int32_t*)ids.data())[at] = P->path_edges[i0 + k];
+                }
+            }
+        }
+    }
+    std::vector<float> cap_n(E), ne_f(E, 0.f), inv_ne(E, 0.f);
+    {
+        std::vector<long long> ne(E, 0);
+        for (long long i = 0; i < P->nnz; ++i) ne[P->path_edges[i]]++;
+        for (int e = 0; e < E; ++e) {
+            cap_n[e] = (float)(C[e] / scale);
+            ne_f[e] = (float)ne[e];
+            inv_ne[e] = ne[e] > 0 ? (float)(1.0 / (double)ne[e]) : 0.f;
+        }
+    }
+
+    // ---------------- persistent grid ----------------
+    if (te::iter_smem_bytes(E) > 227 * 1024) {
+        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 19000 edges)", E);
+        return bail(TE_EUNSUPPORTED);
+    }
+    int bps = 0, nsm = 0;
+    te_status st;
+    if ((st = h->cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device), "device query")))
+        return bail(st);
+    if ((st = h->cuda(te::iter_occupancy(id_bytes, kmax, E, &bps), "occupancy query"))) return bail(st);
+    if (bps < 1) { h->err = "iteration kernel does not fit on an SM"; return bail(TE_EUNSUPPORTED); }
+    h->grid = nsm * bps;
+    std::vector<int> cta_blk(h->grid + 1, nblocks);
+    {
+        std::vector<long long> cost(nblocks);
+        long long total = 0;
+        for (int b = 0; b < nblocks; ++b) {
+            long long cst = 0;
+            for (int s = slotbase[b]; s < slotbase[b + 1]; ++s) cst += (long long)(rowoff[s + 1] - rowoff[s]) + 2;
+            cost[b] = cst + 1;
+            total += cost[b];
+        }
+        long long acc = 0;
+        int c = 0;
+        cta_blk[0] = 0;
+        for (int b = 0; b < nblocks && c < h->grid - 1; ++b) {
+            acc += cost[b];
+            while (c < h->grid - 1 && acc * h->grid >= (long long)(c + 1) * total) {
+                cta_blk[++c] = b + 1;
+            }
+        }
+        for (int k = c + 1; k <= h->grid; ++k) cta_blk[k] = nblocks;
+    }
+
+    // ---------------- device memory ----------------
+    void* d_ids;
+    unsigned* d_rowoff;
+    int *d_slotbase, *d_lane_demand;
+    float *d_Dn, *d_cap, *d_ne, *d_inv;
+    unsigned char* d_np;
+    long long* d_slot_path;
+    const size_t nl = (size_t)nblocks * kLanes, ns = (size_t)nslots * kLanes;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    A(h->alloc(&d_ids, ids.size()));
+    A(h->alloc(&d_rowoff, sizeof(unsigned) * rowoff.size()));
+    A(h->alloc(&d_slotbase, sizeof(int) * slotbase.size()));
+    A(h->alloc(&d_lane_demand, sizeof(int) * nl));
+    A(h->alloc(&d_Dn, sizeof(float) * nl));
+    A(h->alloc(&h->Dc, sizeof(double) * nl));
+    A(h->alloc(&d_np, nl));
+    A(h->alloc(&d_slot_path, sizeof(long long) * ns));
+    A(h->alloc(&d_cap, sizeof(float) * E));
+    A(h->alloc(&d_ne, sizeof(float) * E));
+    A(h->alloc(&d_inv, sizeof(float) * E));
+    A(h->alloc(&h->x, sizeof(float) * 2 * ns));
+    A(h->alloc(&h->u, sizeof(float) * E));
+    A(h->alloc(&h->w, sizeof(float) * E));
+    A(h->alloc(&h->loads, sizeof(float) * 3 * (size_t)E));
+    A(h->alloc(&h->part, sizeof(double) * 2 * 4 * (size_t)h->grid));
+    A(h->alloc(&h->barrier, sizeof(unsigned)));
+    A(h->alloc(&h->status, sizeof(int)));
+    A(h->alloc(&h->sc, sizeof(te::Scalars)));
+    A(h->alloc(&h->trace, sizeof(double) * te::kTraceWidth * kTraceCap));
+    A(h->alloc(&h->cta_blk, sizeof(int) * cta_blk.size()));
+    A(h->alloc(&h->xtmp, sizeof(float) * ns));
+    A(h->alloc(&h->user, sizeof(float) * (size_t)NP));
+    A(h->alloc(&h->gacc, sizeof(double) * 4));
+    A(h->alloc(&h->pbuf, sizeof(double) * E));
+    A(h->alloc(&h->dstage, sizeof(double) * K));
+    A(h->alloc(&h->flag, sizeof(int)));
+    A(h->alloc(&h->lam, sizeof(float) * nl));
+    A(h->alloc(&h->ctr, sizeof(unsigned) * 4));
+    A(h->alloc(&h->ps.S, sizeof(double) * nl));
+    A(h->alloc(&h->ps.loads, sizeof(double) * E));
+    A(h->alloc(&h->ps.viol, (size_t)E));
+    A(h->alloc(&h->ps.vidx, sizeof(int) * E));
+    A(h->alloc(&h->ps.nviol, sizeof(int)));
+    A(h->alloc(&h->ps.hist, sizeof(double) * 256 * (size_t)E));
+    A(h->alloc(&h->ps.prefix, sizeof(unsigned long long) * E));
+    A(h->alloc(&h->ps.rem, sizeof(double) * E));
+    A(h->alloc(&h->ps.Cp, ns));
+    if (ce != cudaSuccess) {
+        h->err = std::string("device allocation failed: ") + cudaGetErrorString(ce);
+        cudaGetLastError();
+        return bail(ce == cudaErrorMemoryAllocation ? TE_ENOMEM : TE_ECUDA);
+    }
+    cudaStream_t s = h->stream;
+    A(cudaMemcpyAsync(d_ids, ids.data(), ids.size(), cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_rowoff, rowoff.data(), sizeof(unsigned) * rowoff.size(), cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_slotbase, slotbase.data(), sizeof(int) * slotbase.size(), cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_lane_demand, lane_demand.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_Dn, Dn.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(h->Dc, Dc.data(), sizeof(double) * nl, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_np, npv.data(), nl, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_slot_path, slot_path.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_cap, cap_n.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_ne, ne_f.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_inv, inv_ne.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(h->cta_blk, cta_blk.data(), sizeof(int) * cta_blk.size(), cudaMemcpyHostToDevice, s));
+    if (ce != cudaSuccess) {
+        h->err = std::string("copy to device failed: ") + cudaGetErrorString(ce);
+        return bail(TE_ECUDA);
+    }
+    te::Layout& L = h->L;
+    L.E = E;
+    L.K = K;
+    L.P = NP;
+    L.nnz = P->nnz;
+    L.nblocks = nblocks;
+    L.nslots = nslots;
+    L.nrows = nrows;
+    L.id_bytes = id_bytes;
+    L.kmax = kmax;
+    L.ids = d_ids;
+    L.rowoff = d_rowoff;
+    L.slotbase = d_slotbase;
+    L.Dn = d_Dn;
+    h->Dn = d_Dn;
+    L.np = d_np;
+    L.lane_demand = d_lane_demand;
+    L.slot_path = d_slot_path;
+    L.cap_n = d_cap;
+    L.ne_f = d_ne;
+    L.inv_ne = d_inv;
+    // algorithmic traffic of one iteration: ids once, rates read and written,
+    // per-lane demand, per-slot row offsets, per-block slot bases
+    h->bytes_per_iter = (long long)ids.size() + 2LL * (long long)sizeof(float) * (long long)ns +
+                        (long long)sizeof(float) * (long long)nl + (long long)sizeof(unsigned) * (nslots + 1) +
+                        (long long)sizeof(int) * (nblocks + 1);
+    te_status rs = te_reset(h);
+    if (rs != TE_OK) return bail(rs);
+    *out = h;
+    return TE_OK;
+}
+
+extern "C" te_status te_reset(te_handle* h) {
+    if (!h) return TE_EINVAL;
+    cudaStream_t s = h->stream;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    A(te::launch_init_x(h->L, h->x, s));
+    h->launches += 1;
+    A(cudaMemsetAsync(h->u, 0, sizeof(float) * h->L.E, s));
+    A(cudaMemsetAsync(h->w, 0, sizeof(float) * h->L.E, s));
+    A(cudaMemsetAsync(h->lam, 0, sizeof(float) * (size_t)h->L.nblocks * kLanes, s));
+    te::Scalars sc{};
+    sc.beta = h->beta0;
+    sc.alpha = (isfinite(h->o.alpha_target) && h->o.alpha_start > h->o.alpha_target) ? h->o.alpha_target
+                                                                                     : h->o.alpha_start;
+    h->hsc = sc;
+    A(cudaMemcpyAsync(h->sc, &h->hsc, sizeof(sc), cudaMemcpyHostToDevice, s));
+    A(cudaStreamSynchronize(s));
+    return h->cuda(ce, "te_reset");
+}
+
+extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* out) {
+    if (!h) return TE_EINVAL;
+    if (max_iters < 0) return h->fail(TE_EINVAL, "max_iters must be >= 0");
+    cudaStream_t s = h->stream;
+    long long done = 0;
+    te_status rc = TE_OK;
+    int converged = 0, reason = 0;
+    while (done < max_iters || (max_iters == 0 && done == 0)) {
+        const long long chunk = std::min<long long>(max_iters - done, kItersPerLaunch);
+        if (chunk <= 0) break;
+        cudaError_t ce = cudaSuccess;
+        auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+        A(cudaMemsetAsync(h->loads, 0, sizeof(float) * 3 * (size_t)h->L.E, s));
+        A(cudaMemsetAsync(h->barrier, 0, sizeof(unsigned), s));
+        A(cudaMemsetAsync(h->ctr, 0, sizeof(unsigned) * 4, s));
+        A(cudaMemsetAsync(h->status, 0, sizeof(int), s));
+        te::IterArgs a{};
+        a.L = h->L;
+        a.o = h->o;
+        a.x = h->x;
+        a.u = h->u;
+        a.w = h->w;
+        a.loads = h->loads;
+        a.part = h->part;
+        a.barrier = h->barrier;
+        a.status = h->status;
+        a.sc = h->sc;
+        a.trace = h->trace;
+        a.trace_cap = kTraceCap;
+        a.cta_blk = h->cta_blk;
+        a.lam = h->lam;
+        a.ctr = h->ctr;
+        a.max_iters = chunk;
+        a.timeout_ns = h->timeout_ns;
+        A(te::launch_iter(a, h->grid, s));
+        h->launches += 1;
+        int status = 0;
+        A(cudaMemcpyAsync(&h->hsc, h->sc, sizeof(te::Scalars), cudaMemcpyDeviceToHost, s));
+        A(cudaMemcpyAsync(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+        A(cudaStreamSynchronize(s));
+        if (ce != cudaSuccess) return h->cuda(ce, "te_solve");
+        done += h->hsc.iters_run;
+        if (status == te::kStatusTimeout) {
+            rc = h->fail(TE_ETIMEOUT, "a grid-wide wait exceeded its time limit; state of the last completed "
+                                      "iteration kept");
+            break;
+        }
+        if (status == te::kStatusNumeric) {
+            rc = h->fail(TE_ENUMERIC, "a residual became NaN or Inf");
+            break;
+        }
+        if (h->hsc.converged) {
+            converged = 1;
+            reason = h->hsc.stop_reason;
+            break;
+        }
+        if (h->hsc.iters_run < chunk) break;
+    }
+    if (out) {
+        out->iters = done;
+        out->total_iters = h->hsc.iter_total;
+        out->r = h->hsc.r;
+        out->s = h->hsc.s;
+        out->beta = h->hsc.beta;
+        out->alpha = h->hsc.alpha;
+        out->converged = converged;
+        out->stop_reason = reason;
+    }
+    return rc;
+}
+
+extern "C" te_status te_allocation(te_handle* h, float* x_out, int32_t project, int32_t out_is_device) {
+    if (!h || !x_out) return TE_EINVAL;
+    cudaStream_t s = h->stream;
+    const size_t ns = (size_t)h->L.nslots * kLanes;
+    const float* src = h->x + (size_t)h->hsc.xbuf * ns;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    if (project) {
+        A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
+        A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
+        h->launches += te::kProjectLaunches;
+        src = h->xtmp;
+    }
+    float* dst = out_is_device ? x_out : h->user;
+    A(te::launch_to_user(h->L, src, dst, (float)h->scale, s));
+    h->launches += 1;
+    if (!out_is_device)
+        A(cudaMemcpyAsync(x_out, h->user, sizeof(float) * (size_t)h->L.P, cudaMemcpyDeviceToHost, s));
+    A(cudaStreamSynchronize(s));
+    return h->cuda(ce, "te_allocation");
+}
+
+extern "C" te_status te_gap(te_handle* h, double* gap_out, double* primal_out, double* dual_out) {
+    if (!h) return TE_EINVAL;
+    cudaStream_t s = h->stream;
+    const size_t ns = (size_t)h->L.nslots * kLanes;
+    const float* src = h->x + (size_t)h->hsc.xbuf * ns;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
+    A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
+    A(cudaMemsetAsync(h->gacc, 0, sizeof(double) * 4, s));
+    A(te::launch_gap_impl(h->L, h->xtmp, h->u, h->hsc.beta, h->hsc.alpha, h->scale, h->Dc, h->gacc, s));
+    h->launches += te::kProjectLaunches + 2;
+    double acc[4] = {0, 0, 0, 0};
+    A(cudaMemcpyAsync(acc, h->gacc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+    A(cudaStreamSynchronize(s));
+    if (ce != cudaSuccess) return h->cuda(ce, "te_gap");
+    const double primal = acc[0], dual = acc[1] + acc[2];
+    if (gap_out) *gap_out = dual - primal;
+    if (primal_out) *primal_out = primal;
+    if (dual_out) *dual_out = dual;
+    return TE_OK;
+}
+
+extern "C" te_status te_prices(te_handle* h, double* p_out, int32_t out_is_device) {
+    if (!h || !p_out) return TE_EINVAL;
+    cudaStream_t s = h->stream;
+    const double pscale = h->hsc.beta * pow(h->scale, -h->hsc.alpha);
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    double* dst = out_is_device ? p_out : h->pbuf;
+    A(te::launch_prices(h->L.E, h->u, pscale, dst, s));
+    h->launches += 1;
+    if (!out_is_device) A(cudaMemcpyAsync(p_out, h->pbuf, sizeof(double) * h->L.E, cudaMemcpyDeviceToHost, s));
+    A(cudaStreamSynchronize(s));
+    return h->cuda(ce, "te_prices");
+}
+
+extern "C" te_status te_set_warm_start(te_handle* h, const float* x0, int32_t in_is_device, int32_t keep_duals) {
+    if (!h || !x0) return TE_EINVAL;
+    cudaStream_t s = h->stream;
+    const size_t ns = (size_t)h->L.nslots * kLanes;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    const float* src = x0;
+    if (!in_is_device) {
+        A(cudaMemcpyAsync(h->user, x0, sizeof(float) * (size_t)h->L.P, cudaMemcpyHostToDevice, s));
+        src = h->user;
+    }
+    if (!keep_duals) {
+        te_status r = te_reset(h);
+        if (r != TE_OK) return r;
+    }
+    A(te::launch_from_user(h->L, src, h->x + (size_t)h->hsc.xbuf * ns, (float)(1.0 / h->scale), s));
+    h->launches += 1;
+    A(cudaStreamSynchronize(s));
+    return h->cuda(ce, "te_set_warm_start");
+}
+
+extern "C" te_status te_trace(te_handle* h, double* out, int64_t max_rows, int64_t* rows) {
+    if (!h || (!out && max_rows > 0) || max_rows < 0) return TE_EINVAL;
+    const long long total = h->hsc.iter_total;
+    const long long avail = std::min<long long>(total, kTraceCap);
+    const long long n = std::min<long long>(avail, max_rows);
+    std::vector<double> ring((size_t)kTraceCap * te::kTraceWidth);
+    cudaError_t ce = cudaMemcpyAsync(ring.data(), h->trace, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost,
+                                     h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    if (ce != cudaSuccess) return h->cuda(ce, "te_trace");
+    // oldest row first
+    const long long first = total - avail;
+    for (long long i = 0; i < n; ++i) {
+        const long long it = first + i;
+        memcpy(out + i * te::kTraceWidth, ring.data() + (size_t)(it % kTraceCap) * te::kTraceWidth,
+               sizeof(double) * te::kTraceWidth);
+    }
+    if (rows) *rows = n;
+    return TE_OK;
+}
+
+extern "C" te_status te_layout(const te_handle* h, te_layout_info* info) {
+    if (!h || !info) return TE_EINVAL;
+    info->n_demands = h->L.K;
+    info->n_paths = h->L.P;
+    info->nnz = h->L.nnz;
+    info->id_rows = h->L.nrows;
+    info->slots = h->L.nslots;
+    info->id_bytes = h->L.id_bytes;
+    info->grid = h->grid;
+    info->bytes_per_iter = h->bytes_per_iter;
+    info->device_bytes = h->device_bytes;
+    info->kernel_launches = h->launches;
+    return TE_OK;
+}
+
+extern "C" te_status te_set_demands(te_handle* h, const double* D, int32_t in_is_device) {
+    if (!h || !D) return TE_EINVAL;
+    cudaStream_t s = h->stream;
+    const int K = h->L.K;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    if (!in_is_device) {
+        for (int c = 0; c < K; ++c)
+            if (!(D[c] > 0.0) || !isfinite(D[c])) return h->fail(TE_EINVAL, fmt("demand %lld is not finite and positive", c));
+        A(cudaMemcpyAsync(h->dstage, D, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    } else {
+        A(cudaMemcpyAsync(h->dstage, D, sizeof(double) * K, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        k_check_demands<<<(K + 255) / 256, 256, 0, s>>>(K, h->dstage, h->flag);
+        h->launches += 1;
+        int bad = 0;
+        A(cudaGetLastError());
+        A(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        A(cudaStreamSynchronize(s));
+        if (ce != cudaSuccess) return h->cuda(ce, "te_set_demands");
+        if (bad) return h->fail(TE_EINVAL, "a demand is not finite and positive");
+    }
+    const long long lanes = (long long)h->L.nblocks * kLanes;
+    k_set_demands<<<(unsigned)((lanes + 255) / 256), 256, 0, s>>>(lanes, h->L.lane_demand, h->dstage,
+                                                                  1.0 / h->scale, h->Dn, h->Dc);
+    h->launches += 1;
+    A(cudaGetLastError());
+    A(cudaStreamSynchronize(s));
+    return h->cuda(ce, "te_set_demands");
+}

@@ -1,0 +1,320 @@
+// Feasibility projection of GATE (Algorithm 2, Section 3.5) on the sliced
+// device layout, plus the gathers between the sliced layout and the caller's
+// path order.
+//
+// Steps (all on a copy of the iterate, normalised units):
+//   1. x <- max(x, 0); S_c, L_e, V_e = max(L_e - C_e, 0), C_p = number of
+//      violated edges on p.
+//   2. Demand step: every demand with S_c > D_c trims its paths greedily in
+//      descending score S_c^alpha * C_p.  Inside one demand S_c is common, so
+//      the order is descending C_p, ties to the lower path index.
+//   3. Recompute S_c, L_e, V_e, C_p.
+//   4. Capacity step: every violated edge plans, from this one snapshot, the
+//      trims of its paths in descending score (ties to the lower path index)
+//      until V_e is covered; each path then loses the largest trim planned
+//      for it over its edges.  Each edge's load drops by at least V_e, so the
+//      result is feasible.  The plan of an edge is found without sorting: a
+//      radix select over the 64-bit key (score bits, then inverted path
+//      index) finds the threshold path at which the running sum of rates in
+//      key order reaches V_e; paths above it are trimmed in full and the
+//      threshold path by the remainder.
+// Scores are compared as alpha*log(S_c) + log(C_p) in FP32.
+#include <math.h>
+#include <stdint.h>
+
+#include "te_internal.cuh"
+
+namespace te {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 1048576) b = 1048576;
+    return (unsigned)b;
+}
+
+template <typename IdT>
+__device__ __forceinline__ const IdT* ids_of(const Layout& L) {
+    return static_cast<const IdT*>(L.ids);
+}
+
+// x <- max(x, 0) on every slot; S[lane] = sum of the lane's rates.
+__global__ void k_clamp_sum(Layout L, float* x, double* S) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    double acc = 0.0;
+    for (int j = 0; j < KB; ++j) {
+        float* p = &x[(size_t)(s0 + j) * kLanes + lane];
+        const float v = fmaxf(*p, 0.f);
+        *p = v;
+        acc += (double)v;
+    }
+    S[i] = acc;
+}
+
+// L_e = sum of rates over the paths through e (loads must be zeroed).
+template <typename IdT>
+__global__ void k_loads(Layout L, const float* x, double* loads) {
+    const IdT* ids = ids_of<IdT>(L);
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    for (int j = 0; j < KB; ++j) {
+        const size_t sl = (size_t)(s0 + j);
+        const float v = x[sl * kLanes + lane];
+        if (v == 0.f) continue;
+        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+            const IdT id = ids[(size_t)r * kLanes + lane];
+            if ((int)id != L.E) atomicAdd(&loads[id], (double)v);
+        }
+    }
+}
+
+// V_e > 0 flags, compact indices of violated edges and their violation.
+__global__ void k_viol(Layout L, const double* loads, unsigned char* viol, int* vidx, int* nviol, double* rem,
+                       unsigned long long* prefix) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= L.E) return;
+    const double V = loads[e] - (double)L.cap_n[e];
+    if (V > 0.0) {
+        viol[e] = 1;
+        const int v = atomicAdd(nviol, 1);
+        vidx[e] = v;
+        rem[v] = V;
+        prefix[v] = 0ull;
+    } else {
+        viol[e] = 0;
+        vidx[e] = -1;
+    }
+}
+
+// C_p = number of violated edges on each path.
+template <typename IdT>
+__global__ void k_count_viol(Layout L, const unsigned char* viol, unsigned char* Cp) {
+    const IdT* ids = ids_of<IdT>(L);
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    for (int j = 0; j < KB; ++j) {
+        const size_t sl = (size_t)(s0 + j);
+        int c = 0;
+        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+            const IdT id = ids[(size_t)r * kLanes + lane];
+            if ((int)id != L.E) c += viol[id];
+        }
+        Cp[sl * kLanes + lane] = (unsigned char)(c > 255 ? 255 : c);
+    }
+}
+
+// Demand step: trims S_c - D_c from the demand's paths in descending C_p,
+// ties to the lower path (slot) index.
+__global__ void k_demand_trim(Layout L, float* x, const double* S, const unsigned char* Cp) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const double D = (double)L.Dn[i];
+    double Ec = S[i] - D;
+    if (!(Ec > 0.0) || D <= 0.0) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b];
+    const int np = L.np[i];
+    unsigned taken = 0u;  // np <= 32
+    for (int k = 0; k < np && Ec > 0.0; ++k) {
+        int best = -1, bc = -1;
+        for (int j = 0; j < np; ++j) {
+            if (taken & (1u << j)) continue;
+            const int c = Cp[(size_t)(s0 + j) * kLanes + lane];
+            if (c > bc) { bc = c; best = j; }
+        }
+        taken |= 1u << best;
+        float* p = &x[(size_t)(s0 + best) * kLanes + lane];
+        const double d = fmin(Ec, (double)*p);
+        *p = d >= (double)*p ? 0.f : __double2float_rd((double)*p - d);
+        Ec -= d;
+    }
+}
+
+__device__ __forceinline__ unsigned orderable(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Key of a path: high word = orderable(alpha log S_c + log C_p), low word =
+// inverted caller path index (lower index ranks first among equal scores).
+__device__ __forceinline__ unsigned long long path_key(double S, int Cp, float alpha, long long user_path) {
+    float ls;
+    if (Cp <= 0) ls = -INFINITY;
+    else if (alpha == 0.f) ls = logf((float)Cp);
+    else ls = (S > 0.0) ? fmaf(alpha, logf((float)S), logf((float)Cp)) : -INFINITY;
+    return ((unsigned long long)orderable(ls) << 32) | (unsigned long long)(0xffffffffu - (unsigned)user_path);
+}
+
+// One radix-select pass: per violated edge, histogram of the rates of the
+// candidate paths (keys matching the selected prefix) by the next 8-bit digit.
+template <typename IdT>
+__global__ void k_select_hist(Layout L, const float* x, const double* S, const unsigned char* Cp,
+                              const int* vidx, const unsigned long long* prefix, const unsigned char* done,
+                              double* hist, float alpha, int pass) {
+    const IdT* ids = ids_of<IdT>(L);
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    const int shift = 56 - 8 * pass;
+    for (int j = 0; j < KB; ++j) {
+        const size_t sl = (size_t)(s0 + j);
+        const float v = x[sl * kLanes + lane];
+        const int c = Cp[sl * kLanes + lane];
+        if (v == 0.f || c == 0) continue;
+        const unsigned long long key = path_key(S[i], c, alpha, L.slot_path[sl * kLanes + lane]);
+        const int digit = (int)((key >> shift) & 0xffull);
+        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+            const IdT id = ids[(size_t)r * kLanes + lane];
+            if ((int)id == L.E) continue;
+            const int vi = vidx[id];
+            if (vi < 0 || done[vi]) continue;
+            if (pass > 0 && ((key ^ prefix[vi]) >> (shift + 8)) != 0ull) continue;
+            atomicAdd(&hist[(size_t)vi * 256 + digit], (double)v);
+        }
+    }
+}
+
+// Per violated edge: choose the digit at which the running sum (from the top
+// digit down) reaches the remaining violation.
+__global__ void k_select_pick(const int* nviol, double* hist, unsigned long long* prefix, double* rem,
+                              unsigned char* done, int pass) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= *nviol || done[v]) return;
+    const int shift = 56 - 8 * pass;
+    double* h = hist + (size_t)v * 256;
+    double cum = 0.0;
+    const double need = rem[v];
+    int pick = -1;
+    for (int d = 255; d >= 0; --d) {
+        const double c = h[d];
+        h[d] = 0.0;  // ready for the next pass
+        if (pick < 0) {
+            if (cum + c >= need && c > 0.0) pick = d;
+            else cum += c;
+        }
+    }
+    if (pick < 0) {
+        // rounding left the candidates short of V_e: trim all of them in full
+        done[v] = 2;
+        return;
+    }
+    prefix[v] |= (unsigned long long)pick << shift;
+    rem[v] = need - cum;
+}
+
+// Apply: every path loses the largest trim planned for it by its violated
+// edges.
+template <typename IdT>
+__global__ void k_edge_trim(Layout L, float* x, const double* S, const unsigned char* Cp, const int* vidx,
+                            const unsigned long long* prefix, const double* rem, const unsigned char* done,
+                            float alpha) {
+    const IdT* ids = ids_of<IdT>(L);
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    for (int j = 0; j < KB; ++j) {
+        const size_t sl = (size_t)(s0 + j);
+        const float v = x[sl * kLanes + lane];
+        const int c = Cp[sl * kLanes + lane];
+        if (v == 0.f || c == 0) continue;
+        const unsigned long long key = path_key(S[i], c, alpha, L.slot_path[sl * kLanes + lane]);
+        double trim = 0.0;
+        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+            const IdT id = ids[(size_t)r * kLanes + lane];
+            if ((int)id == L.E) continue;
+            const int vi = vidx[id];
+            if (vi < 0) continue;
+            double t;
+            if (done[vi] == 2) {
+                // all candidates (keys at or above the chosen prefix) in full
+                t = key >= prefix[vi] ? (double)v : 0.0;
+            } else if (key > prefix[vi]) {
+                t = (double)v;
+            } else if (key == prefix[vi]) {
+                t = fmin((double)v, rem[vi]);
+            } else {
+                t = 0.0;
+            }
+            trim = fmax(trim, t);
+        }
+        // a full trim leaves exactly zero; a partial one rounds down so the
+        // edge ends at or below its capacity
+        x[sl * kLanes + lane] = trim >= (double)v ? 0.f : __double2float_rd((double)v - trim);
+    }
+}
+
+__global__ void k_to_user(Layout L, const float* x, float* out, float scale) {
+    const long long n = L.nslots * kLanes;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long p = L.slot_path[i];
+        if (p >= 0) out[p] = x[i] * scale;
+    }
+}
+
+__global__ void k_from_user(Layout L, const float* in, float* x, float inv_scale) {
+    const long long n = L.nslots * kLanes;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long p = L.slot_path[i];
+        x[i] = p >= 0 ? in[p] * inv_scale : 0.f;
+    }
+}
+
+template <typename IdT>
+cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st) {
+    const long long lanes = (long long)L.nblocks * kLanes;
+    const unsigned gl = grid_for(lanes, kThreads);
+    const unsigned ge = grid_for(L.E, kThreads);
+    cudaError_t err;
+    for (int round = 0; round < 2; ++round) {
+        k_clamp_sum<<<gl, kThreads, 0, st>>>(L, x, s.S);
+        if ((err = cudaMemsetAsync(s.loads, 0, sizeof(double) * (size_t)L.E, st)) != cudaSuccess) return err;
+        if ((err = cudaMemsetAsync(s.nviol, 0, sizeof(int), st)) != cudaSuccess) return err;
+        k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
+        k_viol<<<ge, kThreads, 0, st>>>(L, s.loads, s.viol, s.vidx, s.nviol, s.rem, s.prefix);
+        k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, s.viol, s.Cp);
+        if (round == 0) k_demand_trim<<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp);
+    }
+    // capacity step: radix select of each violated edge's threshold path
+    unsigned char* done = s.viol;  // reuse: per violated-edge flags (E bytes >= nviol)
+    if ((err = cudaMemsetAsync(done, 0, (size_t)L.E, st)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(s.hist, 0, sizeof(double) * 256 * (size_t)L.E, st)) != cudaSuccess) return err;
+    for (int pass = 0; pass < 8; ++pass) {
+        k_select_hist<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, done, s.hist, alpha, pass);
+        k_select_pick<<<ge, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);
+    }
+    k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, s.rem, done, alpha);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_project(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st) {
+    if (L.id_bytes == 2) return project_t<uint16_t>(L, x, alpha, s, st);
+    return project_t<int32_t>(L, x, alpha, s, st);
+}
+
+cudaError_t launch_to_user(const Layout& L, const float* x, float* out, float scale, cudaStream_t st) {
+    k_to_user<<<grid_for(L.nslots * kLanes, kThreads), kThreads, 0, st>>>(L, x, out, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_user(const Layout& L, const float* in, float* x, float inv_scale, cudaStream_t st) {
+    k_from_user<<<grid_for(L.nslots * kLanes, kThreads), kThreads, 0, st>>>(L, in, x, inv_scale);
+    return cudaGetLastError();
+}
+
+}  // namespace te

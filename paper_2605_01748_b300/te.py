@@ -1,0 +1,295 @@
+"""Python binding of libte.so (include/te.h): argument marshalling only.
+
+Every step of the TE iteration runs inside libte's CUDA kernels; this module
+only turns NumPy arrays and torch CUDA tensors into pointers.  Importing it
+loads libte.so and fails loudly when the library has not been built
+(``python -m paper_2605_01748_b300.build``); there is no CPU fallback.
+
+The functions mirror the C entry points one to one (``te_create``,
+``te_solve``, ``te_allocation``, ``te_gap``, ``te_prices``,
+``te_set_warm_start``, ``te_reset``, ``te_trace``, ``te_layout``,
+``te_destroy``, ``te_last_error``); :class:`TE` bundles a handle with them.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libte.so")
+
+TE_OK, TE_EINVAL, TE_ENOMEM, TE_ECUDA, TE_ETIMEOUT, TE_ENUMERIC, TE_ENOTCONVERGED, TE_EUNSUPPORTED = range(8)
+STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "TE_ETIMEOUT",
+                5: "TE_ENUMERIC", 6: "TE_ENOTCONVERGED", 7: "TE_EUNSUPPORTED"}
+
+EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_gap", "te_prices",
+            "te_set_warm_start", "te_set_demands", "te_reset", "te_trace", "te_layout", "te_destroy",
+            "te_last_error")
+
+
+class TEError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class te_topology(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("edge_src", ctypes.c_void_p), ("edge_dst", ctypes.c_void_p)]
+
+
+class te_paths(ctypes.Structure):
+    _fields_ = [("n_demands", ctypes.c_int32), ("pad_", ctypes.c_int32), ("n_paths", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("demand_src", ctypes.c_void_p), ("demand_dst", ctypes.c_void_p),
+                ("demand_path_off", ctypes.c_void_p), ("path_edge_off", ctypes.c_void_p),
+                ("path_edges", ctypes.c_void_p)]
+
+
+class te_options(ctypes.Structure):
+    _fields_ = [("alpha_target", ctypes.c_double), ("alpha_start", ctypes.c_double),
+                ("alpha_step", ctypes.c_double), ("alpha_max", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("A", ctypes.c_double), ("C", ctypes.c_double), ("beta0", ctypes.c_double),
+                ("adapt_beta", ctypes.c_int32), ("continuation", ctypes.c_int32),
+                ("scale_mode", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
+                ("test_withhold_cta", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+class te_solve_result(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int64), ("total_iters", ctypes.c_int64), ("r", ctypes.c_double),
+                ("s", ctypes.c_double), ("beta", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("converged", ctypes.c_int32), ("stop_reason", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class te_layout_info(ctypes.Structure):
+    _fields_ = [("n_demands", ctypes.c_int64), ("n_paths", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("id_rows", ctypes.c_int64), ("slots", ctypes.c_int64), ("id_bytes", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("bytes_per_iter", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2605_01748_b300.build` "
+                          "(the TE engine has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    H = ctypes.c_void_p
+    lib.te_default_options.restype = None
+    lib.te_default_options.argtypes = [ctypes.POINTER(te_options)]
+    lib.te_create.restype = ctypes.c_int
+    lib.te_create.argtypes = [ctypes.POINTER(te_topology), ctypes.POINTER(te_paths), P, P,
+                              ctypes.POINTER(te_options), ctypes.POINTER(H)]
+    lib.te_solve.restype = ctypes.c_int
+    lib.te_solve.argtypes = [H, ctypes.c_int64, ctypes.POINTER(te_solve_result)]
+    lib.te_allocation.restype = ctypes.c_int
+    lib.te_allocation.argtypes = [H, P, ctypes.c_int32, ctypes.c_int32]
+    lib.te_gap.restype = ctypes.c_int
+    lib.te_gap.argtypes = [H, P, P, P]
+    lib.te_prices.restype = ctypes.c_int
+    lib.te_prices.argtypes = [H, P, ctypes.c_int32]
+    lib.te_set_warm_start.restype = ctypes.c_int
+    lib.te_set_warm_start.argtypes = [H, P, ctypes.c_int32, ctypes.c_int32]
+    lib.te_set_demands.restype = ctypes.c_int
+    lib.te_set_demands.argtypes = [H, P, ctypes.c_int32]
+    lib.te_reset.restype = ctypes.c_int
+    lib.te_reset.argtypes = [H]
+    lib.te_trace.restype = ctypes.c_int
+    lib.te_trace.argtypes = [H, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.te_layout.restype = ctypes.c_int
+    lib.te_layout.argtypes = [H, ctypes.POINTER(te_layout_info)]
+    lib.te_destroy.restype = None
+    lib.te_destroy.argtypes = [H]
+    lib.te_last_error.restype = ctypes.c_char_p
+    lib.te_last_error.argtypes = [H]
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _ptr(a) -> int:
+    """Pointer of a NumPy array or a torch tensor (host or device)."""
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    return int(a.ctypes.data)
+
+
+def _is_device(a) -> bool:
+    return bool(getattr(a, "is_cuda", False))
+
+
+def te_last_error(h) -> str:
+    msg = _lib.te_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def _check(status: int, h) -> None:
+    if status != TE_OK:
+        raise TEError(status, te_last_error(h))
+
+
+def te_default_options(**overrides) -> te_options:
+    o = te_options()
+    _lib.te_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "cuda_stream" and v is not None and not isinstance(v, int):
+            v = int(getattr(v, "cuda_stream", v))
+        setattr(o, k, v)
+    return o
+
+
+class _Keep:
+    """Holds contiguous copies of the inputs while te_create reads them."""
+
+    def __init__(self, inst):
+        c = np.ascontiguousarray
+        self.edge_src = c(inst.edge_src, dtype=np.int32)
+        self.edge_dst = c(inst.edge_dst, dtype=np.int32)
+        self.capacity = c(inst.capacity, dtype=np.float64)
+        self.demand_src = c(inst.demand_src, dtype=np.int32)
+        self.demand_dst = c(inst.demand_dst, dtype=np.int32)
+        self.demand = c(inst.demand, dtype=np.float64)
+        self.dpo = c(inst.demand_path_off, dtype=np.int64)
+        self.peo = c(inst.path_edge_off, dtype=np.int64)
+        self.pe = c(inst.path_edges, dtype=np.int32)
+
+
+def te_create(inst, options: Optional[te_options] = None, check_walks: bool = True):
+    """Creates a handle from an instance (any object with the fields of
+    paper_2605_01748_b300.instances.Instance)."""
+    k = _Keep(inst)
+    topo = te_topology(int(inst.n_nodes), k.capacity.shape[0], _ptr(k.edge_src) if check_walks else 0,
+                       _ptr(k.edge_dst) if check_walks else 0)
+    paths = te_paths(k.demand.shape[0], 0, k.peo.shape[0] - 1, k.pe.shape[0],
+                     _ptr(k.demand_src) if check_walks else 0, _ptr(k.demand_dst) if check_walks else 0,
+                     _ptr(k.dpo), _ptr(k.peo), _ptr(k.pe))
+    h = ctypes.c_void_p()
+    opts = options if options is not None else te_default_options()
+    st = _lib.te_create(ctypes.byref(topo), ctypes.byref(paths), _ptr(k.demand), _ptr(k.capacity),
+                        ctypes.byref(opts), ctypes.byref(h))
+    if st != TE_OK:
+        raise TEError(st, te_last_error(None))
+    return h
+
+
+def te_solve(h, max_iters: int) -> te_solve_result:
+    res = te_solve_result()
+    _check(_lib.te_solve(h, int(max_iters), ctypes.byref(res)), h)
+    return res
+
+
+def te_allocation(h, out, project: bool = True) -> None:
+    """Writes rates (caller path order, FP32) into `out`: a NumPy float32
+    array or a torch float32 CUDA tensor of n_paths entries."""
+    _check(_lib.te_allocation(h, _ptr(out), int(bool(project)), int(_is_device(out))), h)
+
+
+def te_gap(h):
+    g, p, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.te_gap(h, ctypes.byref(g), ctypes.byref(p), ctypes.byref(d)), h)
+    return g.value, p.value, d.value
+
+
+def te_prices(h, out) -> None:
+    _check(_lib.te_prices(h, _ptr(out), int(_is_device(out))), h)
+
+
+def te_set_warm_start(h, x0, keep_duals: bool = False) -> None:
+    _check(_lib.te_set_warm_start(h, _ptr(x0), int(_is_device(x0)), int(bool(keep_duals))), h)
+
+
+def te_set_demands(h, demands) -> None:
+    """demands: FP64 NumPy array (host) or torch float64 CUDA tensor."""
+    _check(_lib.te_set_demands(h, _ptr(demands), int(_is_device(demands))), h)
+
+
+def te_reset(h) -> None:
+    _check(_lib.te_reset(h), h)
+
+
+def te_trace(h, max_rows: int) -> np.ndarray:
+    out = np.zeros((max(int(max_rows), 0), 5), dtype=np.float64)
+    n = ctypes.c_int64()
+    _check(_lib.te_trace(h, _ptr(out) if max_rows > 0 else 0, int(max_rows), ctypes.byref(n)), h)
+    return out[:n.value]
+
+
+def te_layout(h) -> dict:
+    info = te_layout_info()
+    _check(_lib.te_layout(h, ctypes.byref(info)), h)
+    return info.as_dict()
+
+
+def te_destroy(h) -> None:
+    _lib.te_destroy(h)
+
+
+class TE:
+    """One TE instance resident on the current CUDA device."""
+
+    def __init__(self, inst, **options):
+        self.n_paths = int(inst.n_paths)
+        self.n_edges = int(inst.n_edges)
+        self.options = te_default_options(**options)
+        self.h = te_create(inst, self.options)
+
+    def solve(self, max_iters: int) -> dict:
+        return te_solve(self.h, max_iters).as_dict()
+
+    def allocation(self, project: bool = True, out=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros(self.n_paths, dtype=np.float32)
+        te_allocation(self.h, out, project)
+        return out
+
+    def gap(self):
+        return te_gap(self.h)
+
+    def prices(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros(self.n_edges, dtype=np.float64)
+        te_prices(self.h, out)
+        return out
+
+    def warm_start(self, x0, keep_duals: bool = False) -> None:
+        te_set_warm_start(self.h, x0, keep_duals)
+
+    def set_demands(self, demands) -> None:
+        te_set_demands(self.h, demands)
+
+    def reset(self) -> None:
+        te_reset(self.h)
+
+    def trace(self, max_rows: int = 1 << 16) -> np.ndarray:
+        return te_trace(self.h, max_rows)
+
+    def layout(self) -> dict:
+        return te_layout(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            te_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,214 @@
+"""CUDA path (through the C-ABI) against the FP64 oracle on the same seeded
+inputs.
+
+Tolerances: after an equal number of iterations the FP32 iterate must match
+the FP64 oracle within 1e-4 relative in the max-norm over paths (relative to
+the largest rate); per-demand totals within 1e-4 relative where the total is
+at least 1% of the largest total, and within 1e-4 of the largest total
+elsewhere; prices likewise in the max-norm.  The FP32 iterate carries
+absolute rounding errors proportional to the largest rates and prices (the
+consensus terms of all demands share the edge prices), so a relative bound
+on a demand far below the largest one would measure that floor, not the
+method.  FP32 rounding (2^-24 per operation) amplified over these horizons
+stays about an order of magnitude under the 1e-4 bar.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import refsolvers as R
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def te():
+    from paper_2605_01748_b300 import build
+    build.build_te()
+    from paper_2605_01748_b300 import te as te_mod
+    return te_mod
+
+
+def _rel_inf(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _compare(inst, x_gpu, x_ref, tol=TOL):
+    assert _rel_inf(x_gpu, x_ref) <= tol, _rel_inf(x_gpu, x_ref)
+    Sg = O.demand_totals(inst, x_gpu)
+    Sr = O.demand_totals(inst, x_ref)
+    err = np.abs(Sg - Sr) / np.maximum(Sr, 1e-2 * Sr.max())
+    assert err.max() <= tol, err.max()
+
+
+def _pair(te, inst, iters, **kw):
+    """Runs the GPU and the oracle with the same options for `iters` steps."""
+    t = te.TE(inst, **kw)
+    res = t.solve(iters)
+    okw = {k: v for k, v in kw.items() if k in ("alpha_target", "alpha_start", "alpha_step", "alpha_max",
+                                               "gamma", "A", "C", "beta0", "adapt_beta", "continuation")}
+    s = O.OracleSolver(inst, **okw)
+    s.run(iters)
+    return t, res, s
+
+
+@pytest.mark.parametrize("alpha,beta0", [(0.0, 2.0), (1.0, 1.0), (2.0, 4.0), (3.5, 1.0)])
+def test_fixed_schedule_parity_tiny(te, tiny, alpha, beta0):
+    kw = dict(alpha_target=alpha, alpha_start=alpha, beta0=beta0, adapt_beta=0, continuation=0, gamma=-1.0)
+    for iters in (1, 7, 60):
+        t, res, s = _pair(te, tiny, iters, **kw)
+        assert res["iters"] == iters and s.iters == iters
+        _compare(tiny, t.allocation(project=False), s.allocation())
+        p = t.prices()
+        assert _rel_inf(p, s.prices()) <= TOL
+        assert (p >= 0).all()
+        t.close()
+
+
+def test_adaptive_continuation_parity_tiny(te, tiny):
+    """Default options (residual balancing, max-min continuation): the beta and
+    alpha decisions match the oracle's, and so does the iterate."""
+    iters = 400
+    t, res, s = _pair(te, tiny, iters, gamma=1e-3)
+    tg = t.trace(iters)
+    to = s.trace
+    n = min(tg.shape[0], to.shape[0])
+    assert n == iters
+    same = np.where((tg[:n, 2] != to[:n, 2]) | (tg[:n, 3] != to[:n, 3]))[0]
+    first_diff = int(same[0]) if same.size else n
+    assert first_diff >= 150, first_diff
+    np.testing.assert_allclose(tg[:first_diff, 0], to[:first_diff, 0], rtol=2e-3, atol=1e-7)
+    np.testing.assert_allclose(tg[:first_diff, 1], to[:first_diff, 1], rtol=2e-3, atol=1e-7)
+    if first_diff == n:
+        _compare(tiny, t.allocation(project=False), s.allocation(), tol=1e-3)
+    t.close()
+
+
+def test_fixed_schedule_parity_medium(te, medium):
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=2.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t, res, s = _pair(te, medium, 40, **kw)
+    _compare(medium, t.allocation(project=False), s.allocation())
+    t.close()
+
+
+def test_ragged_and_wide_instances(te, tiny):
+    """A demand subset that leaves a ragged last block, single-path demands,
+    and a demand with 32 paths (the widest supported)."""
+    from paper_2605_01748_b300 import instances
+    sub = instances.subset(tiny, np.arange(0, tiny.n_demands, 3))
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t, _, s = _pair(te, sub, 30, **kw)
+    _compare(sub, t.allocation(project=False), s.allocation())
+    t.close()
+    k1 = R.first_path_only(tiny)
+    t, _, s = _pair(te, k1, 30, **kw)
+    _compare(k1, t.allocation(project=False), s.allocation())
+    t.close()
+    # 32 parallel two-hop paths between one pair, plus a competing demand
+    from paper_2605_01748_b300.instances import Instance
+    n_mid = 32
+    src = np.concatenate([np.zeros(n_mid), 1 + np.arange(n_mid)]).astype(np.int32)
+    dst = np.concatenate([1 + np.arange(n_mid), np.full(n_mid, n_mid + 1)]).astype(np.int32)
+    cap = np.linspace(1.0, 4.0, 2 * n_mid)
+    pe = np.stack([np.arange(n_mid), n_mid + np.arange(n_mid)], 1).ravel().astype(np.int32)
+    inst = Instance("wide", n_mid + 2, src, dst, cap, np.array([0, 0], np.int32),
+                    np.array([n_mid + 1, 1], np.int32), np.array([200.0, 3.0]),
+                    np.array([0, n_mid, n_mid + 1], np.int64),
+                    np.concatenate([np.arange(0, 2 * n_mid + 1, 2), [2 * n_mid + 1]]).astype(np.int64),
+                    np.concatenate([pe, [0]]).astype(np.int32), {})
+    t, _, s = _pair(te, inst, 30, **kw)
+    _compare(inst, t.allocation(project=False), s.allocation())
+    t.close()
+
+
+def test_int32_edge_ids(te):
+    """More than 65534 edges switches the device layout to 32-bit ids."""
+    from paper_2605_01748_b300.instances import Instance
+    rng = np.random.default_rng(1)
+    E = 70000
+    # a star of parallel one-hop links between node 0 and 1 plus decoys
+    src = np.zeros(E, np.int32)
+    dst = np.ones(E, np.int32)
+    cap = rng.uniform(1.0, 2.0, E)
+    K = 300
+    npaths = rng.integers(1, 5, K)
+    dpo = np.concatenate([[0], np.cumsum(npaths)]).astype(np.int64)
+    P = int(dpo[-1])
+    pe = rng.integers(0, E, P).astype(np.int32)
+    pe[:50] = E - 1 - np.arange(50)
+    inst = Instance("many-edges", 2, src, dst, cap, np.zeros(K, np.int32), np.ones(K, np.int32),
+                    rng.uniform(0.5, 3.0, K), dpo, np.arange(P + 1, dtype=np.int64), pe, {})
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t = te.TE(inst, **kw)
+    assert t.layout()["id_bytes"] == 4
+    t.solve(20)
+    s = O.OracleSolver(inst, **kw)
+    s.run(20)
+    _compare(inst, t.allocation(project=False), s.allocation())
+    t.close()
+
+
+def test_parking_lot_closed_form_on_gpu(te):
+    L = 3
+    inst = R.parking_lot(L)
+    for alpha in (1.0, 2.0):
+        t = te.TE(inst, alpha_target=alpha, alpha_start=alpha, gamma=1e-7)
+        res = t.solve(100000)
+        assert res["converged"] == 1
+        x = t.allocation(project=False)
+        assert abs(x[0] - R.parking_lot_alpha_fair(L, alpha)) <= 1e-3
+        t.close()
+
+
+def test_projection_parity_and_feasibility(te, tiny, medium):
+    for inst, iters in ((tiny, 25), (tiny, 200), (medium, 30)):
+        t = te.TE(inst, gamma=-1.0)
+        t.solve(iters)
+        x = t.allocation(project=False)
+        xg = t.allocation(project=True)
+        alpha = t.solve(0)["alpha"]
+        # feasibility of the GPU's own projection (FP32 sums: relative 1e-5)
+        assert (xg >= 0).all()
+        assert (O.demand_totals(inst, xg) <= inst.demand * (1 + 1e-5)).all()
+        assert (O.edge_loads(inst, xg) <= inst.capacity * (1 + 1e-5)).all()
+        # the oracle's FP64 projection of the same input
+        xo = O.project(inst, x.astype(np.float64), alpha)
+        assert _rel_inf(xg, xo) <= 1e-3, _rel_inf(xg, xo)
+        # near-ties aside, both keep the same served total
+        assert abs(xg.sum() - xo.sum()) <= 1e-4 * xo.sum()
+        t.close()
+
+
+def test_gap_parity(te, tiny):
+    for alpha in (0.0, 1.0):
+        t = te.TE(tiny, alpha_target=alpha, alpha_start=alpha, gamma=1e-5)
+        t.solve(20000)
+        g, pr, du = t.gap()
+        xp = t.allocation(project=True).astype(np.float64)
+        go, pro, duo = O.gap(tiny, xp, t.prices(), alpha)
+        assert abs(pr - pro) <= 1e-6 * max(1.0, abs(pro))
+        assert abs(du - duo) <= 1e-6 * max(1.0, abs(duo))
+        assert g >= -1e-6 * abs(pr)
+        assert g <= 1e-2 * abs(pr), (g, pr)
+        t.close()
+
+
+def test_warm_start_and_reset(te, tiny):
+    t = te.TE(tiny, gamma=1e-3)
+    t.solve(300)
+    x_warm = t.allocation(project=True)
+    t.reset()
+    r0 = t.solve(0)
+    assert r0["total_iters"] == 0
+    x0 = t.allocation(project=False)
+    npaths = np.diff(tiny.demand_path_off)
+    np.testing.assert_allclose(x0, np.repeat(tiny.demand / npaths, npaths), rtol=1e-6)
+    t.warm_start(x_warm)
+    np.testing.assert_allclose(t.allocation(project=False), x_warm, rtol=1e-6, atol=1e-6)
+    t.close()

@@ -106,7 +106,7 @@ def test_collapse_matches_expanded_iteration(tiny, alpha, beta):
     s = O.OracleSolver(tiny, alpha_target=alpha, alpha_start=alpha, beta0=beta, adapt_beta=False,
                        continuation=False, gamma=-1.0)
     s.run(iters)
-    x_e, y_e, u_e = O.run_expanded(tiny, beta, alpha, iters)
+    x_e, y_e, u_e = O.run_expanded(tiny, beta, alpha, iters, scale=s.scale)
     assert np.max(np.abs(s.x - x_e)) <= 1e-11 * max(1.0, np.max(np.abs(x_e)))
     # every consensus dual on an edge equals that edge's price; y = x - d
     plen = np.diff(tiny.path_edge_off)
@@ -210,7 +210,7 @@ def test_iteration_invariants_and_balancing_rule(tiny):
         assert (s.u >= 0).all()
         assert (s.x >= 0).all()
     tr = s.trace
-    beta_before = np.concatenate([[1.0], tr[:-1, 2]])
+    beta_before = np.concatenate([[beta_prev], tr[:-1, 2]])
     r, sres, beta = tr[:, 0], tr[:, 1], tr[:, 2]
     up = r > 10 * sres
     down = (~up) & (sres > 10 * r)

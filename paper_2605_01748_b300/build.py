@@ -61,18 +61,20 @@ def build_gen(force: bool = False, verbose: bool = False) -> str:
     return LIBTEGEN
 
 
-def build_te(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale(LIBTE, TE_SOURCES, _headers()):
-        return LIBTE
+def build_te(force: bool = False, verbose: bool = False, out: str = LIBTE) -> str:
+    if not force and not _stale(out, TE_SOURCES, _headers()):
+        return out
     nvcc = _nvcc()
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-I", INCLUDE, "-I", CSRC, "-o", LIBTE]
+           "-I", INCLUDE, "-I", CSRC, "-o", out]
     if os.environ.get("TE_PTXAS_VERBOSE"):
         cmd += ["-Xptxas", "-v"]
+    if os.environ.get("TE_ITER_THREADS"):
+        cmd += [f"-DTE_ITER_THREADS={int(os.environ['TE_ITER_THREADS'])}"]
     cmd += [os.path.join(CSRC, s) for s in TE_SOURCES]
     cmd += ["-lcudart"]
     _run(cmd, verbose)
-    return LIBTE
+    return out
 
 
 def build_all(force: bool = False, verbose: bool = False) -> None:

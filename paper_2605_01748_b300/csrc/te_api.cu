@@ -298,15 +298,27 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
         order[c] = {key, c};
     }
     std::sort(order.begin(), order.end());
-    const int nblocks = (K + kLanes - 1) / kLanes;
+    // lanes per demand: no lane holds more than kMaxPathsPerLane paths
+    const int G = kmax <= te::kMaxPathsPerLane ? 1 : (kmax <= 2 * te::kMaxPathsPerLane ? 2 : 4);
+    const int DPB = kLanes / G;  // demands per block
+    const int kl = (kmax + G - 1) / G;
+    const int nblocks = (K + DPB - 1) / DPB;
+    auto demand_at = [&](int b, int t) -> int {  // demand index of block b, position t, or -1
+        const long long q = (long long)b * DPB + t;
+        return q < K ? order[q].second : -1;
+    };
+    auto path_len = [&](int c, long long p) -> long long {
+        const long long r = P->demand_path_off[c] + p;
+        return P->path_edge_off[r + 1] - P->path_edge_off[r];
+    };
     std::vector<int> slotbase(nblocks + 1, 0);
     for (int b = 0; b < nblocks; ++b) {
         int kb = 0;
-        for (int t = 0; t < kLanes; ++t) {
-            const int q = b * kLanes + t;
-            if (q >= K) break;
-            const int c = order[q].second;
-            kb = std::max(kb, (int)(P->demand_path_off[c + 1] - P->demand_path_off[c]));
+        for (int t = 0; t < DPB; ++t) {
+            const int c = demand_at(b, t);
+            if (c < 0) break;
+            const int np = (int)(P->demand_path_off[c + 1] - P->demand_path_off[c]);
+            kb = std::max(kb, (np + G - 1) / G);
         }
         slotbase[b + 1] = slotbase[b] + kb;
     }
@@ -315,13 +327,14 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     for (int b = 0; b < nblocks; ++b) {
         for (int j = 0; j < slotbase[b + 1] - slotbase[b]; ++j) {
             long long H = 0;
-            for (int t = 0; t < kLanes; ++t) {
-                const int q = b * kLanes + t;
-                if (q >= K) break;
-                const int c = order[q].second;
-                const long long p0 = P->demand_path_off[c];
-                if (j < P->demand_path_off[c + 1] - p0)
-                    H = std::max<long long>(H, P->path_edge_off[p0 + j + 1] - P->path_edge_off[p0 + j]);
+            for (int t = 0; t < DPB; ++t) {
+                const int c = demand_at(b, t);
+                if (c < 0) break;
+                const long long np = P->demand_path_off[c + 1] - P->demand_path_off[c];
+                for (int hh = 0; hh < G; ++hh) {
+                    const long long p = (long long)j * G + hh;
+                    if (p < np) H = std::max<long long>(H, path_len(c, p));
+                }
             }
             const long long s = slotbase[b] + j;
             const long long next = (long long)rowoff[s] + H;
@@ -345,22 +358,25 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
         std::fill(q, q + (size_t)nrows * kLanes, (int32_t)E);
     }
     for (int b = 0; b < nblocks; ++b) {
-        for (int t = 0; t < kLanes; ++t) {
-            const int q = b * kLanes + t;
-            if (q >= K) break;
-            const int c = order[q].second;
-            const size_t li = (size_t)b * kLanes + t;
-            lane_demand[li] = c;
-            Dn[li] = (float)(D[c] / scale);
-            Dc[li] = D[c];
+        for (int t = 0; t < DPB; ++t) {
+            const int c = demand_at(b, t);
+            if (c < 0) break;
             const long long p0 = P->demand_path_off[c], np = P->demand_path_off[c + 1] - p0;
-            npv[li] = (unsigned char)np;
-            for (int j = 0; j < np; ++j) {
-                const long long s = slotbase[b] + j, r = p0 + j;
-                slot_path[(size_t)s * kLanes + t] = r;
+            for (int hh = 0; hh < G; ++hh) {
+                const int lane = t * G + hh;
+                const size_t li = (size_t)b * kLanes + lane;
+                lane_demand[li] = c;
+                Dn[li] = (float)(D[c] / scale);
+                Dc[li] = D[c];
+                npv[li] = (unsigned char)np;
+            }
+            for (long long p = 0; p < np; ++p) {
+                const int lane = t * G + (int)(p % G);
+                const long long s = slotbase[b] + p / G, r = p0 + p;
+                slot_path[(size_t)s * kLanes + lane] = r;
                 const long long i0 = P->path_edge_off[r], n = P->path_edge_off[r + 1] - i0;
                 for (long long k = 0; k < n; ++k) {
-                    const size_t at = ((size_t)rowoff[s] + (size_t)k) * kLanes + t;
+                    const size_t at = ((size_t)rowoff[s] + (size_t)k) * kLanes + lane;
                     if (id_bytes == 2) ((uint16_t*)ids.data())[at] = (uint16_t)P->path_edges[i0 + k];
                     else ((int32_t*)ids.data())[at] = P->path_edges[i0 + k];
                 }
@@ -380,14 +396,14 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
 
     // ---------------- persistent grid ----------------
     if (te::iter_smem_bytes(E) > 227 * 1024) {
-        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 19000 edges)", E);
+        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 14500 edges)", E);
         return bail(TE_EUNSUPPORTED);
     }
     int bps = 0, nsm = 0;
     te_status st;
     if ((st = h->cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device), "device query")))
         return bail(st);
-    if ((st = h->cuda(te::iter_occupancy(id_bytes, kmax, E, &bps), "occupancy query"))) return bail(st);
+    if ((st = h->cuda(te::iter_occupancy(id_bytes, kl, G, E, &bps), "occupancy query"))) return bail(st);
     if (bps < 1) { h->err = "iteration kernel does not fit on an SM"; return bail(TE_EUNSUPPORTED); }
     h->grid = nsm * bps;
     std::vector<int> cta_blk(h->grid + 1, nblocks);
@@ -492,6 +508,8 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     L.nrows = nrows;
     L.id_bytes = id_bytes;
     L.kmax = kmax;
+    L.G = G;
+    L.kl = kl;
     L.ids = d_ids;
     L.rowoff = d_rowoff;
     L.slotbase = d_slotbase;

@@ -42,25 +42,30 @@ template <typename IdT>
 __global__ void k_gap_demands(Layout L, const float* x, const float* u, double pscale, double alpha,
                               double scale, const double* Dc, double* acc) {
     const IdT* ids = static_cast<const IdT*>(L.ids);
+    const int DPB = kLanes / L.G;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double pr = 0.0, du = 0.0;
-    if (i < (long long)L.nblocks * kLanes && L.np[i] > 0) {
-        const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
-        const int s0 = L.slotbase[b];
-        const int np = L.np[i];
-        double S = 0.0, pi = INFINITY;
-        for (int j = 0; j < np; ++j) {
-            const size_t sl = (size_t)(s0 + j);
-            S += (double)x[sl * kLanes + lane];
-            double q = 0.0;
-            for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
-                const IdT id = ids[(size_t)r * kLanes + lane];
-                if ((int)id != L.E) q += (double)u[id];
+    if (i < (long long)L.nblocks * DPB) {
+        const int b = (int)(i / DPB), t = (int)(i % DPB);
+        const size_t l0 = (size_t)b * kLanes + t * L.G;
+        const int np = L.np[l0];
+        if (np > 0) {
+            const int s0 = L.slotbase[b];
+            double S = 0.0, pi = INFINITY;
+            for (int p = 0; p < np; ++p) {
+                const int lane = t * L.G + p % L.G;
+                const size_t sl = (size_t)(s0 + p / L.G);
+                S += (double)x[sl * kLanes + lane];
+                double q = 0.0;
+                for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+                    const IdT id = ids[(size_t)r * kLanes + lane];
+                    if ((int)id != L.E) q += (double)u[id];
+                }
+                pi = fmin(pi, q);
             }
-            pi = fmin(pi, q);
+            pr = utility(S * scale, alpha);
+            du = conj_term(Dc[l0], pi * pscale, alpha);
         }
-        pr = utility(S * scale, alpha);
-        du = conj_term(Dc[i], pi * pscale, alpha);
     }
     pr = warp_sum(pr);
     du = warp_sum(du);
@@ -87,8 +92,8 @@ cudaError_t launch_gap_impl(const Layout& L, const float* x, const float* u, dou
                             double scale, const double* Dc, double* acc, cudaStream_t st) {
     // p = beta * u in normalised units; in caller units U' scales by scale^-alpha
     const double pscale = beta * pow(scale, -alpha);
-    const long long lanes = (long long)L.nblocks * kLanes;
-    const unsigned g = (unsigned)((lanes + kThreads - 1) / kThreads);
+    const long long nd = (long long)L.nblocks * (kLanes / L.G);
+    const unsigned g = (unsigned)((nd + kThreads - 1) / kThreads);
     if (L.id_bytes == 2)
         k_gap_demands<uint16_t><<<g, kThreads, 0, st>>>(L, x, u, pscale, alpha, scale, Dc, acc);
     else

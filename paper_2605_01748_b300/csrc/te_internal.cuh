@@ -1,16 +1,20 @@
 // Internal declarations shared by the libte translation units (not installed).
 //
 // Device layout ("sliced" incidence).  Demands are sorted by their vector of
-// path lengths and grouped into blocks of 32, one demand per warp lane.
-// Block b owns flat slots slotbase[b] .. slotbase[b+1]-1; slot j of a block
-// holds path j of each of its 32 demands.  Per flat slot s:
+// path lengths and grouped into blocks of 32/G demands; demand t of a block
+// owns the G adjacent warp lanes t*G .. t*G+G-1 (G = 1, 2 or 4 lanes per
+// demand, so that no lane holds more than 8 paths), and path p of the
+// demand sits on lane t*G + p%G in slot p/G.  Block b owns flat slots
+// slotbase[b] .. slotbase[b+1]-1.  Per flat slot s:
 //   x[s*32 + lane]                      rate of that path (FP32, normalised)
 //   ids[(row)*32 + lane], row in [rowoff[s], rowoff[s+1])
 //                                       edge ids of that path, hop by hop; a
 //                                       shorter path (or a missing one) is
 //                                       padded with the sentinel id E
 // so every warp-wide load of a slot's rate or of one hop of its paths is one
-// contiguous 128 B (rates) or 64 B (16-bit ids) transaction.
+// contiguous 128 B (rates) or 64 B (16-bit ids) transaction.  Per-demand
+// values (demand, path count, multiplier) are stored once per lane, i.e.
+// repeated on the G lanes of a demand.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,7 +25,11 @@ namespace te {
 constexpr int kLanes = 32;
 constexpr int kMaxPaths = 32;     // paths per demand
 constexpr int kMaxHops = 255;     // edges per path
-constexpr int kIterThreads = 512;
+constexpr int kMaxPathsPerLane = 8;
+#ifndef TE_ITER_THREADS
+#define TE_ITER_THREADS 1024
+#endif
+constexpr int kIterThreads = TE_ITER_THREADS;
 constexpr int kIterWarps = kIterThreads / 32;
 constexpr int kTraceWidth = 5;
 
@@ -55,12 +63,14 @@ struct Layout {
     long long nrows;     // padded id rows (32 ids each)
     int id_bytes;        // 2 (uint16) or 4 (int32)
     int kmax;            // largest paths-per-demand
+    int G;               // lanes per demand (1, 2, 4)
+    int kl;              // largest paths per lane (<= 8)
     // device arrays
     const void* ids;             // [nrows*32]
     const unsigned* rowoff;      // [nslots+1]
     const int* slotbase;         // [nblocks+1]
-    const float* Dn;             // [nblocks*32] normalised demand, 0 on padding lanes
-    const unsigned char* np;     // [nblocks*32] paths of each lane
+    const float* Dn;             // [nblocks*32] normalised demand of the lane's demand, 0 on padding
+    const unsigned char* np;     // [nblocks*32] paths of the lane's demand
     const int* lane_demand;      // [nblocks*32] user demand index, -1 on padding
     const long long* slot_path;  // [nslots*32] user path index, -1 on padding
     const float* cap_n;          // [E] normalised capacity
@@ -82,9 +92,9 @@ struct IterArgs {
     Scalars* sc;           // in/out
     double* trace;         // [trace_cap*5] ring
     long long trace_cap;
-    const int* cta_blk;    // [grid+1] block range of each CTA (unused by the dynamic schedule)
+    const int* cta_blk;    // [grid+1] block range of each CTA
     float* lam;            // [nblocks*32] previous multiplier lambda = beta*nu of each demand
-    unsigned* ctr;         // [3] block work counters (triple buffered, zeroed before launch)
+    unsigned* ctr;         // [4] scratch counters (zeroed before launch)
     long long max_iters;
     long long timeout_ns;  // bound on every grid-wide wait
 };
@@ -95,7 +105,7 @@ constexpr int kStatusNumeric = 5;
 
 // Launchers (host side), defined in te_iter.cu / te_proj.cu / te_gap.cu.
 size_t iter_smem_bytes(int E);
-cudaError_t iter_occupancy(int id_bytes, int kmax, int E, int* blocks_per_sm);
+cudaError_t iter_occupancy(int id_bytes, int kl, int G, int E, int* blocks_per_sm);
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st);
 
@@ -104,7 +114,7 @@ cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st);
 // are FP64 so that the violation tests see the loads of the FP32 rates
 // without accumulation error.
 struct ProjScratch {
-    double* S;           // [nblocks*32] demand totals
+    double* S;           // [nblocks*32] demand totals (repeated on the demand's lanes)
     double* loads;       // [E]
     unsigned char* viol; // [E] 1 if L_e > C_e
     int* vidx;           // [E] compact index of violated edges or -1

@@ -134,8 +134,31 @@ __device__ __forceinline__ float slack_root(float A, float H, float logbeta, flo
     return __expf(t);
 }
 
-// Per-demand x-block in scaled form.  Paths with an[j] == 0 are absent.
-// Returns nu with x_r = max(0, m_r + nu an_r), where an_r = 1/n_r.
+// Sums / minimum / all-true over the G adjacent lanes of one demand.  The
+// butterfly gives every lane of the group the same value (the additions are
+// commutative at each level), so decisions taken on it are group-uniform.
+template <int G>
+__device__ __forceinline__ float gsum(float v, unsigned gm) {
+    if (G >= 2) v += __shfl_xor_sync(gm, v, 1);
+    if (G >= 4) v += __shfl_xor_sync(gm, v, 2);
+    return v;
+}
+template <int G>
+__device__ __forceinline__ float gmin(float v, unsigned gm) {
+    if (G >= 2) v = fminf(v, __shfl_xor_sync(gm, v, 1));
+    if (G >= 4) v = fminf(v, __shfl_xor_sync(gm, v, 2));
+    return v;
+}
+template <int G>
+__device__ __forceinline__ int gall(int v, unsigned gm) {
+    if (G >= 2) v &= __shfl_xor_sync(gm, v, 1);
+    if (G >= 4) v &= __shfl_xor_sync(gm, v, 2);
+    return v;
+}
+
+// Per-demand x-block in scaled form, the demand's paths spread over G lanes
+// (this lane holds KL of them; an[j] == 0 marks an absent slot).  Returns
+// nu with x_r = max(0, m_r + nu an_r), where an_r = 1/n_r.
 //
 // S(nu) = sum_r max(0, m_r + nu an_r) is convex, piecewise linear and
 // increasing; the solution is the point where S(nu) meets the target
@@ -148,43 +171,47 @@ __device__ __forceinline__ float slack_root(float A, float H, float logbeta, flo
 // the new point equals the one that produced it (then the point is exact).
 // nu0 is the previous iteration's multiplier of this demand (a warm start:
 // typically the first step is already exact and the second confirms it).
-template <int KMAX>
-__device__ __forceinline__ float solve_nu(const float (&m)[KMAX], const float (&an)[KMAX], float D,
-                                          float inv_beta, float logbeta, float alpha, float nu0) {
+template <int KL, int G>
+__device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an)[KL], float D,
+                                          float inv_beta, float logbeta, float alpha, float nu0, unsigned gm) {
     float nu = nu0;
     if (alpha == 0.f) {
         float S = 0.f;
         #pragma unroll
-        for (int j = 0; j < KMAX; ++j)
+        for (int j = 0; j < KL; ++j)
             if (an[j] > 0.f) S += fmaxf(0.f, fmaf(inv_beta, an[j], m[j]));
+        S = gsum<G>(S, gm);
         if (S <= D) return inv_beta;  // lambda = U'(S) = 1, cap slack
         nu = fminf(nu, inv_beta);
     }
     // log of the nu at which (beta nu)^(-1/alpha) = D
     const float tcap = alpha > 0.f ? -alpha * __logf(D) - logbeta : INFINITY;
-    unsigned prev = 0xffffffffu;
+    unsigned prev = 0u;
+    bool have_prev = false;
     #pragma unroll 1
-    for (int it = 0; it < KMAX + 3; ++it) {
+    for (int it = 0; it < KL * G + 3; ++it) {
         float A = 0.f, H = 0.f;
         unsigned mask = 0u;
         #pragma unroll
-        for (int j = 0; j < KMAX; ++j) {
+        for (int j = 0; j < KL; ++j) {
             if (an[j] > 0.f && fmaf(nu, an[j], m[j]) > 0.f) {
                 A += m[j];
                 H += an[j];
                 mask |= 1u << j;
             }
         }
-        if (mask == prev) break;  // nu is the root of this active set's line
+        A = gsum<G>(A, gm);
+        H = gsum<G>(H, gm);
+        if (have_prev && gall<G>(mask == prev, gm)) break;  // nu is the root of this line
         if (!(H > 0.f)) {
             // nothing active at nu: restart from a single-path bound, where
             // one path alone reaches D, so S(nu) >= D >= T(nu)
             float ub = INFINITY;
             #pragma unroll
-            for (int j = 0; j < KMAX; ++j)
+            for (int j = 0; j < KL; ++j)
                 if (an[j] > 0.f) ub = fminf(ub, (D - m[j]) / an[j]);
-            nu = ub;
-            prev = 0xffffffffu;
+            nu = gmin<G>(ub, gm);
+            have_prev = false;
             continue;
         }
         float nn = (D - A) / H;
@@ -192,9 +219,10 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KMAX], const float (&
             const float tn = __logf(nn);
             if (tn > tcap) nn = slack_root(A, H, logbeta, alpha, tcap, tn, nu);
         }
-        if (it > 0 && prev != 0xffffffffu && !(nn < nu)) break;  // rounding: no further descent
+        if (have_prev && !(nn < nu)) break;  // rounding: no further descent
         nu = nn;
         prev = mask;
+        have_prev = true;
     }
     return nu;
 }
@@ -205,27 +233,37 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// One block of 32 demands (one per lane): gather, x-block, scatter.
-template <typename IdT, int KMAX>
+// One block (32/G demands, G lanes each): gather, x-block, scatter.
+template <typename IdT, int KL, int G>
 __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane, const float* __restrict__ xin,
-                                              float* __restrict__ xout, const float* w_s, float* h_s,
+                                              float* __restrict__ xout, const float* w_s,
+                                              unsigned long long* h_s,
                                               float inv_beta, float logbeta, float beta_f, float alpha,
                                               KSum& ds2, KSum& x2, KSum& ex2) {
     const IdT* __restrict__ ids = static_cast<const IdT*>(a.L.ids);
     const IdT sentinel = (IdT)a.L.E;
-    const int s0 = __ldg(&a.L.slotbase[b]);
-    const int KB = __ldg(&a.L.slotbase[b + 1]) - s0;
+    const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    // block metadata in one coalesced load: slot bases, then row offsets
+    int sb = 0;
+    if (lane < 2) sb = __ldg(&a.L.slotbase[b + lane]);
+    const int s0 = __shfl_sync(0xffffffffu, sb, 0);
+    const int KB = __shfl_sync(0xffffffffu, sb, 1) - s0;
+    unsigned ro = 0u;
+    if (lane <= KB) ro = __ldg(&a.L.rowoff[s0 + lane]);
     const size_t li = (size_t)b * kLanes + lane;
     const float D = __ldg(&a.L.Dn[li]);
     const float lam0 = __ldcg(&a.lam[li]);
-    float xo[KMAX], m[KMAX], an[KMAX];
+    float xo[KL], m[KL], an[KL];
     #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
-        xo[j] = 0.f; m[j] = 0.f; an[j] = 0.f;
+    for (int j = 0; j < KL; ++j) {
+        xo[j] = 0.f;
+        if (j < KB) xo[j] = __ldcg(&xin[(size_t)(s0 + j) * kLanes + lane]);
+    }
+    #pragma unroll
+    for (int j = 0; j < KL; ++j) {
+        m[j] = 0.f; an[j] = 0.f;
         if (j < KB) {
-            const size_t sl = (size_t)(s0 + j);
-            xo[j] = __ldcg(&xin[sl * kLanes + lane]);
-            const unsigned r0 = __ldg(&a.L.rowoff[sl]), r1 = __ldg(&a.L.rowoff[sl + 1]);
+            const unsigned r0 = __shfl_sync(0xffffffffu, ro, j), r1 = __shfl_sync(0xffffffffu, ro, j + 1);
             float q = 0.f;
             int n = 0;
             #pragma unroll 4
@@ -242,12 +280,12 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
     }
     float nu = 0.f;
     if (D > 0.f) {
-        nu = solve_nu<KMAX>(m, an, D, inv_beta, logbeta, alpha, lam0 * inv_beta);
+        nu = solve_nu<KL, G>(m, an, D, inv_beta, logbeta, alpha, lam0 * inv_beta, gm);
         __stcg(&a.lam[li], nu * beta_f);
     }
     float bd = 0.f, bx = 0.f, be = 0.f;
     #pragma unroll
-    for (int j = 0; j < KMAX; ++j) {
+    for (int j = 0; j < KL; ++j) {
         if (j < KB) {
             const size_t sl = (size_t)(s0 + j);
             const float xn = an[j] > 0.f ? fmaxf(0.f, fmaf(nu, an[j], m[j])) : 0.f;
@@ -255,13 +293,14 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
             const float dx = xn - xo[j];
             bd = fmaf(dx, dx, bd);
             bx = fmaf(xn, xn, bx);
+            const unsigned r0 = __shfl_sync(0xffffffffu, ro, j), r1 = __shfl_sync(0xffffffffu, ro, j + 1);
             if (xn != 0.f) {
                 be = fmaf(xn * xn, __frcp_rn(an[j]), be);
-                const unsigned r0 = __ldg(&a.L.rowoff[sl]), r1 = __ldg(&a.L.rowoff[sl + 1]);
+                const unsigned long long fx = __float2ull_rn(xn * 0x1p32f);
                 #pragma unroll 4
                 for (unsigned r = r0; r < r1; ++r) {
                     const IdT id = __ldg(&ids[(size_t)r * kLanes + lane]);
-                    if (id != sentinel) atomicAdd(&h_s[id], xn);
+                    if (id != sentinel) atomicAdd(&h_s[id], fx);
                 }
             }
         }
@@ -271,36 +310,34 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
     ex2.add(be);
 }
 
-// Issues the L2 prefetch of block b's incidence rows and rates.
-template <typename IdT>
-__device__ __forceinline__ void prefetch_block(const IterArgs& a, int b, const float* xin) {
-    const int s0 = __ldg(&a.L.slotbase[b]), s1 = __ldg(&a.L.slotbase[b + 1]);
-    const unsigned r0 = __ldg(&a.L.rowoff[s0]), r1 = __ldg(&a.L.rowoff[s1]);
-    const IdT* ids = static_cast<const IdT*>(a.L.ids);
-    if (r1 > r0) prefetch_l2(ids + (size_t)r0 * kLanes, (unsigned)((r1 - r0) * kLanes * sizeof(IdT)));
-    if (s1 > s0) prefetch_l2(xin + (size_t)s0 * kLanes, (unsigned)((s1 - s0) * kLanes * sizeof(float)));
-}
+// Distance, in blocks, of the rolling L2 prefetch window ahead of the
+// blocks being processed by a CTA.
+constexpr int kPrefetchAhead = 2 * kIterWarps;
 
-template <typename IdT, int KMAX>
+template <typename IdT, int KL, int G>
 __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
-    extern __shared__ __align__(16) float smem[];
+    extern __shared__ __align__(16) unsigned long long smem[];
     const int E = a.L.E;
-    float* w_s = smem;            // [E+1] gather weights u_e + d_e; w_s[E] = 0 (sentinel)
-    float* h_s = w_s + (E + 1);   // [E+1] this CTA's edge-load histogram
-    float* u_s = h_s + (E + 1);   // [E]   scaled prices
+    // this CTA's edge-load histogram in 64-bit fixed point (2^-32 units):
+    // integer atomics on shared memory are native, float ones are not
+    unsigned long long* h_s = smem;                  // [E+1]
+    float* w_s = reinterpret_cast<float*>(h_s + (E + 1));  // [E+1] gather weights u_e + d_e; w_s[E] = 0
+    float* u_s = w_s + (E + 1);                      // [E]   scaled prices
     __shared__ double red[kIterWarps];
     __shared__ double s_fin[4];
+    __shared__ int s_next;  // next block of this CTA's range (relative)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int G = gridDim.x;
-    const int nblocks = a.L.nblocks;
+    const int NG = gridDim.x;  // CTAs in the grid
+    const int b_lo = a.cta_blk[blockIdx.x], b_hi = a.cta_blk[blockIdx.x + 1];
+    if (tid == 0) s_next = 0;
 
     for (int e = tid; e < E; e += kIterThreads) {
         u_s[e] = a.u[e];
         w_s[e] = a.w[e];
-        h_s[e] = 0.f;
+        h_s[e] = 0ull;
     }
-    if (tid == 0) { w_s[E] = 0.f; h_s[E] = 0.f; }
+    if (tid == 0) { w_s[E] = 0.f; h_s[E] = 0ull; }
     Scalars sc = *a.sc;
     int xbuf = sc.xbuf;
     sc.converged = 0;
@@ -321,43 +358,70 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         KSum ds2, x2, ex2;
 
         // ---------------- phase A: per-demand rate updates ----------------
-        // blocks are handed out grid-wide, one at a time per warp; the next
-        // block's rows and rates are prefetched into L2 while this one runs
-        unsigned* ctr = a.ctr + (it % 3);
-        int b = 0;
-        if (lane == 0) b = (int)atomicAdd(ctr, 1u);
-        b = __shfl_sync(0xffffffffu, b, 0);
-        while (b < nblocks) {
-            int bn = 0;
-            if (lane == 0) {
-                bn = (int)atomicAdd(ctr, 1u);
-                if (bn < nblocks) prefetch_block<IdT>(a, bn, xin);
+        // each CTA owns a contiguous range of blocks (balanced by their
+        // rows); its warps take blocks one at a time from a shared counter.
+        // The CTA's rows and rates are contiguous in memory, so the warp that
+        // takes block b also prefetches block b + kPrefetchAhead into L2 (its
+        // bounds are loaded when b is taken and the bulk prefetch is issued
+        // after b is processed, so no warp waits on them).
+        {
+            const IdT* ids = static_cast<const IdT*>(a.L.ids);
+            if (it == 0 && warp == 0) {
+                // warm the start of the window
+                const int pe = min(b_hi, b_lo + kPrefetchAhead);
+                if (lane == 0 && pe > b_lo) {
+                    const int s0 = __ldg(&a.L.slotbase[b_lo]), s1 = __ldg(&a.L.slotbase[pe]);
+                    const unsigned r0 = __ldg(&a.L.rowoff[s0]), r1 = __ldg(&a.L.rowoff[s1]);
+                    if (r1 > r0) prefetch_l2(ids + (size_t)r0 * kLanes, (unsigned)((r1 - r0) * kLanes * sizeof(IdT)));
+                    if (s1 > s0) prefetch_l2(xin + (size_t)s0 * kLanes, (unsigned)((s1 - s0) * kLanes * sizeof(float)));
+                }
             }
-            bn = __shfl_sync(0xffffffffu, bn, 0);
-            process_block<IdT, KMAX>(a, b, lane, xin, xout, w_s, h_s, inv_beta, logbeta, beta_f, alpha, ds2, x2,
-                                     ex2);
-            b = bn;
+            while (true) {
+                int b = 0;
+                if (lane == 0) b = atomicAdd(&s_next, 1);
+                b = __shfl_sync(0xffffffffu, b, 0) + b_lo;
+                if (b >= b_hi) break;
+                // bounds of the block kPrefetchAhead ahead (lanes 0-1 slot bases)
+                const int bp = b + kPrefetchAhead;
+                int psb = 0;
+                if (bp < b_hi && lane < 2) psb = __ldg(&a.L.slotbase[bp + lane]);
+                process_block<IdT, KL, G>(a, b, lane, xin, xout, w_s, h_s, inv_beta, logbeta, beta_f, alpha, ds2,
+                                          x2, ex2);
+                if (bp < b_hi) {
+                    const int ps0 = __shfl_sync(0xffffffffu, psb, 0), ps1 = __shfl_sync(0xffffffffu, psb, 1);
+                    unsigned pro = 0u;
+                    if (lane < 2) pro = __ldg(&a.L.rowoff[lane == 0 ? ps0 : ps1]);
+                    const unsigned pr0 = __shfl_sync(0xffffffffu, pro, 0), pr1 = __shfl_sync(0xffffffffu, pro, 1);
+                    if (lane == 0) {
+                        if (pr1 > pr0)
+                            prefetch_l2(ids + (size_t)pr0 * kLanes, (unsigned)((pr1 - pr0) * kLanes * sizeof(IdT)));
+                        if (ps1 > ps0)
+                            prefetch_l2(xin + (size_t)ps0 * kLanes, (unsigned)((ps1 - ps0) * kLanes * sizeof(float)));
+                    }
+                }
+            }
         }
         __syncthreads();
+        if (tid == 0) s_next = 0;
         // flush this CTA's loads into the global accumulator of this iteration
         float* Lg = a.loads + (size_t)(it % 3) * E;
         for (int e = tid; e < E; e += kIterThreads) {
-            const float v = h_s[e];
-            if (v != 0.f) atomicAdd(&Lg[e], v);
-            h_s[e] = 0.f;
+            const unsigned long long v = h_s[e];
+            if (v != 0ull) atomicAdd(&Lg[e], (float)((double)v * 0x1p-32));
+            h_s[e] = 0ull;
         }
         {
             const double v0 = block_sum((double)ds2.s, red);
             const double v1 = block_sum((double)x2.s, red);
             const double v2 = block_sum((double)ex2.s, red);
             if (tid == 0) {
-                double* p = a.part + ((size_t)(it & 1) * G + blockIdx.x) * 4;
+                double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * 4;
                 __stcg(&p[0], v0);
                 __stcg(&p[1], v1);
                 __stcg(&p[2], v2);
             }
         }
-        if (!grid_sync(a.barrier, (unsigned)((it + 1) * G), a.status, a.timeout_ns,
+        if (!grid_sync(a.barrier, (unsigned)((it + 1) * NG), a.status, a.timeout_ns,
                        (int)blockIdx.x != a.o.withhold_cta)) {
             break;
         }
@@ -382,8 +446,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         const double r2s = block_sum((double)rp, red);
         if (tid < 32) {
             double v0 = 0.0, v1 = 0.0, v2 = 0.0;
-            const double* p = a.part + (size_t)(it & 1) * G * 4;
-            for (int c = lane; c < G; c += 32) {
+            const double* p = a.part + (size_t)(it & 1) * NG * 4;
+            for (int c = lane; c < NG; c += 32) {
                 v0 += __ldcg(&p[c * 4 + 0]);
                 v1 += __ldcg(&p[c * 4 + 1]);
                 v2 += __ldcg(&p[c * 4 + 2]);
@@ -448,11 +512,9 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 double* t = a.trace + (size_t)((sc.iter_total - 1) % a.trace_cap) * kTraceWidth;
                 t[0] = r_res; t[1] = s_res; t[2] = sc.beta; t[3] = sc.alpha; t[4] = (double)event;
             }
-            // the load buffer and the work counter used two iterations from
-            // now must start at zero
+            // the load buffer used two iterations from now must start at zero
             float* Lz = a.loads + (size_t)((it + 2) % 3) * E;
             for (int e = tid; e < E; e += kIterThreads) __stcg(&Lz[e], 0.f);
-            if (tid == 0) __stcg(&a.ctr[(it + 2) % 3], 0u);
         }
         __syncthreads();
         if (stop) {
@@ -475,36 +537,38 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
 }
 
 // Initial rates of Algorithm 1: x_r = D_c / |P_c| on every path of demand c
-// (normalised units), 0 on padding slots.  One thread per (block, lane).
+// (normalised units), 0 on padding slots.  One thread per lane; path p of a
+// demand sits on lane t*G + p%G in slot p/G.
 __global__ void k_init_x(Layout L, float* x) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
     const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int hh = lane % L.G;
     const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
     const int np = L.np[i];
     const float v = np > 0 ? L.Dn[i] / (float)np : 0.f;
-    for (int j = 0; j < KB; ++j) x[(size_t)(s0 + j) * kLanes + lane] = j < np ? v : 0.f;
+    for (int j = 0; j < KB; ++j) x[(size_t)(s0 + j) * kLanes + lane] = j * L.G + hh < np ? v : 0.f;
 }
 
-template <typename IdT, int KMAX>
+template <typename IdT, int KL, int G>
 cudaError_t launch_iter_t(const IterArgs& a, int grid, cudaStream_t st) {
     const size_t smem = iter_smem_bytes(a.L.E);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<IdT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(k_iter<IdT, KL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
     IterArgs args = a;
     void* params[] = {&args};
-    return cudaLaunchCooperativeKernel((const void*)k_iter<IdT, KMAX>, dim3(grid), dim3(kIterThreads), params,
+    return cudaLaunchCooperativeKernel((const void*)k_iter<IdT, KL, G>, dim3(grid), dim3(kIterThreads), params,
                                        smem, st);
 }
 
-template <typename IdT, int KMAX>
+template <typename IdT, int KL, int G>
 cudaError_t occupancy_t(int E, int* blocks) {
     const size_t smem = iter_smem_bytes(E);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<IdT, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(k_iter<IdT, KL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<IdT, KMAX>, kIterThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<IdT, KL, G>, kIterThreads, smem);
 }
 
 }  // namespace
@@ -512,31 +576,32 @@ cudaError_t occupancy_t(int E, int* blocks) {
 
 namespace te {
 
-size_t iter_smem_bytes(int E) { return (size_t)(3 * (size_t)E + 2) * sizeof(float); }
+size_t iter_smem_bytes(int E) {
+    return (size_t)(E + 1) * sizeof(unsigned long long) + (size_t)(2 * (size_t)E + 1) * sizeof(float);
+}
 
-#define TE_DISPATCH(ID_BYTES, KMAX, CALL)                                        \
+// instantiations: (paths per lane, lanes per demand) = (4,1), (8,1), (8,2), (8,4)
+#define TE_DISPATCH(ID_BYTES, KL, G, CALL)                                       \
     do {                                                                         \
         if ((ID_BYTES) == 2) {                                                   \
-            if ((KMAX) <= 4) return CALL(uint16_t, 4);                           \
-            if ((KMAX) <= 8) return CALL(uint16_t, 8);                           \
-            if ((KMAX) <= 16) return CALL(uint16_t, 16);                         \
-            return CALL(uint16_t, 32);                                           \
+            if ((G) == 1) return (KL) <= 4 ? CALL(uint16_t, 4, 1) : CALL(uint16_t, 8, 1); \
+            if ((G) == 2) return CALL(uint16_t, 8, 2);                           \
+            return CALL(uint16_t, 8, 4);                                         \
         }                                                                        \
-        if ((KMAX) <= 4) return CALL(int32_t, 4);                                \
-        if ((KMAX) <= 8) return CALL(int32_t, 8);                                \
-        if ((KMAX) <= 16) return CALL(int32_t, 16);                              \
-        return CALL(int32_t, 32);                                                \
+        if ((G) == 1) return (KL) <= 4 ? CALL(int32_t, 4, 1) : CALL(int32_t, 8, 1); \
+        if ((G) == 2) return CALL(int32_t, 8, 2);                                \
+        return CALL(int32_t, 8, 4);                                              \
     } while (0)
 
-cudaError_t iter_occupancy(int id_bytes, int kmax, int E, int* blocks_per_sm) {
-#define TE_OCC(T, K) occupancy_t<T, K>(E, blocks_per_sm)
-    TE_DISPATCH(id_bytes, kmax, TE_OCC);
+cudaError_t iter_occupancy(int id_bytes, int kl, int G, int E, int* blocks_per_sm) {
+#define TE_OCC(T, K, GG) occupancy_t<T, K, GG>(E, blocks_per_sm)
+    TE_DISPATCH(id_bytes, kl, G, TE_OCC);
 #undef TE_OCC
 }
 
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
-#define TE_LAUNCH(T, K) launch_iter_t<T, K>(a, grid, st)
-    TE_DISPATCH(a.L.id_bytes, a.L.kmax, TE_LAUNCH);
+#define TE_LAUNCH(T, K, GG) launch_iter_t<T, K, GG>(a, grid, st)
+    TE_DISPATCH(a.L.id_bytes, a.L.kl, a.L.G, TE_LAUNCH);
 #undef TE_LAUNCH
 }
 

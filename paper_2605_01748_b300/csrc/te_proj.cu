@@ -41,20 +41,25 @@ __device__ __forceinline__ const IdT* ids_of(const Layout& L) {
     return static_cast<const IdT*>(L.ids);
 }
 
-// x <- max(x, 0) on every slot; S[lane] = sum of the lane's rates.
+// x <- max(x, 0) on every slot; S = the demand's total, written to each of
+// its G lanes.  One thread per demand.
 __global__ void k_clamp_sum(Layout L, float* x, double* S) {
+    const int DPB = kLanes / L.G;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)L.nblocks * kLanes) return;
-    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    if (i >= (long long)L.nblocks * DPB) return;
+    const int b = (int)(i / DPB), t = (int)(i % DPB);
     const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
     double acc = 0.0;
-    for (int j = 0; j < KB; ++j) {
-        float* p = &x[(size_t)(s0 + j) * kLanes + lane];
-        const float v = fmaxf(*p, 0.f);
-        *p = v;
-        acc += (double)v;
+    for (int hh = 0; hh < L.G; ++hh) {
+        const int lane = t * L.G + hh;
+        for (int j = 0; j < KB; ++j) {
+            float* p = &x[(size_t)(s0 + j) * kLanes + lane];
+            const float v = fmaxf(*p, 0.f);
+            *p = v;
+            acc += (double)v;
+        }
     }
-    S[i] = acc;
+    for (int hh = 0; hh < L.G; ++hh) S[(size_t)b * kLanes + t * L.G + hh] = acc;
 }
 
 // L_e = sum of rates over the paths through e (loads must be zeroed).
@@ -114,28 +119,31 @@ __global__ void k_count_viol(Layout L, const unsigned char* viol, unsigned char*
 }
 
 // Demand step: trims S_c - D_c from the demand's paths in descending C_p,
-// ties to the lower path (slot) index.
+// ties to the lower path index.  One thread per demand; path p of the demand
+// is on lane t*G + p%G, slot p/G.
 __global__ void k_demand_trim(Layout L, float* x, const double* S, const unsigned char* Cp) {
+    const int DPB = kLanes / L.G;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)L.nblocks * kLanes) return;
-    const double D = (double)L.Dn[i];
-    double Ec = S[i] - D;
+    if (i >= (long long)L.nblocks * DPB) return;
+    const int b = (int)(i / DPB), t = (int)(i % DPB);
+    const size_t l0 = (size_t)b * kLanes + t * L.G;
+    const double D = (double)L.Dn[l0];
+    double Ec = S[l0] - D;
     if (!(Ec > 0.0) || D <= 0.0) return;
-    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
     const int s0 = L.slotbase[b];
-    const int np = L.np[i];
+    const int np = L.np[l0];
     unsigned taken = 0u;  // np <= 32
     for (int k = 0; k < np && Ec > 0.0; ++k) {
         int best = -1, bc = -1;
-        for (int j = 0; j < np; ++j) {
-            if (taken & (1u << j)) continue;
-            const int c = Cp[(size_t)(s0 + j) * kLanes + lane];
-            if (c > bc) { bc = c; best = j; }
+        for (int p = 0; p < np; ++p) {
+            if (taken & (1u << p)) continue;
+            const int c = Cp[(size_t)(s0 + p / L.G) * kLanes + t * L.G + p % L.G];
+            if (c > bc) { bc = c; best = p; }
         }
         taken |= 1u << best;
-        float* p = &x[(size_t)(s0 + best) * kLanes + lane];
-        const double d = fmin(Ec, (double)*p);
-        *p = d >= (double)*p ? 0.f : __double2float_rd((double)*p - d);
+        float* q = &x[(size_t)(s0 + best / L.G) * kLanes + t * L.G + best % L.G];
+        const double d = fmin(Ec, (double)*q);
+        *q = d >= (double)*q ? 0.f : __double2float_rd((double)*q - d);
         Ec -= d;
     }
 }
@@ -279,14 +287,15 @@ cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch&
     const unsigned gl = grid_for(lanes, kThreads);
     const unsigned ge = grid_for(L.E, kThreads);
     cudaError_t err;
+    const unsigned gd = grid_for((long long)L.nblocks * (kLanes / L.G), kThreads);
     for (int round = 0; round < 2; ++round) {
-        k_clamp_sum<<<gl, kThreads, 0, st>>>(L, x, s.S);
+        k_clamp_sum<<<gd, kThreads, 0, st>>>(L, x, s.S);
         if ((err = cudaMemsetAsync(s.loads, 0, sizeof(double) * (size_t)L.E, st)) != cudaSuccess) return err;
         if ((err = cudaMemsetAsync(s.nviol, 0, sizeof(int), st)) != cudaSuccess) return err;
         k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
         k_viol<<<ge, kThreads, 0, st>>>(L, s.loads, s.viol, s.vidx, s.nviol, s.rem, s.prefix);
         k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, s.viol, s.Cp);
-        if (round == 0) k_demand_trim<<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp);
+        if (round == 0) k_demand_trim<<<gd, kThreads, 0, st>>>(L, x, s.S, s.Cp);
     }
     // capacity step: radix select of each violated edge's threshold path
     unsigned char* done = s.viol;  // reuse: per violated-edge flags (E bytes >= nviol)

@@ -20,7 +20,9 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libte.so")
+# TE_LIBRARY may name another build of the same library (e.g. a variant
+# compiled with different launch parameters)
+LIB_PATH = os.environ.get("TE_LIBRARY") or os.path.join(_HERE, "libte.so")
 
 TE_OK, TE_EINVAL, TE_ENOMEM, TE_ECUDA, TE_ETIMEOUT, TE_ENUMERIC, TE_ENOTCONVERGED, TE_EUNSUPPORTED = range(8)
 STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "TE_ETIMEOUT",

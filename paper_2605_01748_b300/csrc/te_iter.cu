@@ -187,7 +187,7 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
     // log of the nu at which (beta nu)^(-1/alpha) = D
     const float tcap = alpha > 0.f ? -alpha * __logf(D) - logbeta : INFINITY;
     unsigned prev = 0u;
-    bool have_prev = false;
+    bool descending = false;  // nu is a root computed from a supporting line (an upper bound)
     #pragma unroll 1
     for (int it = 0; it < KL * G + 3; ++it) {
         float A = 0.f, H = 0.f;
@@ -202,16 +202,19 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
         }
         A = gsum<G>(A, gm);
         H = gsum<G>(H, gm);
-        if (have_prev && gall<G>(mask == prev, gm)) break;  // nu is the root of this line
+        if (descending && gall<G>(mask == prev, gm)) break;  // nu is the root of this line
         if (!(H > 0.f)) {
-            // nothing active at nu: restart from a single-path bound, where
-            // one path alone reaches D, so S(nu) >= D >= T(nu)
+            // nothing active at nu.  While descending this only happens when
+            // the root lies on a path's breakpoint and rounding switched the
+            // path off: its rate there is zero to rounding, so stop.  At the
+            // start, restart from a single-path bound instead (one path
+            // alone reaches D there, so S(nu) >= D >= T(nu)).
+            if (descending) break;
             float ub = INFINITY;
             #pragma unroll
             for (int j = 0; j < KL; ++j)
                 if (an[j] > 0.f) ub = fminf(ub, (D - m[j]) / an[j]);
             nu = gmin<G>(ub, gm);
-            have_prev = false;
             continue;
         }
         float nn = (D - A) / H;
@@ -219,10 +222,10 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
             const float tn = __logf(nn);
             if (tn > tcap) nn = slack_root(A, H, logbeta, alpha, tcap, tn, nu);
         }
-        if (have_prev && !(nn < nu)) break;  // rounding: no further descent
+        if (descending && !(nn < nu)) break;  // rounding: no further descent
         nu = nn;
         prev = mask;
-        have_prev = true;
+        descending = true;
     }
     return nu;
 }

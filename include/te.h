@@ -200,6 +200,36 @@ typedef struct {
 } te_layout_info;
 te_status te_layout(const te_handle* h, te_layout_info* info);
 
+/* The duality gap of te_gap for a caller-supplied allocation, computed
+ * without allocating any memory (the paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc where they need the
+ * gap, such as code inside a memory pool that owns all device memory or a
+ * control loop whose allocations are frozen after start-up).
+ * Every pointer is a device pointer of the current device, owned by the
+ * caller: the instance in the CSR form of te_paths (demand_path_off
+ * [n_demands+1], path_edge_off [n_paths+1], path_edges [nnz]), demands
+ * [n_demands] and capacities [n_edges] (FP64, caller units), a feasible
+ * allocation x [n_paths] (FP32, e.g. from te_allocation with project = 1),
+ * edge prices [n_edges] (FP64, e.g. from te_prices) and the fairness level
+ * alpha >= 0; out [3] receives {gap, primal, dual} in FP64 as te_gap reports
+ * them.  The work is queued on cuda_stream (NULL: default stream) and the
+ * call returns without synchronising.
+ * Working memory is one static device array of 16384 slots of two doubles
+ * (256 KB, held on every device that loads the library until exit), so
+ * ceil(n_demands/256) + ceil(n_edges/256) must not exceed 16384 (about 4.19
+ * million demands); larger inputs return TE_EUNSUPPORTED before any work is
+ * queued.  Nothing in that array has to start at zero.  All calls on a
+ * device share it: calls that overlap on the GPU race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Errors: TE_EINVAL (null
+ * pointer, bad size, alpha < 0), TE_EUNSUPPORTED (too large), TE_ECUDA. */
+te_status te_gap_noalloc(int32_t n_edges, int32_t n_demands, int64_t n_paths, int64_t nnz,
+                         const int64_t* demand_path_off, const int64_t* path_edge_off,
+                         const int32_t* path_edges, const double* demands, const double* capacities,
+                         const float* x, const double* prices, double alpha, double* out,
+                         void* cuda_stream);
+
 /* Releases every resource of the handle.  NULL is ignored. */
 void te_destroy(te_handle* h);
 

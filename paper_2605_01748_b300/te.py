@@ -30,7 +30,7 @@ STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "T
 
 EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_gap", "te_prices",
             "te_set_warm_start", "te_set_demands", "te_reset", "te_trace", "te_layout", "te_destroy",
-            "te_last_error")
+            "te_last_error", "te_gap_noalloc")
 
 
 class TEError(RuntimeError):
@@ -114,6 +114,9 @@ def _load() -> ctypes.CDLL:
     lib.te_destroy.argtypes = [H]
     lib.te_last_error.restype = ctypes.c_char_p
     lib.te_last_error.argtypes = [H]
+    lib.te_gap_noalloc.restype = ctypes.c_int
+    lib.te_gap_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                   P, P, P, P, P, P, P, ctypes.c_double, P, P]
     return lib
 
 
@@ -237,6 +240,33 @@ def te_layout(h) -> dict:
     info = te_layout_info()
     _check(_lib.te_layout(h, ctypes.byref(info)), h)
     return info.as_dict()
+
+
+def te_gap_noalloc(demand_path_off, path_edge_off, path_edges, demands, capacities, x, prices, alpha: float,
+                   out, stream=None) -> None:
+    """Duality gap without any allocation (see te.h): every argument is a
+    torch CUDA tensor the caller owns (int64, int64, int32, float64,
+    float64, float32, float64); out is a float64 CUDA tensor of 3 entries
+    that receives {gap, primal, dual}.  Queued on `stream` (a torch stream,
+    default: the current one); nothing is synchronised here.  For callers
+    that cannot allocate device memory where they need the gap."""
+    for name, t in (("demand_path_off", demand_path_off), ("path_edge_off", path_edge_off),
+                    ("path_edges", path_edges), ("demands", demands), ("capacities", capacities),
+                    ("x", x), ("prices", prices), ("out", out)):
+        if not _is_device(t):
+            raise TEError(TE_EINVAL, f"te_gap_noalloc: {name} must be a device tensor")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    st = _lib.te_gap_noalloc(int(capacities.shape[0]), int(demands.shape[0]), int(x.shape[0]),
+                             int(path_edges.shape[0]), _ptr(demand_path_off), _ptr(path_edge_off),
+                             _ptr(path_edges), _ptr(demands), _ptr(capacities), _ptr(x), _ptr(prices),
+                             float(alpha), _ptr(out), int(getattr(stream, "cuda_stream", stream)))
+    if st == TE_EUNSUPPORTED:
+        raise TEError(st, "te_gap_noalloc: ceil(n_demands/256) + ceil(n_edges/256) exceeds the 16384 "
+                          "slots of its static scratch (about 4.19 million demands)")
+    if st != TE_OK:
+        raise TEError(st, "te_gap_noalloc failed")
 
 
 def te_destroy(h) -> None:

@@ -20,7 +20,7 @@ namespace {
 thread_local std::string g_create_error;
 
 constexpr long long kTraceCap = 1 << 16;
-constexpr long long kItersPerLaunch = 1LL << 24;  // keeps the barrier counter below 2^32
+constexpr long long kItersPerLaunch = 1LL << 22;  // two barriers per iteration: counter below 2^32
 
 // p_out[e] = pscale * u[e]
 __global__ void k_prices(int E, const float* u, double pscale, double* p) {
@@ -34,13 +34,13 @@ __global__ void k_check_demands(int K, const double* D, int* bad) {
     if (c < K && !(D[c] > 0.0 && D[c] < INFINITY)) atomicOr(bad, 1);
 }
 
-// new demands into lane order: normalised FP32 for the iteration, caller
-// units FP64 for the gap
-__global__ void k_set_demands(long long lanes, const int* lane_demand, const double* D, double inv_scale,
-                              float* Dn, double* Dc) {
+// new demands into demand-slot order: normalised FP32 for the iteration,
+// caller units FP64 for the gap
+__global__ void k_set_demands(long long nd, const int* demand_of, const double* D, double inv_scale, float* Dn,
+                              double* Dc) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= lanes) return;
-    const int c = lane_demand[i];
+    if (i >= nd) return;
+    const int c = demand_of[i];
     if (c < 0) return;
     Dn[i] = (float)(D[c] * inv_scale);
     Dc[i] = D[c];
@@ -71,22 +71,23 @@ struct te_handle {
     float* x = nullptr;       // [2][nslots*32]
     float* u = nullptr;       // [E]
     float* w = nullptr;       // [E]
-    float* loads = nullptr;   // [3E]
+    float* u_next = nullptr;  // [E]
+    float* w_next = nullptr;  // [E]
+    float* loads = nullptr;   // [2E]
     double* part = nullptr;   // [2*grid*4]
     unsigned* barrier = nullptr;
     int* status = nullptr;
     te::Scalars* sc = nullptr;
     double* trace = nullptr;  // [kTraceCap*5]
     int* cta_blk = nullptr;   // [grid+1]
-    double* Dc = nullptr;     // [nblocks*32] caller-unit demands
+    double* Dc = nullptr;     // [nblocks*dpb] caller-unit demands
     float* xtmp = nullptr;    // [nslots*32]
     float* user = nullptr;    // [P]
     double* gacc = nullptr;   // [3]
     double* pbuf = nullptr;   // [E]
     double* dstage = nullptr; // [K] staging of new demands
     int* flag = nullptr;      // [1]
-    float* lam = nullptr;     // [nblocks*32] warm-start multipliers
-    unsigned* ctr = nullptr;  // [3] work counters
+    float* lam = nullptr;     // [nblocks*dpb] warm-start multipliers
     float* Dn = nullptr;      // mutable view of L.Dn
     long long launches = 0;   // kernels launched through this handle
     te::ProjScratch ps{};
@@ -299,7 +300,8 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     }
     std::sort(order.begin(), order.end());
     // lanes per demand: no lane holds more than kMaxPathsPerLane paths
-    const int G = kmax <= te::kMaxPathsPerLane ? 1 : (kmax <= 2 * te::kMaxPathsPerLane ? 2 : 4);
+    int G = 1;
+    while (G * te::kMaxPathsPerLane < kmax) G *= 2;
     const int DPB = kLanes / G;  // demands per block
     const int kl = (kmax + G - 1) / G;
     const int nblocks = (K + DPB - 1) / DPB;
@@ -324,8 +326,12 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     }
     const long long nslots = slotbase[nblocks];
     std::vector<unsigned> rowoff(nslots + 1, 0);
+    std::vector<te::BlockMeta> blkmeta(nblocks);
+    int max_block_rows = 0;
     for (int b = 0; b < nblocks; ++b) {
-        for (int j = 0; j < slotbase[b + 1] - slotbase[b]; ++j) {
+        const int kb = slotbase[b + 1] - slotbase[b];
+        unsigned counts = 0;
+        for (int j = 0; j < kb; ++j) {
             long long H = 0;
             for (int t = 0; t < DPB; ++t) {
                 const int c = demand_at(b, t);
@@ -340,36 +346,41 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
             const long long next = (long long)rowoff[s] + H;
             if (next > 0xffffffffLL) { h->err = "instance too large for the 32-bit row index"; return bail(TE_EUNSUPPORTED); }
             rowoff[s + 1] = (unsigned)next;
+            counts |= (unsigned)H << (8 * j);
         }
+        blkmeta[b].s0 = (unsigned)slotbase[b];
+        blkmeta[b].row0 = rowoff[slotbase[b]];
+        blkmeta[b].counts = counts;
+        blkmeta[b].kb = (unsigned)kb;
+        max_block_rows = std::max<int>(max_block_rows, (int)(rowoff[slotbase[b + 1]] - rowoff[slotbase[b]]));
     }
     const long long nrows = rowoff[nslots];
-    const int id_bytes = (E + 1 <= 65535) ? 2 : 4;
+    if (E + 1 > 65535) {
+        h->err = fmt("n_edges = %lld: the iteration kernel takes 16-bit edge ids (at most 65534 edges)", E);
+        return bail(TE_EUNSUPPORTED);
+    }
+    const int id_bytes = 2;
+    const size_t ND = (size_t)nblocks * DPB;  // demand slots
     std::vector<unsigned char> ids((size_t)nrows * kLanes * id_bytes);
     std::vector<long long> slot_path((size_t)nslots * kLanes, -1);
-    std::vector<int> lane_demand((size_t)nblocks * kLanes, -1);
-    std::vector<float> Dn((size_t)nblocks * kLanes, 0.f);
-    std::vector<double> Dc((size_t)nblocks * kLanes, 0.0);
-    std::vector<unsigned char> npv((size_t)nblocks * kLanes, 0);
-    if (id_bytes == 2) {
+    std::vector<int> demand_of(ND, -1);
+    std::vector<float> Dn(ND, 0.f);
+    std::vector<double> Dc(ND, 0.0);
+    std::vector<unsigned char> npv(ND, 0);
+    {
         uint16_t* q = (uint16_t*)ids.data();
         std::fill(q, q + (size_t)nrows * kLanes, (uint16_t)E);
-    } else {
-        int32_t* q = (int32_t*)ids.data();
-        std::fill(q, q + (size_t)nrows * kLanes, (int32_t)E);
     }
     for (int b = 0; b < nblocks; ++b) {
         for (int t = 0; t < DPB; ++t) {
             const int c = demand_at(b, t);
             if (c < 0) break;
             const long long p0 = P->demand_path_off[c], np = P->demand_path_off[c + 1] - p0;
-            for (int hh = 0; hh < G; ++hh) {
-                const int lane = t * G + hh;
-                const size_t li = (size_t)b * kLanes + lane;
-                lane_demand[li] = c;
-                Dn[li] = (float)(D[c] / scale);
-                Dc[li] = D[c];
-                npv[li] = (unsigned char)np;
-            }
+            const size_t di = (size_t)b * DPB + t;
+            demand_of[di] = c;
+            Dn[di] = (float)(D[c] / scale);
+            Dc[di] = D[c];
+            npv[di] = (unsigned char)np;
             for (long long p = 0; p < np; ++p) {
                 const int lane = t * G + (int)(p % G);
                 const long long s = slotbase[b] + p / G, r = p0 + p;
@@ -377,8 +388,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
                 const long long i0 = P->path_edge_off[r], n = P->path_edge_off[r + 1] - i0;
                 for (long long k = 0; k < n; ++k) {
                     const size_t at = ((size_t)rowoff[s] + (size_t)k) * kLanes + lane;
-                    if (id_bytes == 2) ((uint16_t*)ids.data())[at] = (uint16_t)P->path_edges[i0 + k];
-                    else ((int32_t*)ids.data())[at] = P->path_edges[i0 + k];
+                    ((uint16_t*)ids.data())[at] = (uint16_t)P->path_edges[i0 + k];
                 }
             }
         }
@@ -395,15 +405,15 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     }
 
     // ---------------- persistent grid ----------------
-    if (te::iter_smem_bytes(E) > 227 * 1024) {
-        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 14500 edges)", E);
-        return bail(TE_EUNSUPPORTED);
-    }
     int bps = 0, nsm = 0;
     te_status st;
     if ((st = h->cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device), "device query")))
         return bail(st);
-    if ((st = h->cuda(te::iter_occupancy(id_bytes, kl, G, E, &bps), "occupancy query"))) return bail(st);
+    if (te::iter_smem_bytes(E, nsm) > 227 * 1024) {
+        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 10900 edges)", E);
+        return bail(TE_EUNSUPPORTED);
+    }
+    if ((st = h->cuda(te::iter_occupancy(G, E, nsm, &bps), "occupancy query"))) return bail(st);
     if (bps < 1) { h->err = "iteration kernel does not fit on an SM"; return bail(TE_EUNSUPPORTED); }
     h->grid = nsm * bps;
     std::vector<int> cta_blk(h->grid + 1, nblocks);
@@ -431,20 +441,22 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     // ---------------- device memory ----------------
     void* d_ids;
     unsigned* d_rowoff;
-    int *d_slotbase, *d_lane_demand;
+    int *d_slotbase, *d_demand_of;
+    te::BlockMeta* d_blkmeta;
     float *d_Dn, *d_cap, *d_ne, *d_inv;
     unsigned char* d_np;
     long long* d_slot_path;
-    const size_t nl = (size_t)nblocks * kLanes, ns = (size_t)nslots * kLanes;
+    const size_t ns = (size_t)nslots * kLanes;
     cudaError_t ce = cudaSuccess;
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
     A(h->alloc(&d_ids, ids.size()));
     A(h->alloc(&d_rowoff, sizeof(unsigned) * rowoff.size()));
     A(h->alloc(&d_slotbase, sizeof(int) * slotbase.size()));
-    A(h->alloc(&d_lane_demand, sizeof(int) * nl));
-    A(h->alloc(&d_Dn, sizeof(float) * nl));
-    A(h->alloc(&h->Dc, sizeof(double) * nl));
-    A(h->alloc(&d_np, nl));
+    A(h->alloc(&d_demand_of, sizeof(int) * ND));
+    A(h->alloc(&d_blkmeta, sizeof(te::BlockMeta) * (size_t)nblocks));
+    A(h->alloc(&d_Dn, sizeof(float) * ND));
+    A(h->alloc(&h->Dc, sizeof(double) * ND));
+    A(h->alloc(&d_np, ND));
     A(h->alloc(&d_slot_path, sizeof(long long) * ns));
     A(h->alloc(&d_cap, sizeof(float) * E));
     A(h->alloc(&d_ne, sizeof(float) * E));
@@ -452,7 +464,9 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->x, sizeof(float) * 2 * ns));
     A(h->alloc(&h->u, sizeof(float) * E));
     A(h->alloc(&h->w, sizeof(float) * E));
-    A(h->alloc(&h->loads, sizeof(float) * 3 * (size_t)E));
+    A(h->alloc(&h->u_next, sizeof(float) * E));
+    A(h->alloc(&h->w_next, sizeof(float) * E));
+    A(h->alloc(&h->loads, sizeof(float) * 2 * (size_t)E));
     A(h->alloc(&h->part, sizeof(double) * 2 * 4 * (size_t)h->grid));
     A(h->alloc(&h->barrier, sizeof(unsigned)));
     A(h->alloc(&h->status, sizeof(int)));
@@ -465,9 +479,8 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->pbuf, sizeof(double) * E));
     A(h->alloc(&h->dstage, sizeof(double) * K));
     A(h->alloc(&h->flag, sizeof(int)));
-    A(h->alloc(&h->lam, sizeof(float) * nl));
-    A(h->alloc(&h->ctr, sizeof(unsigned) * 4));
-    A(h->alloc(&h->ps.S, sizeof(double) * nl));
+    A(h->alloc(&h->lam, sizeof(float) * ND));
+    A(h->alloc(&h->ps.S, sizeof(double) * ND));
     A(h->alloc(&h->ps.loads, sizeof(double) * E));
     A(h->alloc(&h->ps.viol, (size_t)E));
     A(h->alloc(&h->ps.vidx, sizeof(int) * E));
@@ -485,10 +498,11 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(cudaMemcpyAsync(d_ids, ids.data(), ids.size(), cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_rowoff, rowoff.data(), sizeof(unsigned) * rowoff.size(), cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_slotbase, slotbase.data(), sizeof(int) * slotbase.size(), cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_lane_demand, lane_demand.data(), sizeof(int) * nl, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_Dn, Dn.data(), sizeof(float) * nl, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(h->Dc, Dc.data(), sizeof(double) * nl, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_np, npv.data(), nl, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_demand_of, demand_of.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_blkmeta, blkmeta.data(), sizeof(te::BlockMeta) * (size_t)nblocks, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_Dn, Dn.data(), sizeof(float) * ND, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(h->Dc, Dc.data(), sizeof(double) * ND, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_np, npv.data(), ND, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_slot_path, slot_path.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_cap, cap_n.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_ne, ne_f.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
@@ -504,6 +518,9 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     L.P = NP;
     L.nnz = P->nnz;
     L.nblocks = nblocks;
+    L.dpb = DPB;
+    L.max_block_rows = max_block_rows;
+    L.blkmeta = d_blkmeta;
     L.nslots = nslots;
     L.nrows = nrows;
     L.id_bytes = id_bytes;
@@ -516,16 +533,17 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     L.Dn = d_Dn;
     h->Dn = d_Dn;
     L.np = d_np;
-    L.lane_demand = d_lane_demand;
+    L.demand_of = d_demand_of;
     L.slot_path = d_slot_path;
     L.cap_n = d_cap;
     L.ne_f = d_ne;
     L.inv_ne = d_inv;
-    // algorithmic traffic of one iteration: ids once, rates read and written,
-    // per-lane demand, per-slot row offsets, per-block slot bases
+    // algorithmic traffic of one iteration: the edge ids once, the rates read
+    // and written, per demand its value and its multiplier read and written,
+    // per block its metadata record
     h->bytes_per_iter = (long long)ids.size() + 2LL * (long long)sizeof(float) * (long long)ns +
-                        (long long)sizeof(float) * (long long)nl + (long long)sizeof(unsigned) * (nslots + 1) +
-                        (long long)sizeof(int) * (nblocks + 1);
+                        3LL * (long long)sizeof(float) * (long long)ND +
+                        (long long)sizeof(te::BlockMeta) * (long long)nblocks;
     te_status rs = te_reset(h);
     if (rs != TE_OK) return bail(rs);
     *out = h;
@@ -541,7 +559,7 @@ extern "C" te_status te_reset(te_handle* h) {
     h->launches += 1;
     A(cudaMemsetAsync(h->u, 0, sizeof(float) * h->L.E, s));
     A(cudaMemsetAsync(h->w, 0, sizeof(float) * h->L.E, s));
-    A(cudaMemsetAsync(h->lam, 0, sizeof(float) * (size_t)h->L.nblocks * kLanes, s));
+    A(cudaMemsetAsync(h->lam, 0, sizeof(float) * (size_t)h->L.nblocks * h->L.dpb, s));
     te::Scalars sc{};
     sc.beta = h->beta0;
     sc.alpha = (isfinite(h->o.alpha_target) && h->o.alpha_start > h->o.alpha_target) ? h->o.alpha_target
@@ -564,9 +582,8 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* 
         if (chunk <= 0) break;
         cudaError_t ce = cudaSuccess;
         auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
-        A(cudaMemsetAsync(h->loads, 0, sizeof(float) * 3 * (size_t)h->L.E, s));
+        A(cudaMemsetAsync(h->loads, 0, sizeof(float) * 2 * (size_t)h->L.E, s));
         A(cudaMemsetAsync(h->barrier, 0, sizeof(unsigned), s));
-        A(cudaMemsetAsync(h->ctr, 0, sizeof(unsigned) * 4, s));
         A(cudaMemsetAsync(h->status, 0, sizeof(int), s));
         te::IterArgs a{};
         a.L = h->L;
@@ -583,7 +600,8 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* 
         a.trace_cap = kTraceCap;
         a.cta_blk = h->cta_blk;
         a.lam = h->lam;
-        a.ctr = h->ctr;
+        a.u_next = h->u_next;
+        a.w_next = h->w_next;
         a.max_iters = chunk;
         a.timeout_ns = h->timeout_ns;
         A(te::launch_iter(a, h->grid, s));
@@ -761,9 +779,9 @@ extern "C" te_status te_set_demands(te_handle* h, const double* D, int32_t in_is
         if (ce != cudaSuccess) return h->cuda(ce, "te_set_demands");
         if (bad) return h->fail(TE_EINVAL, "a demand is not finite and positive");
     }
-    const long long lanes = (long long)h->L.nblocks * kLanes;
-    k_set_demands<<<(unsigned)((lanes + 255) / 256), 256, 0, s>>>(lanes, h->L.lane_demand, h->dstage,
-                                                                  1.0 / h->scale, h->Dn, h->Dc);
+    const long long nd = (long long)h->L.nblocks * h->L.dpb;
+    k_set_demands<<<(unsigned)((nd + 255) / 256), 256, 0, s>>>(nd, h->L.demand_of, h->dstage, 1.0 / h->scale,
+                                                               h->Dn, h->Dc);
     h->launches += 1;
     A(cudaGetLastError());
     A(cudaStreamSynchronize(s));

@@ -42,13 +42,12 @@ template <typename IdT>
 __global__ void k_gap_demands(Layout L, const float* x, const float* u, double pscale, double alpha,
                               double scale, const double* Dc, double* acc) {
     const IdT* ids = static_cast<const IdT*>(L.ids);
-    const int DPB = kLanes / L.G;
+    const int DPB = L.dpb;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double pr = 0.0, du = 0.0;
     if (i < (long long)L.nblocks * DPB) {
         const int b = (int)(i / DPB), t = (int)(i % DPB);
-        const size_t l0 = (size_t)b * kLanes + t * L.G;
-        const int np = L.np[l0];
+        const int np = L.np[i];
         if (np > 0) {
             const int s0 = L.slotbase[b];
             double S = 0.0, pi = INFINITY;
@@ -64,7 +63,7 @@ __global__ void k_gap_demands(Layout L, const float* x, const float* u, double p
                 pi = fmin(pi, q);
             }
             pr = utility(S * scale, alpha);
-            du = conj_term(Dc[l0], pi * pscale, alpha);
+            du = conj_term(Dc[i], pi * pscale, alpha);
         }
     }
     pr = warp_sum(pr);
@@ -92,7 +91,7 @@ cudaError_t launch_gap_impl(const Layout& L, const float* x, const float* u, dou
                             double scale, const double* Dc, double* acc, cudaStream_t st) {
     // p = beta * u in normalised units; in caller units U' scales by scale^-alpha
     const double pscale = beta * pow(scale, -alpha);
-    const long long nd = (long long)L.nblocks * (kLanes / L.G);
+    const long long nd = (long long)L.nblocks * L.dpb;
     const unsigned g = (unsigned)((nd + kThreads - 1) / kThreads);
     if (L.id_bytes == 2)
         k_gap_demands<uint16_t><<<g, kThreads, 0, st>>>(L, x, u, pscale, alpha, scale, Dc, acc);

@@ -2,8 +2,8 @@
 //
 // Device layout ("sliced" incidence).  Demands are sorted by their vector of
 // path lengths and grouped into blocks of 32/G demands; demand t of a block
-// owns the G adjacent warp lanes t*G .. t*G+G-1 (G = 1, 2 or 4 lanes per
-// demand, so that no lane holds more than 8 paths), and path p of the
+// owns the G adjacent warp lanes t*G .. t*G+G-1 (G = 1, 2, 4 or 8 lanes per
+// demand, so that no lane holds more than 4 paths), and path p of the
 // demand sits on lane t*G + p%G in slot p/G.  Block b owns flat slots
 // slotbase[b] .. slotbase[b+1]-1.  Per flat slot s:
 //   x[s*32 + lane]                      rate of that path (FP32, normalised)
@@ -11,10 +11,11 @@
 //                                       edge ids of that path, hop by hop; a
 //                                       shorter path (or a missing one) is
 //                                       padded with the sentinel id E
-// so every warp-wide load of a slot's rate or of one hop of its paths is one
-// contiguous 128 B (rates) or 64 B (16-bit ids) transaction.  Per-demand
-// values (demand, path count, multiplier) are stored once per lane, i.e.
-// repeated on the G lanes of a demand.
+// so every warp-wide load of a slot's rates or of one hop of its paths is one
+// contiguous 128 B (rates) or 64 B (16-bit ids) transaction, and the rows of
+// a whole block are one contiguous range that a single bulk copy moves into
+// shared memory.  Per-demand values (demand, path count, multiplier) are
+// indexed by demand slot d = b*dpb + t.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,12 +26,13 @@ namespace te {
 constexpr int kLanes = 32;
 constexpr int kMaxPaths = 32;     // paths per demand
 constexpr int kMaxHops = 255;     // edges per path
-constexpr int kMaxPathsPerLane = 8;
+constexpr int kMaxPathsPerLane = 4;
 #ifndef TE_ITER_THREADS
-#define TE_ITER_THREADS 1024
+#define TE_ITER_THREADS 512
 #endif
 constexpr int kIterThreads = TE_ITER_THREADS;
 constexpr int kIterWarps = kIterThreads / 32;
+constexpr int kStageRows = 48;    // rows of 16-bit ids per staging buffer (3 KB)
 constexpr int kTraceWidth = 5;
 
 // Solver scalars, kept in device memory between launches.
@@ -54,25 +56,34 @@ struct Options {
     int withhold_cta;  // test hook: this CTA never arrives at the barrier (-1: none)
 };
 
+// Per-block metadata record: first slot, first id row, rows of slots 0..3
+// (8 bits each), number of slots.
+struct BlockMeta {
+    unsigned s0, row0, counts, kb;
+};
+
 struct Layout {
     int E;               // edges
     int K;               // demands
     long long P, nnz;    // user paths and incidences
-    int nblocks;         // ceil(K / 32)
+    int nblocks;         // blocks of dpb demands
+    int dpb;             // demands per block (32 / G)
     long long nslots;    // flat slots
     long long nrows;     // padded id rows (32 ids each)
     int id_bytes;        // 2 (uint16) or 4 (int32)
     int kmax;            // largest paths-per-demand
-    int G;               // lanes per demand (1, 2, 4)
-    int kl;              // largest paths per lane (<= 8)
+    int G;               // lanes per demand (1, 2, 4, 8)
+    int kl;              // largest paths per lane (<= 4)
+    int max_block_rows;  // largest rows of one block
     // device arrays
     const void* ids;             // [nrows*32]
     const unsigned* rowoff;      // [nslots+1]
     const int* slotbase;         // [nblocks+1]
-    const float* Dn;             // [nblocks*32] normalised demand of the lane's demand, 0 on padding
-    const unsigned char* np;     // [nblocks*32] paths of the lane's demand
-    const int* lane_demand;      // [nblocks*32] user demand index, -1 on padding
-    const long long* slot_path;  // [nslots*32] user path index, -1 on padding
+    const BlockMeta* blkmeta;    // [nblocks]
+    const float* Dn;             // [nblocks*dpb] normalised demand, 0 on padding
+    const unsigned char* np;     // [nblocks*dpb] paths of the demand
+    const int* demand_of;        // [nblocks*dpb] caller demand index, -1 on padding
+    const long long* slot_path;  // [nslots*32] caller path index, -1 on padding
     const float* cap_n;          // [E] normalised capacity
     const float* ne_f;           // [E] paths through the edge
     const float* inv_ne;         // [E] 1/ne (0 if unused)
@@ -82,10 +93,12 @@ struct Layout {
 struct IterArgs {
     Layout L;
     Options o;
-    float* x;              // [nslots*32] in/out
+    float* x;              // [2][nslots*32] rate buffers, in/out
     float* u;              // [E] scaled prices, in/out
     float* w;              // [E] u + d (gather weights), in/out
-    float* loads;          // [3*E] edge-load accumulators (triple buffered)
+    float* u_next;         // [E] scratch: prices published for a beta rescale
+    float* w_next;         // [E] scratch: gather weights published each iteration
+    float* loads;          // [2*E] edge-load accumulators (zeroed before launch)
     double* part;          // [2*grid*4] per-CTA residual partials
     unsigned* barrier;     // grid barrier counter (zeroed before launch)
     int* status;           // device status word (0 ok)
@@ -93,10 +106,9 @@ struct IterArgs {
     double* trace;         // [trace_cap*5] ring
     long long trace_cap;
     const int* cta_blk;    // [grid+1] block range of each CTA
-    float* lam;            // [nblocks*32] previous multiplier lambda = beta*nu of each demand
-    unsigned* ctr;         // [4] scratch counters (zeroed before launch)
+    float* lam;            // [nblocks*dpb] previous multiplier lambda = beta*nu of each demand
     long long max_iters;
-    long long timeout_ns;  // bound on every grid-wide wait
+    long long timeout_ns;  // bound on every wait (grid barrier, bulk copy)
 };
 
 // Device status codes (mirror te_status).
@@ -104,8 +116,8 @@ constexpr int kStatusTimeout = 4;
 constexpr int kStatusNumeric = 5;
 
 // Launchers (host side), defined in te_iter.cu / te_proj.cu / te_gap.cu.
-size_t iter_smem_bytes(int E);
-cudaError_t iter_occupancy(int id_bytes, int kl, int G, int E, int* blocks_per_sm);
+size_t iter_smem_bytes(int E, int grid);
+cudaError_t iter_occupancy(int G, int E, int grid_hint, int* blocks_per_sm);
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st);
 
@@ -114,7 +126,7 @@ cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st);
 // are FP64 so that the violation tests see the loads of the FP32 rates
 // without accumulation error.
 struct ProjScratch {
-    double* S;           // [nblocks*32] demand totals (repeated on the demand's lanes)
+    double* S;           // [nblocks*dpb] demand totals
     double* loads;       // [E]
     unsigned char* viol; // [E] 1 if L_e > C_e
     int* vidx;           // [E] compact index of violated edges or -1
@@ -134,7 +146,7 @@ cudaError_t launch_from_user(const Layout& L, const float* in, float* x, float i
 // Duality gap terms of a feasible sliced x (normalised) at prices
 // p = beta*u: acc[0] += sum_c U(S_c), acc[1] += sum_c max_S [U(S) - pi_c S],
 // acc[2] += sum_e p_e C_e, all in caller units (acc zeroed by the caller).
-// Dc: caller-unit demand of each lane (0 on padding lanes).
+// Dc: caller-unit demand of each demand slot (0 on padding).
 cudaError_t launch_gap_impl(const Layout& L, const float* x, const float* u, double beta, double alpha,
                             double scale, const double* Dc, double* acc, cudaStream_t st);
 

@@ -1,23 +1,29 @@
 // Persistent iteration kernel of the GATE ADMM loop (Algorithm 1).
 //
 // One cooperative launch runs many iterations.  Per iteration:
-//   phase A (every CTA, one warp per block of 32 demands, one lane per
+//   phase A (every CTA, one warp per block of 32/G demands, G lanes per
 //            demand): gather the consensus term of each path from the edge
 //            weights w_e = u_e + d_e held in shared memory, solve the demand's
 //            x-block (Eq. 14 and the sum computation of Appendix B.2), write
-//            the new rates, and add each path's new rate into a per-CTA
-//            shared-memory histogram of edge loads; then flush the histogram
-//            into a global load vector and publish the CTA's FP64 residual
-//            partials;
-//   one bounded grid-wide barrier;
-//   phase B (every CTA, redundantly and identically): the per-edge price
+//            the new rates, and add each path's new rate into the CTA's
+//            shared-memory histogram of edge loads (split 32-bit fixed point,
+//            native shared-memory integer atomics).  The
+//            edge ids of a block are brought into shared memory by one bulk
+//            asynchronous copy (TMA), issued one block ahead of use; the
+//            block's metadata record is loaded two blocks ahead.  The CTA then
+//            flushes its histogram into the global load vector and publishes
+//            its FP64 residual partials;
+//   grid barrier 1;
+//   phase B (every CTA, its own slice of the edges): the per-edge price
 //            update u_e' = max(0, u_e + (L_e - C_e)/n_e) (Eqs. 9/13 after the
-//            per-edge collapse of the consensus duals), the residuals r and s
-//            (Eqs. 15-16, cross-thread and cross-CTA sums in FP64), residual
-//            balancing (Eq. 17), the stop rule (Eq. 18) and
-//            alpha-continuation.  Every CTA reads the same loads and partials
-//            in the same order, so all of them hold bit-identical prices and
-//            take the same decisions without a second barrier.
+//            per-edge collapse of the consensus duals) and its part of the
+//            primal residual; publishes the new gather weights;
+//   grid barrier 2;
+//   control (every CTA, identically): the residuals r and s (Eqs. 15-16,
+//            cross-CTA sums in FP64 in a fixed order), residual balancing
+//            (Eq. 17), the stop rule (Eq. 18) and alpha-continuation, then
+//            loads the new gather weights into shared memory.
+// Every wait (grid barriers, bulk copies) is bounded.
 //
 // Rates and prices are FP32.  The per-demand multiplier is kept in scaled
 // form nu = lambda / beta, so x_r = max(0, m_r + nu / n_r) with
@@ -141,18 +147,21 @@ template <int G>
 __device__ __forceinline__ float gsum(float v, unsigned gm) {
     if (G >= 2) v += __shfl_xor_sync(gm, v, 1);
     if (G >= 4) v += __shfl_xor_sync(gm, v, 2);
+    if (G >= 8) v += __shfl_xor_sync(gm, v, 4);
     return v;
 }
 template <int G>
 __device__ __forceinline__ float gmin(float v, unsigned gm) {
     if (G >= 2) v = fminf(v, __shfl_xor_sync(gm, v, 1));
     if (G >= 4) v = fminf(v, __shfl_xor_sync(gm, v, 2));
+    if (G >= 8) v = fminf(v, __shfl_xor_sync(gm, v, 4));
     return v;
 }
 template <int G>
 __device__ __forceinline__ int gall(int v, unsigned gm) {
     if (G >= 2) v &= __shfl_xor_sync(gm, v, 1);
     if (G >= 4) v &= __shfl_xor_sync(gm, v, 2);
+    if (G >= 8) v &= __shfl_xor_sync(gm, v, 4);
     return v;
 }
 
@@ -230,48 +239,92 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
     return nu;
 }
 
-// Bulk prefetch of [p, p + bytes) into L2 by the TMA engine (p and bytes
-// multiples of 16).
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+
+// ---------------------------------------------------------------------------
+// bulk asynchronous copies and mbarriers (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of
+// 16), completion counted on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false on timeout.
+__device__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if ((long long)(globaltimer_ns() - t0) > timeout_ns) return false;
+    }
+    return true;
 }
 
-// One block (32/G demands, G lanes each): gather, x-block, scatter.
-template <typename IdT, int KL, int G>
-__device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane, const float* __restrict__ xin,
-                                              float* __restrict__ xout, const float* w_s,
-                                              unsigned long long* h_s,
-                                              float inv_beta, float logbeta, float beta_f, float alpha,
-                                              KSum& ds2, KSum& x2, KSum& ex2) {
-    const IdT* __restrict__ ids = static_cast<const IdT*>(a.L.ids);
-    const IdT sentinel = (IdT)a.L.E;
+template <bool STAGED>
+__device__ __forceinline__ uint16_t load_id(const uint16_t* p) {
+    if (STAGED) return *p;
+    return __ldg(p);
+}
+
+// One block (32/G demands, G lanes each, at most 4 paths per lane): gather,
+// x-block, scatter.  bids points at the block's first id row, in shared
+// memory (STAGED) or in global memory.
+template <int G, bool STAGED>
+__device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane, const uint16_t* bids, int s0,
+                                              unsigned counts, int KB, const float* __restrict__ xin,
+                                              float* __restrict__ xout, const float* w_s, unsigned* h_hi,
+                                              unsigned* h_lo, float inv_beta, float logbeta,
+                                              float beta_f, float alpha, KSum& ds2, KSum& x2, KSum& ex2) {
+    constexpr int KL = kMaxPathsPerLane;
+    const uint16_t sentinel = (uint16_t)a.L.E;
     const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    // block metadata in one coalesced load: slot bases, then row offsets
-    int sb = 0;
-    if (lane < 2) sb = __ldg(&a.L.slotbase[b + lane]);
-    const int s0 = __shfl_sync(0xffffffffu, sb, 0);
-    const int KB = __shfl_sync(0xffffffffu, sb, 1) - s0;
-    unsigned ro = 0u;
-    if (lane <= KB) ro = __ldg(&a.L.rowoff[s0 + lane]);
-    const size_t li = (size_t)b * kLanes + lane;
-    const float D = __ldg(&a.L.Dn[li]);
-    const float lam0 = __ldcg(&a.lam[li]);
+    const size_t di = (size_t)b * a.L.dpb + lane / G;
+    const float D = __ldg(&a.L.Dn[di]);
+    const float lam0 = __ldcg(&a.lam[di]);
     float xo[KL], m[KL], an[KL];
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
         xo[j] = 0.f;
         if (j < KB) xo[j] = __ldcg(&xin[(size_t)(s0 + j) * kLanes + lane]);
     }
+    unsigned rs = 0;  // first row of slot j within the block
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
-        m[j] = 0.f; an[j] = 0.f;
+        m[j] = 0.f;
+        an[j] = 0.f;
         if (j < KB) {
-            const unsigned r0 = __shfl_sync(0xffffffffu, ro, j), r1 = __shfl_sync(0xffffffffu, ro, j + 1);
+            const unsigned cnt = (counts >> (8 * j)) & 0xffu;
             float q = 0.f;
             int n = 0;
             #pragma unroll 4
-            for (unsigned r = r0; r < r1; ++r) {
-                const IdT id = __ldg(&ids[(size_t)r * kLanes + lane]);
+            for (unsigned r = 0; r < cnt; ++r) {
+                const uint16_t id = load_id<STAGED>(&bids[(size_t)(rs + r) * kLanes + lane]);
                 q += w_s[id];
                 n += (id != sentinel);
             }
@@ -279,33 +332,44 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
                 an[j] = __frcp_rn((float)n);
                 m[j] = fmaf(-q, an[j], xo[j]);
             }
+            rs += cnt;
         }
     }
     float nu = 0.f;
     if (D > 0.f) {
         nu = solve_nu<KL, G>(m, an, D, inv_beta, logbeta, alpha, lam0 * inv_beta, gm);
-        __stcg(&a.lam[li], nu * beta_f);
+        if ((lane & (G - 1)) == 0) __stcg(&a.lam[di], nu * beta_f);
     }
     float bd = 0.f, bx = 0.f, be = 0.f;
+    rs = 0;
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
         if (j < KB) {
+            const unsigned cnt = (counts >> (8 * j)) & 0xffu;
             const size_t sl = (size_t)(s0 + j);
             const float xn = an[j] > 0.f ? fmaxf(0.f, fmaf(nu, an[j], m[j])) : 0.f;
             __stcg(&xout[sl * kLanes + lane], xn);
             const float dx = xn - xo[j];
             bd = fmaf(dx, dx, bd);
             bx = fmaf(xn, xn, bx);
-            const unsigned r0 = __shfl_sync(0xffffffffu, ro, j), r1 = __shfl_sync(0xffffffffu, ro, j + 1);
             if (xn != 0.f) {
                 be = fmaf(xn * xn, __frcp_rn(an[j]), be);
-                const unsigned long long fx = __float2ull_rn(xn * 0x1p32f);
+                // split fixed point: integer part of xn * 2^12 and the
+                // remaining fraction in units of 2^-24 (both exact in FP32)
+                const float vf = xn * 0x1p12f;
+                const float hf = floorf(vf);
+                const unsigned hi = (unsigned)hf;
+                const unsigned lo = (unsigned)__float2uint_rn((vf - hf) * 0x1p12f);
                 #pragma unroll 4
-                for (unsigned r = r0; r < r1; ++r) {
-                    const IdT id = __ldg(&ids[(size_t)r * kLanes + lane]);
-                    if (id != sentinel) atomicAdd(&h_s[id], fx);
+                for (unsigned r = 0; r < cnt; ++r) {
+                    const uint16_t id = load_id<STAGED>(&bids[(size_t)(rs + r) * kLanes + lane]);
+                    if (id != sentinel) {
+                        if (hi) atomicAdd(&h_hi[id], hi);
+                        atomicAdd(&h_lo[id], lo);
+                    }
                 }
             }
+            rs += cnt;
         }
     }
     ds2.add(bd);
@@ -313,43 +377,64 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
     ex2.add(be);
 }
 
-// Distance, in blocks, of the rolling L2 prefetch window ahead of the
-// blocks being processed by a CTA.
-constexpr int kPrefetchAhead = 2 * kIterWarps;
+__device__ __forceinline__ unsigned rows_of(unsigned counts) {
+    return (counts & 0xffu) + ((counts >> 8) & 0xffu) + ((counts >> 16) & 0xffu) + (counts >> 24);
+}
 
-template <typename IdT, int KL, int G>
+template <int G>
 __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
-    extern __shared__ __align__(16) unsigned long long smem[];
+    extern __shared__ __align__(128) unsigned smem[];
     const int E = a.L.E;
-    // this CTA's edge-load histogram in 64-bit fixed point (2^-32 units):
-    // integer atomics on shared memory are native, float ones are not
-    unsigned long long* h_s = smem;                  // [E+1]
-    float* w_s = reinterpret_cast<float*>(h_s + (E + 1));  // [E+1] gather weights u_e + d_e; w_s[E] = 0
-    float* u_s = w_s + (E + 1);                      // [E]   scaled prices
+    const int NG = gridDim.x;  // CTAs in the grid
+    // dynamic shared memory: histogram, gather weights, staging, price slice
+    unsigned* h_hi = smem;                                           // [E+1] units of 2^-12
+    unsigned* h_lo = h_hi + (E + 1);                                 // [E+1] units of 2^-24
+    float* w_s = reinterpret_cast<float*>(h_lo + (E + 1));          // [E+1], w_s[E] = 0
+    uint16_t* stage = reinterpret_cast<uint16_t*>(
+        reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) & ~uintptr_t(127));  // [warps][2][kStageRows*32]
+    float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kStageRows * kLanes);  // price slice
+    const int e_lo = (int)((long long)blockIdx.x * E / NG), e_hi = (int)((long long)(blockIdx.x + 1) * E / NG);
+    float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
+    __shared__ __align__(8) unsigned long long s_mbar[kIterWarps * 2];
     __shared__ double red[kIterWarps];
     __shared__ double s_fin[4];
-    __shared__ int s_next;  // next block of this CTA's range (relative)
+    __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int NG = gridDim.x;  // CTAs in the grid
     const int b_lo = a.cta_blk[blockIdx.x], b_hi = a.cta_blk[blockIdx.x + 1];
-    if (tid == 0) s_next = 0;
+    const uint16_t* ids = static_cast<const uint16_t*>(a.L.ids);
+    uint16_t* wstage[2] = {stage + (size_t)(warp * 2) * kStageRows * kLanes,
+                           stage + (size_t)(warp * 2 + 1) * kStageRows * kLanes};
+    unsigned long long* mb = &s_mbar[warp * 2];
 
     for (int e = tid; e < E; e += kIterThreads) {
-        u_s[e] = a.u[e];
         w_s[e] = a.w[e];
-        h_s[e] = 0ull;
+        h_hi[e] = 0u;
+        h_lo[e] = 0u;
     }
-    if (tid == 0) { w_s[E] = 0.f; h_s[E] = 0ull; }
+    for (int e = e_lo + tid; e < e_hi; e += kIterThreads) s_u[e - e_lo] = a.u[e];
+    if (tid == 0) {
+        w_s[E] = 0.f;
+        h_hi[E] = 0u;
+        h_lo[E] = 0u;
+        s_next = 0;
+    }
+    if (lane == 0) {
+        mbar_init(&mb[0], 1);
+        mbar_init(&mb[1], 1);
+        fence_mbar_init();
+    }
     Scalars sc = *a.sc;
     int xbuf = sc.xbuf;
     sc.converged = 0;
     sc.stop_reason = 0;
+    unsigned par[2] = {0u, 0u};  // phase parity of each staging buffer's mbarrier
+    bool pending[2] = {false, false};
+    bool failed = false;
     __syncthreads();
 
     const size_t xstride = (size_t)a.L.nslots * kLanes;
     long long done = 0;
-    (void)warp;
 
     for (long long it = 0; it < a.max_iters; ++it) {
         const float* __restrict__ xin = a.x + (size_t)xbuf * xstride;
@@ -361,57 +446,84 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         KSum ds2, x2, ex2;
 
         // ---------------- phase A: per-demand rate updates ----------------
-        // each CTA owns a contiguous range of blocks (balanced by their
-        // rows); its warps take blocks one at a time from a shared counter.
-        // The CTA's rows and rates are contiguous in memory, so the warp that
-        // takes block b also prefetches block b + kPrefetchAhead into L2 (its
-        // bounds are loaded when b is taken and the bulk prefetch is issued
-        // after b is processed, so no warp waits on them).
+        // Blocks of this CTA's range are taken one at a time from a shared
+        // counter.  The metadata record of the block after next is loaded
+        // (by lane 0) while the bulk copy of the next block's ids runs and
+        // the current block is processed.
         {
-            const IdT* ids = static_cast<const IdT*>(a.L.ids);
-            if (it == 0 && warp == 0) {
-                // warm the start of the window
-                const int pe = min(b_hi, b_lo + kPrefetchAhead);
-                if (lane == 0 && pe > b_lo) {
-                    const int s0 = __ldg(&a.L.slotbase[b_lo]), s1 = __ldg(&a.L.slotbase[pe]);
-                    const unsigned r0 = __ldg(&a.L.rowoff[s0]), r1 = __ldg(&a.L.rowoff[s1]);
-                    if (r1 > r0) prefetch_l2(ids + (size_t)r0 * kLanes, (unsigned)((r1 - r0) * kLanes * sizeof(IdT)));
-                    if (s1 > s0) prefetch_l2(xin + (size_t)s0 * kLanes, (unsigned)((s1 - s0) * kLanes * sizeof(float)));
+            auto grab = [&]() -> int {
+                int v = 0;
+                if (lane == 0) v = atomicAdd(&s_next, 1);
+                return __shfl_sync(0xffffffffu, v, 0) + b_lo;
+            };
+            auto load_meta = [&](int b) -> BlockMeta {
+                BlockMeta m{0u, 0u, 0u, 0u};
+                if (lane == 0 && b < b_hi) m = a.L.blkmeta[b];
+                return m;
+            };
+            // issues the bulk copy of block b into buffer k; returns whether
+            // the block fits a staging buffer (else it is read from global)
+            auto issue = [&](int b, const BlockMeta& m, int k) -> bool {
+                const unsigned counts = __shfl_sync(0xffffffffu, m.counts, 0);
+                const unsigned row0 = __shfl_sync(0xffffffffu, m.row0, 0);
+                const unsigned rows = rows_of(counts);
+                if (rows > (unsigned)kStageRows || rows == 0) return false;
+                __syncwarp();
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    const unsigned bytes = rows * kLanes * (unsigned)sizeof(uint16_t);
+                    mbar_expect_tx(&mb[k], bytes);
+                    bulk_g2s(wstage[k], ids + (size_t)row0 * kLanes, bytes, &mb[k]);
                 }
-            }
-            while (true) {
-                int b = 0;
-                if (lane == 0) b = atomicAdd(&s_next, 1);
-                b = __shfl_sync(0xffffffffu, b, 0) + b_lo;
-                if (b >= b_hi) break;
-                // bounds of the block kPrefetchAhead ahead (lanes 0-1 slot bases)
-                const int bp = b + kPrefetchAhead;
-                int psb = 0;
-                if (bp < b_hi && lane < 2) psb = __ldg(&a.L.slotbase[bp + lane]);
-                process_block<IdT, KL, G>(a, b, lane, xin, xout, w_s, h_s, inv_beta, logbeta, beta_f, alpha, ds2,
-                                          x2, ex2);
-                if (bp < b_hi) {
-                    const int ps0 = __shfl_sync(0xffffffffu, psb, 0), ps1 = __shfl_sync(0xffffffffu, psb, 1);
-                    unsigned pro = 0u;
-                    if (lane < 2) pro = __ldg(&a.L.rowoff[lane == 0 ? ps0 : ps1]);
-                    const unsigned pr0 = __shfl_sync(0xffffffffu, pro, 0), pr1 = __shfl_sync(0xffffffffu, pro, 1);
-                    if (lane == 0) {
-                        if (pr1 > pr0)
-                            prefetch_l2(ids + (size_t)pr0 * kLanes, (unsigned)((pr1 - pr0) * kLanes * sizeof(IdT)));
-                        if (ps1 > ps0)
-                            prefetch_l2(xin + (size_t)ps0 * kLanes, (unsigned)((ps1 - ps0) * kLanes * sizeof(float)));
+                pending[k] = true;
+                (void)b;
+                return true;
+            };
+            int b0 = grab();
+            BlockMeta m0 = load_meta(b0);
+            int b1 = grab();
+            BlockMeta m1 = load_meta(b1);
+            int cur = 0;
+            bool st0 = (b0 < b_hi) && !failed ? issue(b0, m0, cur) : false;
+            while (b0 < b_hi && !failed) {
+                const int b2 = grab();
+                const BlockMeta m2 = load_meta(b2);
+                const bool st1 = (b1 < b_hi) ? issue(b1, m1, cur ^ 1) : false;
+                const int s0 = (int)__shfl_sync(0xffffffffu, m0.s0, 0);
+                const unsigned counts = __shfl_sync(0xffffffffu, m0.counts, 0);
+                const int KB = (int)__shfl_sync(0xffffffffu, m0.kb, 0);
+                if (st0) {
+                    if (!mbar_wait(&mb[cur], par[cur], a.timeout_ns)) {
+                        if (lane == 0) atomicCAS(a.status, 0, kStatusTimeout);
+                        failed = true;
+                        break;
                     }
+                    par[cur] ^= 1u;
+                    pending[cur] = false;
+                    process_block<G, true>(a, b0, lane, wstage[cur], s0, counts, KB, xin, xout, w_s, h_hi, h_lo,
+                                           inv_beta, logbeta, beta_f, alpha, ds2, x2, ex2);
+                } else {
+                    const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
+                    process_block<G, false>(a, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, xin, xout,
+                                            w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, ds2, x2, ex2);
                 }
+                b0 = b1;
+                m0 = m1;
+                st0 = st1;
+                b1 = b2;
+                m1 = m2;
+                cur ^= 1;
             }
         }
         __syncthreads();
         if (tid == 0) s_next = 0;
         // flush this CTA's loads into the global accumulator of this iteration
-        float* Lg = a.loads + (size_t)(it % 3) * E;
+        float* Lg = a.loads + (size_t)(it & 1) * E;
         for (int e = tid; e < E; e += kIterThreads) {
-            const unsigned long long v = h_s[e];
-            if (v != 0ull) atomicAdd(&Lg[e], (float)((double)v * 0x1p-32));
-            h_s[e] = 0ull;
+            const unsigned hi = h_hi[e], lo = h_lo[e];
+            if ((hi | lo) != 0u) atomicAdd(&Lg[e], (float)((double)hi * 0x1p-12 + (double)lo * 0x1p-24));
+            h_hi[e] = 0u;
+            h_lo[e] = 0u;
         }
         {
             const double v0 = block_sum((double)ds2.s, red);
@@ -424,72 +536,88 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 __stcg(&p[2], v2);
             }
         }
-        if (!grid_sync(a.barrier, (unsigned)((it + 1) * NG), a.status, a.timeout_ns,
+        if (!grid_sync(a.barrier, (unsigned)((2 * it + 1) * NG), a.status, a.timeout_ns,
                        (int)blockIdx.x != a.o.withhold_cta)) {
+            failed = true;
             break;
         }
 
-        // ---------------- phase B: per-edge prices and control ----------------
-        float rp = 0.f;
+        // ---------------- phase B: this CTA's slice of the edge prices ----------------
         {
             KSum r2;
-            for (int e = tid; e < E; e += kIterThreads) {
+            for (int e = e_lo + tid; e < e_hi; e += kIterThreads) {
                 const float ne = __ldg(&a.L.ne_f[e]);
-                const float u = u_s[e];
+                const float u = s_u[e - e_lo];
+                const float L = __ldcg(&Lg[e]);
+                __stcg(&Lg[e], 0.f);  // ready for iteration it + 2
                 float un = 0.f;
-                if (ne > 0.f)
-                    un = fmaxf(0.f, fmaf(__ldcg(&Lg[e]) - __ldg(&a.L.cap_n[e]), __ldg(&a.L.inv_ne[e]), u));
+                if (ne > 0.f) un = fmaxf(0.f, fmaf(L - __ldg(&a.L.cap_n[e]), __ldg(&a.L.inv_ne[e]), u));
                 const float d = un - u;
                 r2.add(ne * d * d);
-                u_s[e] = un;
-                w_s[e] = un + d;
+                s_un[e - e_lo] = un;
+                __stcg(&a.u_next[e], un);
+                __stcg(&a.w_next[e], un + d);
             }
-            rp = r2.s;
+            const double v3 = block_sum((double)r2.s, red);
+            if (tid == 0) __stcg(&a.part[((size_t)(it & 1) * NG + blockIdx.x) * 4 + 3], v3);
         }
-        const double r2s = block_sum((double)rp, red);
+        if (!grid_sync(a.barrier, (unsigned)((2 * it + 2) * NG), a.status, a.timeout_ns, true)) {
+            failed = true;
+            break;
+        }
+
+        // ---------------- control: residuals, beta, alpha, stop ----------------
         if (tid < 32) {
-            double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
             const double* p = a.part + (size_t)(it & 1) * NG * 4;
             for (int c = lane; c < NG; c += 32) {
                 v0 += __ldcg(&p[c * 4 + 0]);
                 v1 += __ldcg(&p[c * 4 + 1]);
                 v2 += __ldcg(&p[c * 4 + 2]);
+                v3 += __ldcg(&p[c * 4 + 3]);
             }
             for (int o = 16; o > 0; o >>= 1) {
                 v0 += __shfl_xor_sync(0xffffffffu, v0, o);
                 v1 += __shfl_xor_sync(0xffffffffu, v1, o);
                 v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+                v3 += __shfl_xor_sync(0xffffffffu, v3, o);
             }
-            if (lane == 0) { s_fin[0] = v0; s_fin[1] = v1; s_fin[2] = v2; }
+            if (lane == 0) { s_fin[0] = v0; s_fin[1] = v1; s_fin[2] = v2; s_fin[3] = v3; }
         }
         __syncthreads();
         const double s_res = sqrt(s_fin[0]) / fmax(sqrt(s_fin[1]), 1e-30);
-        const double r_res = sqrt(r2s) / fmax(sqrt(s_fin[2]), 1e-30);
+        const double r_res = sqrt(s_fin[3]) / fmax(sqrt(s_fin[2]), 1e-30);
         xbuf ^= 1;
         sc.iter_total++;
         sc.iter_alpha++;
         done++;
         int event = 0;
-        if (!isfinite(s_res) || !isfinite(r_res)) {
-            if (tid == 0 && blockIdx.x == 0) atomicCAS(a.status, 0, kStatusNumeric);
-            sc.r = r_res;
-            sc.s = s_res;
-            break;
-        }
-        if (a.o.adapt_beta) {
+        const bool numeric_ok = isfinite(s_res) && isfinite(r_res);
+        float ratio = 1.f;
+        if (numeric_ok && a.o.adapt_beta) {
             double nb = sc.beta;
             if (r_res > a.o.A * s_res) nb = sc.beta * a.o.C;
             else if (s_res > a.o.A * r_res) nb = sc.beta / a.o.C;
             if (nb != sc.beta) {
-                const float ratio = (float)(sc.beta / nb);
-                for (int e = tid; e < E; e += kIterThreads) {
-                    const float u = u_s[e];
-                    w_s[e] = fmaf(u, ratio - 1.f, w_s[e]);
-                    u_s[e] = u * ratio;
-                }
+                ratio = (float)(sc.beta / nb);
                 sc.beta = nb;
                 event |= 1;
             }
+        }
+        // commit the slice's new prices (scaled with beta) and the new gather
+        // weights w = u' + d (the rescale keeps d, a primal quantity)
+        for (int e = e_lo + tid; e < e_hi; e += kIterThreads) s_u[e - e_lo] = s_un[e - e_lo] * ratio;
+        for (int e = tid; e < E; e += kIterThreads) {
+            float w = __ldcg(&a.w_next[e]);
+            if (ratio != 1.f) w = fmaf(__ldcg(&a.u_next[e]), ratio - 1.f, w);
+            w_s[e] = w;
+        }
+        if (!numeric_ok) {
+            if (tid == 0 && blockIdx.x == 0) atomicCAS(a.status, 0, kStatusNumeric);
+            sc.r = r_res;
+            sc.s = s_res;
+            __syncthreads();
+            break;
         }
         bool stop = false;
         if (r_res <= a.o.gamma && s_res <= a.o.gamma) {
@@ -510,14 +638,9 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         }
         sc.r = r_res;
         sc.s = s_res;
-        if (blockIdx.x == 0) {
-            if (tid == 0 && a.trace_cap > 0) {
-                double* t = a.trace + (size_t)((sc.iter_total - 1) % a.trace_cap) * kTraceWidth;
-                t[0] = r_res; t[1] = s_res; t[2] = sc.beta; t[3] = sc.alpha; t[4] = (double)event;
-            }
-            // the load buffer used two iterations from now must start at zero
-            float* Lz = a.loads + (size_t)((it + 2) % 3) * E;
-            for (int e = tid; e < E; e += kIterThreads) __stcg(&Lz[e], 0.f);
+        if (blockIdx.x == 0 && tid == 0 && a.trace_cap > 0) {
+            double* t = a.trace + (size_t)((sc.iter_total - 1) % a.trace_cap) * kTraceWidth;
+            t[0] = r_res; t[1] = s_res; t[2] = sc.beta; t[3] = sc.alpha; t[4] = (double)event;
         }
         __syncthreads();
         if (stop) {
@@ -526,11 +649,16 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
             break;
         }
     }
+    // a warp that gave up may still have bulk copies in flight into its
+    // staging buffers: wait for them (bounded) before the CTA exits
+    if (failed) {
+        for (int k = 0; k < 2; ++k)
+            if (pending[k]) mbar_wait(&mb[k], par[k], a.timeout_ns);
+    }
+    __syncthreads();
+    for (int e = e_lo + tid; e < e_hi; e += kIterThreads) a.u[e] = s_u[e - e_lo];
     if (blockIdx.x == 0) {
-        for (int e = tid; e < E; e += kIterThreads) {
-            a.u[e] = u_s[e];
-            a.w[e] = w_s[e];
-        }
+        for (int e = tid; e < E; e += kIterThreads) a.w[e] = w_s[e];
         if (tid == 0) {
             sc.iters_run = done;
             sc.xbuf = xbuf;
@@ -547,65 +675,61 @@ __global__ void k_init_x(Layout L, float* x) {
     if (i >= (long long)L.nblocks * kLanes) return;
     const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
     const int hh = lane % L.G;
+    const size_t di = (size_t)b * L.dpb + lane / L.G;
     const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
-    const int np = L.np[i];
-    const float v = np > 0 ? L.Dn[i] / (float)np : 0.f;
+    const int np = L.np[di];
+    const float v = np > 0 ? L.Dn[di] / (float)np : 0.f;
     for (int j = 0; j < KB; ++j) x[(size_t)(s0 + j) * kLanes + lane] = j * L.G + hh < np ? v : 0.f;
 }
 
-template <typename IdT, int KL, int G>
+template <int G>
 cudaError_t launch_iter_t(const IterArgs& a, int grid, cudaStream_t st) {
-    const size_t smem = iter_smem_bytes(a.L.E);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<IdT, KL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+    const size_t smem = iter_smem_bytes(a.L.E, grid);
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     IterArgs args = a;
     void* params[] = {&args};
-    return cudaLaunchCooperativeKernel((const void*)k_iter<IdT, KL, G>, dim3(grid), dim3(kIterThreads), params,
-                                       smem, st);
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G>, dim3(grid), dim3(kIterThreads), params, smem, st);
 }
 
-template <typename IdT, int KL, int G>
-cudaError_t occupancy_t(int E, int* blocks) {
-    const size_t smem = iter_smem_bytes(E);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<IdT, KL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+template <int G>
+cudaError_t occupancy_t(int E, int grid_hint, int* blocks) {
+    const size_t smem = iter_smem_bytes(E, grid_hint);
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<IdT, KL, G>, kIterThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G>, kIterThreads, smem);
 }
 
 }  // namespace
-}  // namespace te
 
-namespace te {
-
-size_t iter_smem_bytes(int E) {
-    return (size_t)(E + 1) * sizeof(unsigned long long) + (size_t)(2 * (size_t)E + 1) * sizeof(float);
+// Dynamic shared memory of the iteration kernel: histogram (8 B per edge),
+// gather weights (4 B per edge), staging buffers, and the CTA's price slice
+// (current and next) for a grid of at least `grid` CTAs.
+size_t iter_smem_bytes(int E, int grid) {
+    size_t b = 2 * (size_t)(E + 1) * sizeof(unsigned) + (size_t)(E + 1) * sizeof(float);
+    b = (b + 31 * sizeof(float) + 127) & ~size_t(127);
+    b += (size_t)kIterWarps * 2 * kStageRows * kLanes * sizeof(uint16_t);
+    const int slice = (E + grid - 1) / (grid > 0 ? grid : 1) + 1;
+    b += 2 * (size_t)slice * sizeof(float);
+    return b;
 }
 
-// instantiations: (paths per lane, lanes per demand) = (4,1), (8,1), (8,2), (8,4)
-#define TE_DISPATCH(ID_BYTES, KL, G, CALL)                                       \
-    do {                                                                         \
-        if ((ID_BYTES) == 2) {                                                   \
-            if ((G) == 1) return (KL) <= 4 ? CALL(uint16_t, 4, 1) : CALL(uint16_t, 8, 1); \
-            if ((G) == 2) return CALL(uint16_t, 8, 2);                           \
-            return CALL(uint16_t, 8, 4);                                         \
-        }                                                                        \
-        if ((G) == 1) return (KL) <= 4 ? CALL(int32_t, 4, 1) : CALL(int32_t, 8, 1); \
-        if ((G) == 2) return CALL(int32_t, 8, 2);                                \
-        return CALL(int32_t, 8, 4);                                              \
-    } while (0)
-
-cudaError_t iter_occupancy(int id_bytes, int kl, int G, int E, int* blocks_per_sm) {
-#define TE_OCC(T, K, GG) occupancy_t<T, K, GG>(E, blocks_per_sm)
-    TE_DISPATCH(id_bytes, kl, G, TE_OCC);
-#undef TE_OCC
+cudaError_t iter_occupancy(int G, int E, int grid_hint, int* blocks_per_sm) {
+    switch (G) {
+        case 1: return occupancy_t<1>(E, grid_hint, blocks_per_sm);
+        case 2: return occupancy_t<2>(E, grid_hint, blocks_per_sm);
+        case 4: return occupancy_t<4>(E, grid_hint, blocks_per_sm);
+        default: return occupancy_t<8>(E, grid_hint, blocks_per_sm);
+    }
 }
 
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
-#define TE_LAUNCH(T, K, GG) launch_iter_t<T, K, GG>(a, grid, st)
-    TE_DISPATCH(a.L.id_bytes, a.L.kl, a.L.G, TE_LAUNCH);
-#undef TE_LAUNCH
+    switch (a.L.G) {
+        case 1: return launch_iter_t<1>(a, grid, st);
+        case 2: return launch_iter_t<2>(a, grid, st);
+        case 4: return launch_iter_t<4>(a, grid, st);
+        default: return launch_iter_t<8>(a, grid, st);
+    }
 }
 
 cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st) {

@@ -44,7 +44,7 @@ __device__ __forceinline__ const IdT* ids_of(const Layout& L) {
 // x <- max(x, 0) on every slot; S = the demand's total, written to each of
 // its G lanes.  One thread per demand.
 __global__ void k_clamp_sum(Layout L, float* x, double* S) {
-    const int DPB = kLanes / L.G;
+    const int DPB = L.dpb;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * DPB) return;
     const int b = (int)(i / DPB), t = (int)(i % DPB);
@@ -59,7 +59,7 @@ __global__ void k_clamp_sum(Layout L, float* x, double* S) {
             acc += (double)v;
         }
     }
-    for (int hh = 0; hh < L.G; ++hh) S[(size_t)b * kLanes + t * L.G + hh] = acc;
+    S[i] = acc;
 }
 
 // L_e = sum of rates over the paths through e (loads must be zeroed).
@@ -122,16 +122,15 @@ __global__ void k_count_viol(Layout L, const unsigned char* viol, unsigned char*
 // ties to the lower path index.  One thread per demand; path p of the demand
 // is on lane t*G + p%G, slot p/G.
 __global__ void k_demand_trim(Layout L, float* x, const double* S, const unsigned char* Cp) {
-    const int DPB = kLanes / L.G;
+    const int DPB = L.dpb;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * DPB) return;
     const int b = (int)(i / DPB), t = (int)(i % DPB);
-    const size_t l0 = (size_t)b * kLanes + t * L.G;
-    const double D = (double)L.Dn[l0];
-    double Ec = S[l0] - D;
+    const double D = (double)L.Dn[i];
+    double Ec = S[i] - D;
     if (!(Ec > 0.0) || D <= 0.0) return;
     const int s0 = L.slotbase[b];
-    const int np = L.np[l0];
+    const int np = L.np[i];
     unsigned taken = 0u;  // np <= 32
     for (int k = 0; k < np && Ec > 0.0; ++k) {
         int best = -1, bc = -1;
@@ -180,7 +179,8 @@ __global__ void k_select_hist(Layout L, const float* x, const double* S, const u
         const float v = x[sl * kLanes + lane];
         const int c = Cp[sl * kLanes + lane];
         if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(S[i], c, alpha, L.slot_path[sl * kLanes + lane]);
+        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha,
+                                                L.slot_path[sl * kLanes + lane]);
         const int digit = (int)((key >> shift) & 0xffull);
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
@@ -237,7 +237,8 @@ __global__ void k_edge_trim(Layout L, float* x, const double* S, const unsigned 
         const float v = x[sl * kLanes + lane];
         const int c = Cp[sl * kLanes + lane];
         if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(S[i], c, alpha, L.slot_path[sl * kLanes + lane]);
+        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha,
+                                                L.slot_path[sl * kLanes + lane]);
         double trim = 0.0;
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
@@ -287,7 +288,7 @@ cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch&
     const unsigned gl = grid_for(lanes, kThreads);
     const unsigned ge = grid_for(L.E, kThreads);
     cudaError_t err;
-    const unsigned gd = grid_for((long long)L.nblocks * (kLanes / L.G), kThreads);
+    const unsigned gd = grid_for((long long)L.nblocks * L.dpb, kThreads);
     for (int round = 0; round < 2; ++round) {
         k_clamp_sum<<<gd, kThreads, 0, st>>>(L, x, s.S);
         if ((err = cudaMemsetAsync(s.loads, 0, sizeof(double) * (size_t)L.E, st)) != cudaSuccess) return err;

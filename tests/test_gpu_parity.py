@@ -169,11 +169,11 @@ def test_int32_edge_ids(te):
     inst = Instance("many-edges", 2, src, dst, cap, np.zeros(K, np.int32), np.ones(K, np.int32),
                     rng.uniform(0.5, 3.0, K), dpo, np.arange(P + 1, dtype=np.int64), pe, {})
     kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
-    # the iteration kernel keeps its edge tiles in shared memory, which caps
-    # the edge count well below the 32-bit id range: te_create says so
+    # the iteration kernel takes 16-bit edge ids and keeps its edge tiles in
+    # shared memory: te_create refuses such instances with a clear message
     with pytest.raises(te.TEError) as ei:
         te.TE(inst, **kw)
-    assert ei.value.status == te.TE_EUNSUPPORTED and "shared memory" in str(ei.value)
+    assert ei.value.status == te.TE_EUNSUPPORTED and "edge" in str(ei.value)
 
 
 def test_parking_lot_closed_form_on_gpu(te):

@@ -73,7 +73,7 @@ struct te_handle {
     float* w = nullptr;       // [E]
     float* u_next = nullptr;  // [E]
     float* w_next = nullptr;  // [E]
-    float* loads = nullptr;   // [2E]
+    float* loads = nullptr;   // [grid*E] per-CTA partial loads
     double* part = nullptr;   // [2*grid*4]
     unsigned* barrier = nullptr;
     int* status = nullptr;
@@ -416,6 +416,10 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     if ((st = h->cuda(te::iter_occupancy(G, E, nsm, &bps), "occupancy query"))) return bail(st);
     if (bps < 1) { h->err = "iteration kernel does not fit on an SM"; return bail(TE_EUNSUPPORTED); }
     h->grid = nsm * bps;
+    if ((E + h->grid - 1) / h->grid > te::kIterThreads) {  // one edge of a CTA's price slice per thread
+        h->err = "too many edges per CTA price slice";
+        return bail(TE_EUNSUPPORTED);
+    }
     std::vector<int> cta_blk(h->grid + 1, nblocks);
     {
         std::vector<long long> cost(nblocks);
@@ -466,7 +470,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->w, sizeof(float) * E));
     A(h->alloc(&h->u_next, sizeof(float) * E));
     A(h->alloc(&h->w_next, sizeof(float) * E));
-    A(h->alloc(&h->loads, sizeof(float) * 2 * (size_t)E));
+    A(h->alloc(&h->loads, sizeof(float) * (size_t)h->grid * (size_t)E));
     A(h->alloc(&h->part, sizeof(double) * 2 * 4 * (size_t)h->grid));
     A(h->alloc(&h->barrier, sizeof(unsigned)));
     A(h->alloc(&h->status, sizeof(int)));
@@ -582,7 +586,6 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* 
         if (chunk <= 0) break;
         cudaError_t ce = cudaSuccess;
         auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
-        A(cudaMemsetAsync(h->loads, 0, sizeof(float) * 2 * (size_t)h->L.E, s));
         A(cudaMemsetAsync(h->barrier, 0, sizeof(unsigned), s));
         A(cudaMemsetAsync(h->status, 0, sizeof(int), s));
         te::IterArgs a{};

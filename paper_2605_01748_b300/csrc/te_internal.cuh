@@ -98,7 +98,7 @@ struct IterArgs {
     float* w;              // [E] u + d (gather weights), in/out
     float* u_next;         // [E] scratch: prices published for a beta rescale
     float* w_next;         // [E] scratch: gather weights published each iteration
-    float* loads;          // [2*E] edge-load accumulators (zeroed before launch)
+    float* loads;          // [grid*E] per-CTA partial edge loads
     double* part;          // [2*grid*4] per-CTA residual partials
     unsigned* barrier;     // grid barrier counter (zeroed before launch)
     int* status;           // device status word (0 ok)

@@ -11,13 +11,15 @@
 //            edge ids of a block are brought into shared memory by one bulk
 //            asynchronous copy (TMA), issued one block ahead of use; the
 //            block's metadata record is loaded two blocks ahead.  The CTA then
-//            flushes its histogram into the global load vector and publishes
-//            its FP64 residual partials;
+//            publishes its per-edge partial loads and its FP64 residual
+//            partials;
 //   grid barrier 1;
-//   phase B (every CTA, its own slice of the edges): the per-edge price
-//            update u_e' = max(0, u_e + (L_e - C_e)/n_e) (Eqs. 9/13 after the
-//            per-edge collapse of the consensus duals) and its part of the
-//            primal residual; publishes the new gather weights;
+//   phase B (every CTA, its own slice of the edges): the loads L_e as FP64
+//            sums of the CTAs' partials in a fixed order (so a run is
+//            deterministic), the per-edge price update
+//            u_e' = max(0, u_e + (L_e - C_e)/n_e) (Eqs. 9/13 after the per-edge
+//            collapse of the consensus duals) and its part of the primal
+//            residual; publishes the new gather weights;
 //   grid barrier 2;
 //   control (every CTA, identically): the residuals r and s (Eqs. 15-16,
 //            cross-CTA sums in FP64 in a fixed order), residual balancing
@@ -398,7 +400,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     __shared__ __align__(8) unsigned long long s_mbar[kIterWarps * 2];
     __shared__ double red[kIterWarps];
     __shared__ double s_fin[4];
-    __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int b_lo = a.cta_blk[blockIdx.x], b_hi = a.cta_blk[blockIdx.x + 1];
@@ -417,7 +418,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         w_s[E] = 0.f;
         h_hi[E] = 0u;
         h_lo[E] = 0u;
-        s_next = 0;
     }
     if (lane == 0) {
         mbar_init(&mb[0], 1);
@@ -446,15 +446,18 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         KSum ds2, x2, ex2;
 
         // ---------------- phase A: per-demand rate updates ----------------
-        // Blocks of this CTA's range are taken one at a time from a shared
-        // counter.  The metadata record of the block after next is loaded
-        // (by lane 0) while the bulk copy of the next block's ids runs and
-        // the current block is processed.
+        // Warp w of the CTA takes blocks b_lo + w, b_lo + w + kIterWarps, ...
+        // (a fixed assignment, so that the residual partial sums, and with
+        // them beta and the stop rule, do not depend on warp scheduling).
+        // The metadata record of the block after next is loaded (by lane 0)
+        // while the bulk copy of the next block's ids runs and the current
+        // block is processed.
         {
+            int nxt = b_lo + warp;
             auto grab = [&]() -> int {
-                int v = 0;
-                if (lane == 0) v = atomicAdd(&s_next, 1);
-                return __shfl_sync(0xffffffffu, v, 0) + b_lo;
+                const int v = nxt;
+                nxt += kIterWarps;
+                return v;
             };
             auto load_meta = [&](int b) -> BlockMeta {
                 BlockMeta m{0u, 0u, 0u, 0u};
@@ -516,12 +519,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
             }
         }
         __syncthreads();
-        if (tid == 0) s_next = 0;
-        // flush this CTA's loads into the global accumulator of this iteration
-        float* Lg = a.loads + (size_t)(it & 1) * E;
+        // publish this CTA's partial loads
+        float* Lp = a.loads + (size_t)blockIdx.x * E;
         for (int e = tid; e < E; e += kIterThreads) {
             const unsigned hi = h_hi[e], lo = h_lo[e];
-            if ((hi | lo) != 0u) atomicAdd(&Lg[e], (float)((double)hi * 0x1p-12 + (double)lo * 0x1p-24));
+            __stcg(&Lp[e], (float)((double)hi * 0x1p-12 + (double)lo * 0x1p-24));
             h_hi[e] = 0u;
             h_lo[e] = 0u;
         }
@@ -544,12 +546,34 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
 
         // ---------------- phase B: this CTA's slice of the edge prices ----------------
         {
+            // L_e of the slice: the CTAs' partials summed in FP64 in CTA
+            // order; thread t adds the partials of CTAs c = t / ns, t / ns +
+            // kIterThreads / ns, ... for edge e_lo + t % ns, then each edge's
+            // per-thread sums are combined in thread order
+            const int ns = e_hi - e_lo;
+            double* s_L = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(s_un + ns) + 7) &
+                                                    ~uintptr_t(7));  // [kIterThreads] doubles
+            if (ns > 0) {
+                const int per = kIterThreads / ns > 0 ? kIterThreads / ns : 1;
+                double acc = 0.0;
+                if (tid < per * ns) {
+                    const int e = e_lo + tid % ns;
+                    for (int c = tid / ns; c < NG; c += per) acc += (double)__ldcg(&a.loads[(size_t)c * E + e]);
+                }
+                s_L[tid] = acc;
+                __syncthreads();
+                if (tid < ns) {
+                    double L = 0.0;
+                    for (int k = 0; k < per; ++k) L += s_L[k * ns + tid];
+                    s_L[tid] = L;  // each slot read and written by its own thread only
+                }
+                __syncthreads();
+            }
             KSum r2;
             for (int e = e_lo + tid; e < e_hi; e += kIterThreads) {
                 const float ne = __ldg(&a.L.ne_f[e]);
                 const float u = s_u[e - e_lo];
-                const float L = __ldcg(&Lg[e]);
-                __stcg(&Lg[e], 0.f);  // ready for iteration it + 2
+                const float L = (float)s_L[e - e_lo];
                 float un = 0.f;
                 if (ne > 0.f) un = fmaxf(0.f, fmaf(L - __ldg(&a.L.cap_n[e]), __ldg(&a.L.inv_ne[e]), u));
                 const float d = un - u;
@@ -711,6 +735,8 @@ size_t iter_smem_bytes(int E, int grid) {
     b += (size_t)kIterWarps * 2 * kStageRows * kLanes * sizeof(uint16_t);
     const int slice = (E + grid - 1) / (grid > 0 ? grid : 1) + 1;
     b += 2 * (size_t)slice * sizeof(float);
+    b = (b + 7) & ~size_t(7);
+    b += (size_t)kIterThreads * sizeof(double);
     return b;
 }
 

@@ -235,3 +235,19 @@ def test_warm_start_and_reset(te, tiny):
     t.warm_start(x_warm)
     np.testing.assert_allclose(t.allocation(project=False), x_warm, rtol=1e-6, atol=1e-6)
     t.close()
+
+
+def test_runs_are_bit_identical(te, medium):
+    """Edge loads and residuals are reduced in a fixed order, so two solves of
+    the same instance with the same options give the same bits (iterate,
+    prices, residuals, step size and iteration count)."""
+    outs = []
+    for _ in range(2):
+        t = te.TE(medium)
+        res = t.solve(400)
+        outs.append((t.allocation(project=False), t.prices(), res))
+        t.close()
+    (x0, p0, r0), (x1, p1, r1) = outs
+    assert r0 == r1
+    assert np.array_equal(x0.view(np.uint32), x1.view(np.uint32))
+    assert np.array_equal(np.asarray(p0).view(np.uint64), np.asarray(p1).view(np.uint64))

@@ -13,6 +13,8 @@ Functions (all FP64; paper references are to GATE, Section 3 and Appendix B):
 * :func:`run_expanded` -- the same iteration with every consensus copy
   y_{e,r} and dual u_{e,r} kept per incidence (Eqs. 5-7, 10, 13).
 * :func:`project` -- the feasibility projection (Algorithm 2).
+* :func:`project_scale` -- a proportional feasibility scaling (not in the
+  paper; scales where Algorithm 2 trims whole paths).
 * :func:`gap` -- the Lagrangian duality gap of a feasible allocation.
 * :func:`optimality` -- the optimality metric of Section 4.1.
 """
@@ -83,6 +85,8 @@ def _L() -> ctypes.CDLL:
                                         ctypes.c_int64]
         lib.or_project.restype = None
         lib.or_project.argtypes = [P, P, ctypes.c_double]
+        lib.or_project_scale.restype = None
+        lib.or_project_scale.argtypes = [P, P]
         lib.or_gap.restype = ctypes.c_double
         lib.or_gap.argtypes = [P, P, P, ctypes.c_double, P, P]
         lib.or_utility.restype = ctypes.c_double
@@ -215,6 +219,16 @@ def project(inst, x: np.ndarray, alpha: float) -> np.ndarray:
     v = _InstanceView(inst)
     out = np.array(x, dtype=np.float64, copy=True)
     _L().or_project(ctypes.byref(v.s), out.ctypes.data, float(alpha))
+    return out
+
+
+def project_scale(inst, x: np.ndarray) -> np.ndarray:
+    """Proportional feasibility scaling (not in the paper) on a copy of x
+    (caller units): clamp at 0, scale each over-served demand down to D_c,
+    then scale each path by min over its edges of min(1, C_e / L_e)."""
+    v = _InstanceView(inst)
+    out = np.array(x, dtype=np.float64, copy=True)
+    _L().or_project_scale(ctypes.byref(v.s), out.ctypes.data)
     return out
 
 

@@ -41,8 +41,9 @@
  * Values are normalised by scale = max_e C_e (the alpha-fair argmax is
  * invariant to a common scaling of C and D).
  *
- * Also here: the feasibility projection (Algorithm 2) and the duality gap of
- * a feasible allocation.  Parallel loops (OpenMP) run over independent
+ * Also here: the feasibility projection (Algorithm 2), a proportional
+ * feasibility scaling (not in the paper) and the duality gap of a feasible
+ * allocation.  Parallel loops (OpenMP) run over independent
  * demands or edges only, so results do not depend on the thread count.
  */
 #include <math.h>
@@ -538,6 +539,41 @@ void or_project(const or_instance* I, double* x, double alpha) {
     free(eb); free(trim); free(pd);
     csc_free(&T);
     free(S); free(L); free(Cp);
+}
+
+/* ------------------------------------------------------------------ */
+/* Proportional feasibility scaling -- not in the paper: an alternative  */
+/* to Algorithm 2 that scales instead of trimming, so that no demand    */
+/* with a positive rate loses all of it.  x[P] in/out (units of cap and  */
+/* demand):                                                              */
+/*   1. x <- max(x, 0)                                                   */
+/*   2. every path of a demand with S_c > D_c is scaled by D_c / S_c     */
+/*   3. with L_e the loads after step 2 and f_e = min(1, C_e / L_e),     */
+/*      every path is scaled by the smallest f_e over its edges          */
+/* After step 3, L_e' <= f_e L_e <= C_e and S_c' <= S_c <= D_c.          */
+/* ------------------------------------------------------------------ */
+void or_project_scale(const or_instance* I, double* x) {
+    const int E = I->n_edges;
+    const int64_t P = I->n_paths;
+    for (int64_t r = 0; r < P; ++r) if (!(x[r] > 0.0)) x[r] = 0.0;
+    for (int32_t c = 0; c < I->n_demands; ++c) {
+        double S = 0.0;
+        for (int64_t r = I->dpo[c]; r < I->dpo[c + 1]; ++r) S += x[r];
+        if (S > I->demand[c]) {
+            const double g = I->demand[c] / S;
+            for (int64_t r = I->dpo[c]; r < I->dpo[c + 1]; ++r) x[r] *= g;
+        }
+    }
+    double* L = (double*)calloc((size_t)(E > 0 ? E : 1), sizeof(double));
+    for (int64_t r = 0; r < P; ++r)
+        for (int64_t i = I->peo[r]; i < I->peo[r + 1]; ++i) L[I->pe[i]] += x[r];
+    for (int e = 0; e < E; ++e) L[e] = (L[e] > I->cap[e]) ? I->cap[e] / L[e] : 1.0;  /* f_e */
+    for (int64_t r = 0; r < P; ++r) {
+        double g = 1.0;
+        for (int64_t i = I->peo[r]; i < I->peo[r + 1]; ++i) g = fmin(g, L[I->pe[i]]);
+        x[r] *= g;
+    }
+    free(L);
 }
 
 /* ------------------------------------------------------------------ */

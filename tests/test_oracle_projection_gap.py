@@ -112,3 +112,52 @@ def test_gap_tight_at_lp_optimum(tiny):
     # a wrong price (all zero) must show a large gap
     g0, _, _ = O.gap(tiny, x, np.zeros(tiny.n_edges), 0.0)
     assert g0 > 1e-2 * abs(pr)
+
+
+# ---------------- proportional feasibility scaling (not in the paper) ----------------
+
+def test_project_scale_postconditions(tiny):
+    rng = np.random.default_rng(11)
+    for _ in range(5):
+        x = _perturbed(tiny, rng)
+        xp = O.project_scale(tiny, x)
+        assert (xp >= 0).all()
+        assert (O.demand_totals(tiny, xp) <= tiny.demand * (1 + 1e-12)).all()
+        assert (O.edge_loads(tiny, xp) <= tiny.capacity * (1 + 1e-12)).all()
+        # scaling only: every path keeps a fraction in (0, 1] of max(x, 0)
+        xc = np.maximum(x, 0)
+        assert (xp <= xc * (1 + 1e-15)).all()
+        assert ((xp > 0) == (xc > 0)).all()
+
+
+def test_project_scale_keeps_feasible_points(tiny):
+    rng = np.random.default_rng(13)
+    x = O.project_scale(tiny, _perturbed(tiny, rng))
+    x = x * (1 - 1e-9)  # strictly inside: no factor may fire
+    assert np.array_equal(O.project_scale(tiny, x), x)
+
+
+def test_project_scale_hand_example():
+    """Same instance as the Algorithm 2 example, x = (1, 0.5, 1, 0.75).
+    Demand A: S_A = 2.5 > 2 -> factor 0.8: (a0, a1, a2) = (0.8, 0.4, 0.8).
+    Loads: e0 = a0 + a1 + b0 = 1.95 > 1 -> f_e0 = 1/1.95; e1 = a1 + b0 =
+    1.15 <= 10; e2 = a2 = 0.8 <= 10.  Paths through e0 (a0, a1, b0) are
+    scaled by 1/1.95, a2 is kept: x = (0.8, 0.4, 0.8*1.95, 0.75) / 1.95."""
+    inst, x, _ = _two_demand_example()
+    want = np.array([0.8 / 1.95, 0.4 / 1.95, 0.8, 0.75 / 1.95])
+    got = O.project_scale(inst, x)
+    assert np.allclose(got, want, rtol=1e-15, atol=0)
+    assert abs(O.edge_loads(inst, got)[0] - 1.0) <= 1e-15
+
+
+def test_project_scale_uses_smallest_edge_factor():
+    """A path on two violated edges takes the smaller factor of the two.
+    Edges e0 (C=1), e1 (C=1); p0 = [e0, e1], p1 = [e0], p2 = [e1];
+    x = (1, 1, 3): L_e0 = 2 -> 1/2, L_e1 = 4 -> 1/4.  p0 -> 1/4, p1 -> 1/2,
+    p2 -> 3/4; loads end at e0 = 0.75, e1 = 1."""
+    inst = Instance("two-edges", 3, np.array([0, 1], np.int32), np.array([1, 2], np.int32), np.ones(2),
+                    np.array([0, 0, 1], np.int32), np.array([2, 1, 2], np.int32), np.array([5.0, 5.0, 5.0]),
+                    np.arange(4, dtype=np.int64), np.array([0, 2, 3, 4], np.int64),
+                    np.array([0, 1, 0, 1], np.int32), {})
+    xp = O.project_scale(inst, np.array([1.0, 1.0, 3.0]))
+    assert np.allclose(xp, [0.25, 0.5, 0.75], rtol=0, atol=1e-15)

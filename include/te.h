@@ -145,11 +145,25 @@ te_status te_create(const te_topology* topo, const te_paths* paths, const double
  * TE_ECUDA. */
 te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* out);
 
+/* Feasibility step applied by te_allocation. */
+enum {
+    TE_PROJECT_NONE = 0,  /* the raw iterate (may violate S_c <= D_c, L_e <= C_e) */
+    TE_PROJECT_ALG2 = 1,  /* Algorithm 2: non-negativity, demand trims, capacity
+                             trims of whole paths in descending S_c^alpha * C_p */
+    TE_PROJECT_SCALE = 2  /* not in the paper: non-negativity, each over-served
+                             demand scaled to D_c, then each path scaled by the
+                             smallest min(1, C_e / L_e) over its edges; never
+                             empties a demand that has a positive rate */
+};
+
 /* Writes the current rates in the caller's path order and units to x_out
- * [n_paths] (FP32).  project = 1 first applies the feasibility projection of
- * Algorithm 2 (non-negativity, demand trims, capacity trims in descending
- * score S_c^alpha * C_p) to a copy; the iterate itself is not changed.
- * out_is_device selects whether x_out is a device or a host pointer. */
+ * [n_paths] (FP32).  project (TE_PROJECT_*) selects the feasibility step,
+ * applied to a copy; the iterate itself is not changed.  Both feasibility
+ * steps sum in FP64 and round their trims and factors toward zero, so the
+ * FP32 result satisfies the constraints up to the FP32 rounding of the
+ * conversion to caller units.  out_is_device selects whether x_out is a
+ * device or a host pointer.  Errors: TE_EINVAL (NULL pointer, unknown
+ * project), TE_ECUDA. */
 te_status te_allocation(te_handle* h, float* x_out, int32_t project, int32_t out_is_device);
 
 /* Duality gap of the projected allocation x^ (caller units, FP64): the

@@ -645,16 +645,21 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* 
 }
 
 extern "C" te_status te_allocation(te_handle* h, float* x_out, int32_t project, int32_t out_is_device) {
-    if (!h || !x_out) return TE_EINVAL;
+    if (!h || !x_out || project < TE_PROJECT_NONE || project > TE_PROJECT_SCALE) return TE_EINVAL;
     cudaStream_t s = h->stream;
     const size_t ns = (size_t)h->L.nslots * kLanes;
     const float* src = h->x + (size_t)h->hsc.xbuf * ns;
     cudaError_t ce = cudaSuccess;
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
-    if (project) {
+    if (project != TE_PROJECT_NONE) {
         A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
-        A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
-        h->launches += te::kProjectLaunches;
+        if (project == TE_PROJECT_ALG2) {
+            A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
+            h->launches += te::kProjectLaunches;
+        } else {
+            A(te::launch_project_scale(h->L, h->xtmp, h->ps, s));
+            h->launches += te::kProjectScaleLaunches;
+        }
         src = h->xtmp;
     }
     float* dst = out_is_device ? x_out : h->user;

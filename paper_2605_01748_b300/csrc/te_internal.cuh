@@ -139,6 +139,12 @@ struct ProjScratch {
 cudaError_t launch_project(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st);
 constexpr int kProjectLaunches = 26;  // kernels launch_project issues
 
+// Proportional feasibility scaling (not in the paper): x <- max(x, 0); every
+// demand with S_c > D_c scaled by D_c / S_c; then every path by the smallest
+// min(1, C_e / L_e) over its edges.  Uses S, loads and rem of the scratch.
+cudaError_t launch_project_scale(const Layout& L, float* x, const ProjScratch& s, cudaStream_t st);
+constexpr int kProjectScaleLaunches = 5;
+
 // Gather a sliced array to caller path order, times scale.
 cudaError_t launch_to_user(const Layout& L, const float* x, float* out, float scale, cudaStream_t st);
 cudaError_t launch_from_user(const Layout& L, const float* in, float* x, float inv_scale, cudaStream_t st);

@@ -282,6 +282,75 @@ __global__ void k_from_user(Layout L, const float* in, float* x, float inv_scale
     }
 }
 
+// ---------------- proportional feasibility scaling (not in the paper) ----------------
+// te_allocation with project = 2: every over-served demand is scaled to D_c,
+// then every path by the smallest min(1, C_e / L_e) over its edges.  The
+// factors are rounded toward zero (FP64 quotient, its FP32 conversion, and
+// the FP32 product), so the FP32 result never exceeds a bound the exact
+// scaling meets.
+
+// x <- x * D_c / S_c on every path of a demand with S_c > D_c.  One thread
+// per demand.
+__global__ void k_demand_scale(Layout L, float* x, const double* S) {
+    const int DPB = L.dpb;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * DPB) return;
+    const double D = (double)L.Dn[i];
+    if (!(S[i] > D)) return;
+    const float g = __double2float_rz(__ddiv_rz(D, S[i]));
+    const int b = (int)(i / DPB), t = (int)(i % DPB);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    for (int hh = 0; hh < L.G; ++hh)
+        for (int j = 0; j < KB; ++j) {
+            float* q = &x[(size_t)(s0 + j) * kLanes + t * L.G + hh];
+            *q = __fmul_rz(*q, g);
+        }
+}
+
+// f_e = min(1, C_e / L_e).
+__global__ void k_edge_factor(Layout L, const double* loads, double* f) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= L.E) return;
+    const double C = (double)L.cap_n[e];
+    f[e] = loads[e] > C ? __ddiv_rz(C, loads[e]) : 1.0;
+}
+
+// x_p <- x_p * min_{e in p} f_e.  One thread per lane of a block.
+template <typename IdT>
+__global__ void k_path_scale(Layout L, float* x, const double* f) {
+    const IdT* ids = ids_of<IdT>(L);
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    for (int j = 0; j < KB; ++j) {
+        const size_t sl = (size_t)(s0 + j);
+        const float v = x[sl * kLanes + lane];
+        if (v == 0.f) continue;
+        double g = 1.0;
+        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+            const IdT id = ids[(size_t)r * kLanes + lane];
+            if ((int)id != L.E) g = fmin(g, f[id]);
+        }
+        if (g < 1.0) x[sl * kLanes + lane] = __fmul_rz(v, __double2float_rz(g));
+    }
+}
+
+template <typename IdT>
+cudaError_t project_scale_t(const Layout& L, float* x, const ProjScratch& s, cudaStream_t st) {
+    const unsigned gl = grid_for((long long)L.nblocks * kLanes, kThreads);
+    const unsigned ge = grid_for(L.E, kThreads);
+    const unsigned gd = grid_for((long long)L.nblocks * L.dpb, kThreads);
+    cudaError_t err;
+    k_clamp_sum<<<gd, kThreads, 0, st>>>(L, x, s.S);
+    k_demand_scale<<<gd, kThreads, 0, st>>>(L, x, s.S);
+    if ((err = cudaMemsetAsync(s.loads, 0, sizeof(double) * (size_t)L.E, st)) != cudaSuccess) return err;
+    k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
+    k_edge_factor<<<ge, kThreads, 0, st>>>(L, s.loads, s.rem);
+    k_path_scale<IdT><<<gl, kThreads, 0, st>>>(L, x, s.rem);
+    return cudaGetLastError();
+}
+
 template <typename IdT>
 cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st) {
     const long long lanes = (long long)L.nblocks * kLanes;
@@ -315,6 +384,11 @@ cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch&
 cudaError_t launch_project(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st) {
     if (L.id_bytes == 2) return project_t<uint16_t>(L, x, alpha, s, st);
     return project_t<int32_t>(L, x, alpha, s, st);
+}
+
+cudaError_t launch_project_scale(const Layout& L, float* x, const ProjScratch& s, cudaStream_t st) {
+    if (L.id_bytes == 2) return project_scale_t<uint16_t>(L, x, s, st);
+    return project_scale_t<int32_t>(L, x, s, st);
 }
 
 cudaError_t launch_to_user(const Layout& L, const float* x, float* out, float scale, cudaStream_t st) {

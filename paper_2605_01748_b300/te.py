@@ -25,6 +25,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("TE_LIBRARY") or os.path.join(_HERE, "libte.so")
 
 TE_OK, TE_EINVAL, TE_ENOMEM, TE_ECUDA, TE_ETIMEOUT, TE_ENUMERIC, TE_ENOTCONVERGED, TE_EUNSUPPORTED = range(8)
+# feasibility step of te_allocation: none, Algorithm 2, proportional scaling (not in the paper)
+PROJECT_NONE, PROJECT_ALG2, PROJECT_SCALE = 0, 1, 2
 STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "TE_ETIMEOUT",
                 5: "TE_ENUMERIC", 6: "TE_ENOTCONVERGED", 7: "TE_EUNSUPPORTED"}
 
@@ -200,10 +202,12 @@ def te_solve(h, max_iters: int) -> te_solve_result:
     return res
 
 
-def te_allocation(h, out, project: bool = True) -> None:
+def te_allocation(h, out, project: int = PROJECT_ALG2) -> None:
     """Writes rates (caller path order, FP32) into `out`: a NumPy float32
-    array or a torch float32 CUDA tensor of n_paths entries."""
-    _check(_lib.te_allocation(h, _ptr(out), int(bool(project)), int(_is_device(out))), h)
+    array or a torch float32 CUDA tensor of n_paths entries.  `project` is
+    one of PROJECT_NONE, PROJECT_ALG2, PROJECT_SCALE (True/False map to
+    PROJECT_ALG2/PROJECT_NONE)."""
+    _check(_lib.te_allocation(h, _ptr(out), int(project), int(_is_device(out))), h)
 
 
 def te_gap(h):
@@ -285,7 +289,7 @@ class TE:
     def solve(self, max_iters: int) -> dict:
         return te_solve(self.h, max_iters).as_dict()
 
-    def allocation(self, project: bool = True, out=None) -> np.ndarray:
+    def allocation(self, project: int = PROJECT_ALG2, out=None) -> np.ndarray:
         if out is None:
             out = np.zeros(self.n_paths, dtype=np.float32)
         te_allocation(self.h, out, project)

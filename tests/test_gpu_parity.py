@@ -251,3 +251,24 @@ def test_runs_are_bit_identical(te, medium):
     assert r0 == r1
     assert np.array_equal(x0.view(np.uint32), x1.view(np.uint32))
     assert np.array_equal(np.asarray(p0).view(np.uint64), np.asarray(p1).view(np.uint64))
+
+
+def test_project_scale_parity_and_feasibility(te, tiny, medium):
+    """Proportional feasibility scaling (te_allocation with PROJECT_SCALE)
+    against the oracle's FP64 scaling of the same raw iterate."""
+    for inst, iters in ((tiny, 25), (tiny, 200), (medium, 30), (medium, 400)):
+        t = te.TE(inst, gamma=-1.0)
+        t.solve(iters)
+        x = t.allocation(project=te.PROJECT_NONE)
+        xg = t.allocation(project=te.PROJECT_SCALE)
+        assert (xg >= 0).all()
+        # factors and products round toward zero; the FP32 conversion to
+        # caller units may add one rounding (relative 2^-24 per path)
+        assert (O.demand_totals(inst, xg) <= inst.demand * (1 + 1e-6)).all()
+        assert (O.edge_loads(inst, xg) <= inst.capacity * (1 + 1e-6)).all()
+        xo = O.project_scale(inst, x.astype(np.float64))
+        err = np.abs(xg - xo) / np.maximum(xo, 1e-6 * xo.max())
+        assert err.max() <= 1e-5, err.max()
+        # scaling never empties a demand that had a positive rate
+        assert ((O.demand_totals(inst, xg) > 0) == (O.demand_totals(inst, np.maximum(x, 0)) > 0)).all()
+        t.close()

@@ -7,10 +7,12 @@
 
 #include <algorithm>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
 #include "te.h"
+#include "te_banks.h"
 #include "te_internal.cuh"
 
 using te::kLanes;
@@ -392,6 +394,20 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
                 }
             }
         }
+    }
+    // hop order within each slot: spread every row's ids over the shared-memory banks
+    {
+        uint16_t* q = (uint16_t*)ids.data();
+        const unsigned hw = std::thread::hardware_concurrency();
+        const long long nt = std::max<long long>(1, std::min<long long>({hw ? (long long)hw : 1LL, 64LL, nslots}));
+        std::vector<std::thread> pool;
+        for (long long w = 0; w < nt; ++w)
+            pool.emplace_back([&, w]() {
+                for (long long s = w; s < nslots; s += nt)
+                    te::balance_slot_banks(q + (size_t)rowoff[s] * kLanes, (int)(rowoff[s + 1] - rowoff[s]),
+                                           (uint16_t)E);
+            });
+        for (auto& t : pool) t.join();
     }
     std::vector<float> cap_n(E), ne_f(E, 0.f), inv_ne(E, 0.f);
     {

@@ -297,9 +297,31 @@ __device__ __forceinline__ uint16_t load_id(const uint16_t* p) {
 // One block (32/G demands, G lanes each, at most 4 paths per lane): gather,
 // x-block, scatter.  bids points at the block's first id row, in shared
 // memory (STAGED) or in global memory.
+// Per-lane inputs of one block read from global memory: the lane's rates,
+// its demand and the demand's multiplier.  Loaded one block ahead of use.
+struct BlockIn {
+    float x[kMaxPathsPerLane];
+    float D, lam;
+};
+
+template <int G>
+__device__ __forceinline__ BlockIn load_block_in(const IterArgs& a, int b, int lane, int s0, int KB,
+                                                 const float* __restrict__ xin) {
+    BlockIn in;
+    const size_t di = (size_t)b * a.L.dpb + lane / G;
+    in.D = __ldg(&a.L.Dn[di]);
+    in.lam = __ldcg(&a.lam[di]);
+    #pragma unroll
+    for (int j = 0; j < kMaxPathsPerLane; ++j) {
+        in.x[j] = 0.f;
+        if (j < KB) in.x[j] = __ldcg(&xin[(size_t)(s0 + j) * kLanes + lane]);
+    }
+    return in;
+}
+
 template <int G, bool STAGED>
 __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane, const uint16_t* bids, int s0,
-                                              unsigned counts, int KB, const float* __restrict__ xin,
+                                              unsigned counts, int KB, const BlockIn& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
                                               unsigned* h_lo, float inv_beta, float logbeta,
                                               float beta_f, float alpha, KSum& ds2, KSum& x2, KSum& ex2) {
@@ -307,14 +329,11 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
     const uint16_t sentinel = (uint16_t)a.L.E;
     const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const size_t di = (size_t)b * a.L.dpb + lane / G;
-    const float D = __ldg(&a.L.Dn[di]);
-    const float lam0 = __ldcg(&a.lam[di]);
+    const float D = in.D;
+    const float lam0 = in.lam;
     float xo[KL], m[KL], an[KL];
     #pragma unroll
-    for (int j = 0; j < KL; ++j) {
-        xo[j] = 0.f;
-        if (j < KB) xo[j] = __ldcg(&xin[(size_t)(s0 + j) * kLanes + lane]);
-    }
+    for (int j = 0; j < KL; ++j) xo[j] = in.x[j];
     unsigned rs = 0;  // first row of slot j within the block
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
@@ -362,13 +381,13 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
                 const float hf = floorf(vf);
                 const unsigned hi = (unsigned)hf;
                 const unsigned lo = (unsigned)__float2uint_rn((vf - hf) * 0x1p12f);
+                // no per-row branch: padding entries (the sentinel id E) add
+                // into the unused histogram slot E
                 #pragma unroll 4
                 for (unsigned r = 0; r < cnt; ++r) {
                     const uint16_t id = load_id<STAGED>(&bids[(size_t)(rs + r) * kLanes + lane]);
-                    if (id != sentinel) {
-                        if (hi) atomicAdd(&h_hi[id], hi);
-                        atomicAdd(&h_lo[id], lo);
-                    }
+                    atomicAdd(&h_hi[id], hi);
+                    atomicAdd(&h_lo[id], lo);
                 }
             }
             rs += cnt;
@@ -449,9 +468,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         // Warp w of the CTA takes blocks b_lo + w, b_lo + w + kIterWarps, ...
         // (a fixed assignment, so that the residual partial sums, and with
         // them beta and the stop rule, do not depend on warp scheduling).
-        // The metadata record of the block after next is loaded (by lane 0)
-        // while the bulk copy of the next block's ids runs and the current
-        // block is processed.
+        // The metadata record of the block after next is loaded (by lane 0),
+        // and the next block's rates, demands and multipliers are loaded into
+        // registers, while the bulk copy of the next block's ids runs and the
+        // current block is processed.
         {
             int nxt = b_lo + warp;
             auto grab = [&]() -> int {
@@ -482,16 +502,25 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 (void)b;
                 return true;
             };
+            auto prefetch = [&](int b, const BlockMeta& m) -> BlockIn {
+                const int s0 = (int)__shfl_sync(0xffffffffu, m.s0, 0);
+                const int KB = (int)__shfl_sync(0xffffffffu, m.kb, 0);
+                BlockIn in{};
+                if (b < b_hi) in = load_block_in<G>(a, b, lane, s0, KB, xin);
+                return in;
+            };
             int b0 = grab();
             BlockMeta m0 = load_meta(b0);
             int b1 = grab();
             BlockMeta m1 = load_meta(b1);
             int cur = 0;
             bool st0 = (b0 < b_hi) && !failed ? issue(b0, m0, cur) : false;
+            BlockIn in0 = prefetch(b0, m0);
             while (b0 < b_hi && !failed) {
                 const int b2 = grab();
                 const BlockMeta m2 = load_meta(b2);
                 const bool st1 = (b1 < b_hi) ? issue(b1, m1, cur ^ 1) : false;
+                const BlockIn in1 = prefetch(b1, m1);
                 const int s0 = (int)__shfl_sync(0xffffffffu, m0.s0, 0);
                 const unsigned counts = __shfl_sync(0xffffffffu, m0.counts, 0);
                 const int KB = (int)__shfl_sync(0xffffffffu, m0.kb, 0);
@@ -503,15 +532,16 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                     }
                     par[cur] ^= 1u;
                     pending[cur] = false;
-                    process_block<G, true>(a, b0, lane, wstage[cur], s0, counts, KB, xin, xout, w_s, h_hi, h_lo,
+                    process_block<G, true>(a, b0, lane, wstage[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                            inv_beta, logbeta, beta_f, alpha, ds2, x2, ex2);
                 } else {
                     const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
-                    process_block<G, false>(a, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, xin, xout,
+                    process_block<G, false>(a, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
                                             w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, ds2, x2, ex2);
                 }
                 b0 = b1;
                 m0 = m1;
+                in0 = in1;
                 st0 = st1;
                 b1 = b2;
                 m1 = m2;

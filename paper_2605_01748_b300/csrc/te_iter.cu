@@ -129,8 +129,10 @@ __device__ __forceinline__ float slack_root(float A, float H, float logbeta, flo
         if (s > 0.f) {
             const float g = __logf(s) + (t + logbeta) * ia;
             if (g > 0.f) thi = t; else tlo = t;
-            const float dg = H * et / s + ia;
-            tn = t - g / dg;
+            // the step only has to move t towards the root: its quotients
+            // may be approximate (the accepted t still solves g(t) = 0)
+            const float dg = __fdividef(H * et, s) + ia;
+            tn = t - __fdividef(g, dg);
         } else {
             tlo = t;
             tn = 0.5f * (tlo + thi);

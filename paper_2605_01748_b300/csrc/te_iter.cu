@@ -292,7 +292,11 @@ __device__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long ti
 
 template <bool STAGED>
 __device__ __forceinline__ uint16_t load_id(const uint16_t* p) {
-    if (STAGED) return *p;
+    if (STAGED) {  // an explicit shared-memory load (the staging pointer is generic)
+        unsigned short v;
+        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(smem_u32(p)));
+        return v;
+    }
     return __ldg(p);
 }
 

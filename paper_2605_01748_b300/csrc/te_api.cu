@@ -75,13 +75,13 @@ struct te_handle {
     float* w = nullptr;       // [E]
     float* u_next = nullptr;  // [E]
     float* w_next = nullptr;  // [E]
-    float* loads = nullptr;   // [grid*E] per-CTA partial loads
+    uint2* loads = nullptr;   // [grid*E] per-CTA partial loads
     double* part = nullptr;   // [2*grid*4]
+    float* blkres = nullptr;  // [nblocks*3] per-block residual terms
     unsigned* barrier = nullptr;
     int* status = nullptr;
     te::Scalars* sc = nullptr;
     double* trace = nullptr;  // [kTraceCap*5]
-    int* cta_blk = nullptr;   // [grid+1]
     double* Dc = nullptr;     // [nblocks*dpb] caller-unit demands
     float* xtmp = nullptr;    // [nslots*32]
     float* user = nullptr;    // [P]
@@ -418,6 +418,26 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
             ne_f[e] = (float)ne[e];
             inv_ne[e] = ne[e] > 0 ? (float)(1.0 / (double)ne[e]) : 0.f;
         }
+        // range of the kernel's 32-bit fixed-point load histograms: a rate
+        // adds floor(x 2^12) and a remainder below 2^12 (units of 2^-24), and
+        // the rates of a demand sum to at most D_c, so every per-CTA sum stays
+        // below 2^32 when each edge has fewer than 2^19 paths and the demands
+        // with a path through it total less than 2^19 (normalised)
+        std::vector<double> dsum(E, 0.0);
+        std::vector<int> stamp(E, -1);
+        for (int c = 0; c < K; ++c) {
+            const double d = D[c] / scale;
+            for (long long i = P->path_edge_off[P->demand_path_off[c]]; i < P->path_edge_off[P->demand_path_off[c + 1]]; ++i) {
+                const int e = P->path_edges[i];
+                if (stamp[e] != c) { stamp[e] = c; dsum[e] += d; }
+            }
+        }
+        for (int e = 0; e < E; ++e)
+            if (ne[e] >= (1LL << 19) || dsum[e] >= (double)(1 << 19)) {
+                h->err = fmt("edge %lld: %lld paths, or the demands with a path through it, exceed the range of the "
+                             "load histograms (2^19 paths, 2^19 in normalised demand)", e, ne[e]);
+                return bail(TE_EUNSUPPORTED);
+            }
     }
 
     // ---------------- persistent grid ----------------
@@ -435,27 +455,6 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     if ((E + h->grid - 1) / h->grid > te::kIterThreads) {  // one edge of a CTA's price slice per thread
         h->err = "too many edges per CTA price slice";
         return bail(TE_EUNSUPPORTED);
-    }
-    std::vector<int> cta_blk(h->grid + 1, nblocks);
-    {
-        std::vector<long long> cost(nblocks);
-        long long total = 0;
-        for (int b = 0; b < nblocks; ++b) {
-            long long cst = 0;
-            for (int s = slotbase[b]; s < slotbase[b + 1]; ++s) cst += (long long)(rowoff[s + 1] - rowoff[s]) + 2;
-            cost[b] = cst + 1;
-            total += cost[b];
-        }
-        long long acc = 0;
-        int c = 0;
-        cta_blk[0] = 0;
-        for (int b = 0; b < nblocks && c < h->grid - 1; ++b) {
-            acc += cost[b];
-            while (c < h->grid - 1 && acc * h->grid >= (long long)(c + 1) * total) {
-                cta_blk[++c] = b + 1;
-            }
-        }
-        for (int k = c + 1; k <= h->grid; ++k) cta_blk[k] = nblocks;
     }
 
     // ---------------- device memory ----------------
@@ -486,13 +485,13 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->w, sizeof(float) * E));
     A(h->alloc(&h->u_next, sizeof(float) * E));
     A(h->alloc(&h->w_next, sizeof(float) * E));
-    A(h->alloc(&h->loads, sizeof(float) * (size_t)h->grid * (size_t)E));
+    A(h->alloc(&h->loads, sizeof(uint2) * (size_t)h->grid * (size_t)E));
     A(h->alloc(&h->part, sizeof(double) * 2 * 4 * (size_t)h->grid));
+    A(h->alloc(&h->blkres, sizeof(float) * 3 * (size_t)nblocks));
     A(h->alloc(&h->barrier, sizeof(unsigned)));
     A(h->alloc(&h->status, sizeof(int)));
     A(h->alloc(&h->sc, sizeof(te::Scalars)));
     A(h->alloc(&h->trace, sizeof(double) * te::kTraceWidth * kTraceCap));
-    A(h->alloc(&h->cta_blk, sizeof(int) * cta_blk.size()));
     A(h->alloc(&h->xtmp, sizeof(float) * ns));
     A(h->alloc(&h->user, sizeof(float) * (size_t)NP));
     A(h->alloc(&h->gacc, sizeof(double) * 4));
@@ -527,7 +526,6 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(cudaMemcpyAsync(d_cap, cap_n.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_ne, ne_f.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_inv, inv_ne.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(h->cta_blk, cta_blk.data(), sizeof(int) * cta_blk.size(), cudaMemcpyHostToDevice, s));
     if (ce != cudaSuccess) {
         h->err = std::string("copy to device failed: ") + cudaGetErrorString(ce);
         return bail(TE_ECUDA);
@@ -612,12 +610,12 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* 
         a.w = h->w;
         a.loads = h->loads;
         a.part = h->part;
+        a.blkres = h->blkres;
         a.barrier = h->barrier;
         a.status = h->status;
         a.sc = h->sc;
         a.trace = h->trace;
         a.trace_cap = kTraceCap;
-        a.cta_blk = h->cta_blk;
         a.lam = h->lam;
         a.u_next = h->u_next;
         a.w_next = h->w_next;

@@ -98,14 +98,14 @@ struct IterArgs {
     float* w;              // [E] u + d (gather weights), in/out
     float* u_next;         // [E] scratch: prices published for a beta rescale
     float* w_next;         // [E] scratch: gather weights published each iteration
-    float* loads;          // [grid*E] per-CTA partial edge loads
+    uint2* loads;          // [grid*E] per-CTA partial edge loads (fixed point: 2^-12 and 2^-24 units)
     double* part;          // [2*grid*4] per-CTA residual partials
+    float* blkres;         // [nblocks*3] per-block residual terms
     unsigned* barrier;     // grid barrier counter (zeroed before launch)
     int* status;           // device status word (0 ok)
     Scalars* sc;           // in/out
     double* trace;         // [trace_cap*5] ring
     long long trace_cap;
-    const int* cta_blk;    // [grid+1] block range of each CTA
     float* lam;            // [nblocks*dpb] previous multiplier lambda = beta*nu of each demand
     long long max_iters;
     long long timeout_ns;  // bound on every wait (grid barrier, bulk copy)

@@ -330,7 +330,7 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
                                               unsigned counts, int KB, const BlockIn& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
                                               unsigned* h_lo, float inv_beta, float logbeta,
-                                              float beta_f, float alpha, KSum& ds2, KSum& x2, KSum& ex2) {
+                                              float beta_f, float alpha) {
     constexpr int KL = kMaxPathsPerLane;
     const uint16_t sentinel = (uint16_t)a.L.E;
     const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -399,9 +399,21 @@ __device__ __forceinline__ void process_block(const IterArgs& a, int b, int lane
             rs += cnt;
         }
     }
-    ds2.add(bd);
-    x2.add(bx);
-    ex2.add(be);
+    // the block's residual terms, summed over the warp in a fixed order and
+    // stored per block, so that their totals do not depend on which warp
+    // processed which block
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bd += __shfl_xor_sync(0xffffffffu, bd, o);
+        bx += __shfl_xor_sync(0xffffffffu, bx, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+    }
+    if (lane == 0) {
+        float* r = a.blkres + (size_t)b * 3;
+        __stcg(&r[0], bd);
+        __stcg(&r[1], bx);
+        __stcg(&r[2], be);
+    }
 }
 
 __device__ __forceinline__ unsigned rows_of(unsigned counts) {
@@ -425,9 +437,13 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     __shared__ __align__(8) unsigned long long s_mbar[kIterWarps * 2];
     __shared__ double red[kIterWarps];
     __shared__ double s_fin[4];
+    __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int b_lo = a.cta_blk[blockIdx.x], b_hi = a.cta_blk[blockIdx.x + 1];
+    // blocks of this CTA: blockIdx.x, blockIdx.x + NG, ... (round robin, so
+    // that every CTA gets a sample of all kinds of blocks)
+    const int b_hi = a.L.nblocks;  // block indices >= b_hi mean "none"
+    const int nbc = blockIdx.x < (unsigned)b_hi ? (b_hi - (int)blockIdx.x + NG - 1) / NG : 0;
     const uint16_t* ids = static_cast<const uint16_t*>(a.L.ids);
     uint16_t* wstage[2] = {stage + (size_t)(warp * 2) * kStageRows * kLanes,
                            stage + (size_t)(warp * 2 + 1) * kStageRows * kLanes};
@@ -443,6 +459,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         w_s[E] = 0.f;
         h_hi[E] = 0u;
         h_lo[E] = 0u;
+        s_next = 0;
     }
     if (lane == 0) {
         mbar_init(&mb[0], 1);
@@ -468,22 +485,22 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         const float logbeta = (float)log(sc.beta);
         const float beta_f = (float)sc.beta;
         const float alpha = (float)sc.alpha;
-        KSum ds2, x2, ex2;
 
         // ---------------- phase A: per-demand rate updates ----------------
-        // Warp w of the CTA takes blocks b_lo + w, b_lo + w + kIterWarps, ...
-        // (a fixed assignment, so that the residual partial sums, and with
-        // them beta and the stop rule, do not depend on warp scheduling).
+        // Warps take the blocks of this CTA one at a time from a shared
+        // counter (results do not depend on which warp takes which block:
+        // the loads are integer sums and the residual terms are stored per
+        // block).
         // The metadata record of the block after next is loaded (by lane 0),
         // and the next block's rates, demands and multipliers are loaded into
         // registers, while the bulk copy of the next block's ids runs and the
         // current block is processed.
         {
-            int nxt = b_lo + warp;
             auto grab = [&]() -> int {
-                const int v = nxt;
-                nxt += kIterWarps;
-                return v;
+                int v = 0;
+                if (lane == 0) v = atomicAdd(&s_next, 1);
+                v = __shfl_sync(0xffffffffu, v, 0);
+                return v < nbc ? (int)blockIdx.x + v * NG : b_hi;
             };
             auto load_meta = [&](int b) -> BlockMeta {
                 BlockMeta m{0u, 0u, 0u, 0u};
@@ -539,11 +556,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                     par[cur] ^= 1u;
                     pending[cur] = false;
                     process_block<G, true>(a, b0, lane, wstage[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
-                                           inv_beta, logbeta, beta_f, alpha, ds2, x2, ex2);
+                                           inv_beta, logbeta, beta_f, alpha);
                 } else {
                     const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
                     process_block<G, false>(a, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
-                                            w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, ds2, x2, ex2);
+                                            w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha);
                 }
                 b0 = b1;
                 m0 = m1;
@@ -555,18 +572,28 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
             }
         }
         __syncthreads();
+        if (tid == 0) s_next = 0;  // read again only after the next barriers
         // publish this CTA's partial loads
-        float* Lp = a.loads + (size_t)blockIdx.x * E;
+        uint2* Lp = a.loads + (size_t)blockIdx.x * E;
         for (int e = tid; e < E; e += kIterThreads) {
-            const unsigned hi = h_hi[e], lo = h_lo[e];
-            __stcg(&Lp[e], (float)((double)hi * 0x1p-12 + (double)lo * 0x1p-24));
+            __stcg(&Lp[e], make_uint2(h_hi[e], h_lo[e]));
             h_hi[e] = 0u;
             h_lo[e] = 0u;
         }
         {
-            const double v0 = block_sum((double)ds2.s, red);
-            const double v1 = block_sum((double)x2.s, red);
-            const double v2 = block_sum((double)ex2.s, red);
+            // this CTA's residual partials: its blocks' terms in FP64, each
+            // thread over a fixed stride of the block range, then a fixed-order
+            // CTA reduction
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+            for (int k = tid; k < nbc; k += kIterThreads) {
+                const float* r = a.blkres + ((size_t)blockIdx.x + (size_t)k * NG) * 3;
+                t0 += (double)__ldcg(&r[0]);
+                t1 += (double)__ldcg(&r[1]);
+                t2 += (double)__ldcg(&r[2]);
+            }
+            const double v0 = block_sum(t0, red);
+            const double v1 = block_sum(t1, red);
+            const double v2 = block_sum(t2, red);
             if (tid == 0) {
                 double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * 4;
                 __stcg(&p[0], v0);
@@ -582,26 +609,35 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
 
         // ---------------- phase B: this CTA's slice of the edge prices ----------------
         {
-            // L_e of the slice: the CTAs' partials summed in FP64 in CTA
-            // order; thread t adds the partials of CTAs c = t / ns, t / ns +
-            // kIterThreads / ns, ... for edge e_lo + t % ns, then each edge's
-            // per-thread sums are combined in thread order
+            // L_e of the slice: the CTAs' integer partials summed exactly in
+            // 64 bits (so L_e does not depend on how blocks are spread over
+            // CTAs) and converted once; thread t adds the partials of CTAs
+            // c = t / ns, t / ns + kIterThreads / ns, ... for edge e_lo + t % ns
             const int ns = e_hi - e_lo;
-            double* s_L = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(s_un + ns) + 7) &
-                                                    ~uintptr_t(7));  // [kIterThreads] doubles
+            unsigned long long* s_L = reinterpret_cast<unsigned long long*>(
+                (reinterpret_cast<uintptr_t>(s_un + ns) + 7) & ~uintptr_t(7));  // [2][kIterThreads]
             if (ns > 0) {
                 const int per = kIterThreads / ns > 0 ? kIterThreads / ns : 1;
-                double acc = 0.0;
+                unsigned long long sh = 0ull, sl = 0ull;
                 if (tid < per * ns) {
                     const int e = e_lo + tid % ns;
-                    for (int c = tid / ns; c < NG; c += per) acc += (double)__ldcg(&a.loads[(size_t)c * E + e]);
+                    for (int c = tid / ns; c < NG; c += per) {
+                        const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
+                        sh += v.x;
+                        sl += v.y;
+                    }
                 }
-                s_L[tid] = acc;
+                s_L[tid] = sh;
+                s_L[kIterThreads + tid] = sl;
                 __syncthreads();
                 if (tid < ns) {
-                    double L = 0.0;
-                    for (int k = 0; k < per; ++k) L += s_L[k * ns + tid];
-                    s_L[tid] = L;  // each slot read and written by its own thread only
+                    unsigned long long H = 0ull, Lo = 0ull;
+                    for (int k = 0; k < per; ++k) {
+                        H += s_L[k * ns + tid];
+                        Lo += s_L[kIterThreads + k * ns + tid];
+                    }
+                    s_L[tid] = H;  // each slot read and written by its own thread only
+                    s_L[kIterThreads + tid] = Lo;
                 }
                 __syncthreads();
             }
@@ -609,7 +645,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
             for (int e = e_lo + tid; e < e_hi; e += kIterThreads) {
                 const float ne = __ldg(&a.L.ne_f[e]);
                 const float u = s_u[e - e_lo];
-                const float L = (float)s_L[e - e_lo];
+                const float L = (float)((double)s_L[e - e_lo] * 0x1p-12 + (double)s_L[kIterThreads + e - e_lo] * 0x1p-24);
                 float un = 0.f;
                 if (ne > 0.f) un = fmaxf(0.f, fmaf(L - __ldg(&a.L.cap_n[e]), __ldg(&a.L.inv_ne[e]), u));
                 const float d = un - u;
@@ -772,7 +808,7 @@ size_t iter_smem_bytes(int E, int grid) {
     const int slice = (E + grid - 1) / (grid > 0 ? grid : 1) + 1;
     b += 2 * (size_t)slice * sizeof(float);
     b = (b + 7) & ~size_t(7);
-    b += (size_t)kIterThreads * sizeof(double);
+    b += 2 * (size_t)kIterThreads * sizeof(unsigned long long);
     return b;
 }
 

@@ -197,8 +197,9 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
         if (S <= D) return inv_beta;  // lambda = U'(S) = 1, cap slack
         nu = fminf(nu, inv_beta);
     }
-    // log of the nu at which (beta nu)^(-1/alpha) = D
+    // the nu at which (beta nu)^(-1/alpha) = D, and its log
     const float tcap = alpha > 0.f ? -alpha * __logf(D) - logbeta : INFINITY;
+    const float nucap = alpha > 0.f ? __expf(tcap) : INFINITY;
     unsigned prev = 0u;
     bool descending = false;  // nu is a root computed from a supporting line (an upper bound)
     #pragma unroll 1
@@ -213,9 +214,9 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
                 mask |= 1u << j;
             }
         }
+        if (descending && gall<G>(mask == prev, gm)) break;  // nu is the root of this line
         A = gsum<G>(A, gm);
         H = gsum<G>(H, gm);
-        if (descending && gall<G>(mask == prev, gm)) break;  // nu is the root of this line
         if (!(H > 0.f)) {
             // nothing active at nu.  While descending this only happens when
             // the root lies on a path's breakpoint and rounding switched the
@@ -231,10 +232,7 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
             continue;
         }
         float nn = (D - A) / H;
-        if (alpha > 0.f && nn > 0.f) {
-            const float tn = __logf(nn);
-            if (tn > tcap) nn = slack_root(A, H, logbeta, alpha, tcap, tn, nu);
-        }
+        if (nn > nucap) nn = slack_root(A, H, logbeta, alpha, tcap, __logf(nn), nu);
         if (descending && !(nn < nu)) break;  // rounding: no further descent
         nu = nn;
         prev = mask;

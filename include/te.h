@@ -191,6 +191,15 @@ te_status te_set_warm_start(te_handle* h, const float* x0, int32_t in_is_device,
  * (nothing is changed then). */
 te_status te_set_demands(te_handle* h, const double* demands, int32_t in_is_device);
 
+/* Replaces the capacities C_e (edge order and caller units, [n_edges],
+ * FP64, finite and >= 0) without rebuilding the instance: a link failure is
+ * a capacity of 0 (its paths' rates go to 0 in the limit), a repair or an
+ * upgrade a new value (Section 2: TE re-runs when the network changes).
+ * in_is_device selects a device or host pointer.  The iterate, prices and
+ * alpha are kept (a warm start); call te_reset for a cold start.  Errors:
+ * TE_EINVAL if a capacity is not finite and >= 0 (nothing is changed then). */
+te_status te_set_capacities(te_handle* h, const double* capacities, int32_t in_is_device);
+
 /* Returns to the initial state of te_create. */
 te_status te_reset(te_handle* h);
 

@@ -48,6 +48,17 @@ __global__ void k_set_demands(long long nd, const int* demand_of, const double* 
     Dc[i] = D[c];
 }
 
+__global__ void k_check_capacities(int E, const double* C, int* bad) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < E && !(C[e] >= 0.0 && C[e] < INFINITY)) atomicOr(bad, 1);
+}
+
+// new capacities, normalised FP32
+__global__ void k_set_capacities(int E, const double* C, double inv_scale, float* cap_n) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < E) cap_n[e] = (float)(C[e] * inv_scale);
+}
+
 }  // namespace
 
 namespace te {
@@ -88,6 +99,8 @@ struct te_handle {
     double* gacc = nullptr;   // [3]
     double* pbuf = nullptr;   // [E]
     double* dstage = nullptr; // [K] staging of new demands
+    double* cstage = nullptr; // [E] staging of new capacities
+    float* cap_n = nullptr;   // [E] normalised capacities (the layout's copy)
     int* flag = nullptr;      // [1]
     float* lam = nullptr;     // [nblocks*dpb] warm-start multipliers
     float* Dn = nullptr;      // mutable view of L.Dn
@@ -497,6 +510,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->gacc, sizeof(double) * 4));
     A(h->alloc(&h->pbuf, sizeof(double) * E));
     A(h->alloc(&h->dstage, sizeof(double) * K));
+    A(h->alloc(&h->cstage, sizeof(double) * E));
     A(h->alloc(&h->flag, sizeof(int)));
     A(h->alloc(&h->lam, sizeof(float) * ND));
     A(h->alloc(&h->ps.S, sizeof(double) * ND));
@@ -554,6 +568,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     L.demand_of = d_demand_of;
     L.slot_path = d_slot_path;
     L.cap_n = d_cap;
+    h->cap_n = d_cap;
     L.ne_f = d_ne;
     L.inv_ne = d_inv;
     // algorithmic traffic of one iteration: the edge ids once, the rates read
@@ -808,4 +823,33 @@ extern "C" te_status te_set_demands(te_handle* h, const double* D, int32_t in_is
     A(cudaGetLastError());
     A(cudaStreamSynchronize(s));
     return h->cuda(ce, "te_set_demands");
+}
+
+extern "C" te_status te_set_capacities(te_handle* h, const double* C, int32_t in_is_device) {
+    if (!h || !C) return TE_EINVAL;
+    cudaStream_t s = h->stream;
+    const int E = h->L.E;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    if (!in_is_device) {
+        for (int e = 0; e < E; ++e)
+            if (!(C[e] >= 0.0) || !isfinite(C[e])) return h->fail(TE_EINVAL, fmt("capacity %lld is not finite and >= 0", e));
+        A(cudaMemcpyAsync(h->cstage, C, sizeof(double) * E, cudaMemcpyHostToDevice, s));
+    } else {
+        A(cudaMemcpyAsync(h->cstage, C, sizeof(double) * E, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemsetAsync(h->flag, 0, sizeof(int), s));
+        k_check_capacities<<<(E + 255) / 256, 256, 0, s>>>(E, h->cstage, h->flag);
+        h->launches += 1;
+        int bad = 0;
+        A(cudaGetLastError());
+        A(cudaMemcpyAsync(&bad, h->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        A(cudaStreamSynchronize(s));
+        if (ce != cudaSuccess) return h->cuda(ce, "te_set_capacities");
+        if (bad) return h->fail(TE_EINVAL, "a capacity is not finite and >= 0");
+    }
+    k_set_capacities<<<(E + 255) / 256, 256, 0, s>>>(E, h->cstage, 1.0 / h->scale, h->cap_n);
+    h->launches += 1;
+    A(cudaGetLastError());
+    A(cudaStreamSynchronize(s));
+    return h->cuda(ce, "te_set_capacities");
 }

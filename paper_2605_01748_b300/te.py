@@ -31,8 +31,8 @@ STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "T
                 5: "TE_ENUMERIC", 6: "TE_ENOTCONVERGED", 7: "TE_EUNSUPPORTED"}
 
 EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_gap", "te_prices",
-            "te_set_warm_start", "te_set_demands", "te_reset", "te_trace", "te_layout", "te_destroy",
-            "te_last_error", "te_gap_noalloc")
+            "te_set_warm_start", "te_set_demands", "te_set_capacities", "te_reset", "te_trace", "te_layout",
+            "te_destroy", "te_last_error", "te_gap_noalloc")
 
 
 class TEError(RuntimeError):
@@ -106,6 +106,8 @@ def _load() -> ctypes.CDLL:
     lib.te_set_warm_start.argtypes = [H, P, ctypes.c_int32, ctypes.c_int32]
     lib.te_set_demands.restype = ctypes.c_int
     lib.te_set_demands.argtypes = [H, P, ctypes.c_int32]
+    lib.te_set_capacities.restype = ctypes.c_int
+    lib.te_set_capacities.argtypes = [H, P, ctypes.c_int32]
     lib.te_reset.restype = ctypes.c_int
     lib.te_reset.argtypes = [H]
     lib.te_trace.restype = ctypes.c_int
@@ -224,9 +226,20 @@ def te_set_warm_start(h, x0, keep_duals: bool = False) -> None:
     _check(_lib.te_set_warm_start(h, _ptr(x0), int(_is_device(x0)), int(bool(keep_duals))), h)
 
 
+def _f64_host(a):
+    return a if _is_device(a) or hasattr(a, "data_ptr") else np.ascontiguousarray(a, dtype=np.float64)
+
+
 def te_set_demands(h, demands) -> None:
-    """demands: FP64 NumPy array (host) or torch float64 CUDA tensor."""
+    """demands: FP64 NumPy array (host) or torch float64 tensor (host or CUDA)."""
+    demands = _f64_host(demands)
     _check(_lib.te_set_demands(h, _ptr(demands), int(_is_device(demands))), h)
+
+
+def te_set_capacities(h, capacities) -> None:
+    """capacities: FP64 NumPy array (host) or torch float64 tensor (host or CUDA)."""
+    capacities = _f64_host(capacities)
+    _check(_lib.te_set_capacities(h, _ptr(capacities), int(_is_device(capacities))), h)
 
 
 def te_reset(h) -> None:
@@ -309,6 +322,9 @@ class TE:
 
     def set_demands(self, demands) -> None:
         te_set_demands(self.h, demands)
+
+    def set_capacities(self, capacities) -> None:
+        te_set_capacities(self.h, capacities)
 
     def reset(self) -> None:
         te_reset(self.h)

@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--target", type=float, default=0.99)
     ap.add_argument("--oracle-sample-iters", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ablation", action="store_true",
+                    help="iterations to 1%% with and without adaptive beta, and cold versus warm re-solves "
+                         "after a demand change (Section 4 factor analysis), one JSON line")
     ap.add_argument("--iters", type=int, default=0,
                     help="profiling runs only: use this K and skip the reference run and the probe")
     return ap.parse_args()
@@ -431,6 +434,97 @@ def oracle_k(inst, O, target: float, every: int, cap: int, threads: int):
     return s.iters
 
 
+def run_ablation(a):
+    """Iterations (and device time) to optimality >= 0.99 for: the default
+    solver; residual balancing off (fixed beta0); and, after every demand is
+    scaled by a seeded factor in [0.8, 1.2], a cold start, the paper's warm
+    start (previous rates, duals and alpha reset, Algorithm 1's optional x^0)
+    and a full warm start (rates, prices, beta and alpha kept).  OPT of each
+    demand matrix: its own run to the stop rule, proportionally scaled."""
+    import numpy as np
+    import torch
+    from paper_2605_01748_b300 import instances, te
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    inst = instances.make(a.workload, threads=os.cpu_count() or 0)
+    xdev = torch.empty(inst.n_paths, dtype=torch.float32, device=dev)
+    SCALE = te.PROJECT_SCALE
+
+    def reference(t):
+        t.reset()
+        r = t.solve(a.ref_iters)
+        te.te_allocation(t.h, xdev, SCALE)
+        return r
+
+    def probe(t, opt, start_iters, cap):
+        """Iterations beyond start_iters to reach the target (coarse, then fine)."""
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n, lo, ms = 0, 0, 0.0
+        while n < cap:
+            ev0.record(stream)
+            r = t.solve(a.probe_every)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            n = t.solve(0)["total_iters"] - start_iters
+            te.te_allocation(t.h, xdev, SCALE)
+            q = opt(xdev)
+            if q >= a.target:
+                return n, round(q, 5), round(ms, 1)
+            if r["converged"]:
+                return None, round(q, 5), round(ms, 1)
+        return None, round(q, 5), round(ms, 1)
+
+    out = {"mode": "ablation", "workload": workload_desc(inst), "target": a.target,
+           "probe_every": a.probe_every, "unit": "iterations (device ms of those iterations)"}
+    base = te.TE(inst, cuda_stream=stream.cuda_stream)
+    opt = Optimality(inst, dev)
+    rr = reference(base)
+    opt.set_reference(xdev)
+    out["reference_iters"] = rr["total_iters"]
+    base.reset()
+    K, q, ms = probe(base, opt, 0, rr["total_iters"])
+    out["default"] = {"iters": K, "optimality": q, "ms": ms}
+    x_at_K = torch.empty_like(xdev)
+    te.te_allocation(base.h, x_at_K, te.PROJECT_NONE)
+    # residual balancing off: beta stays at beta0
+    fixed = te.TE(inst, adapt_beta=0, cuda_stream=stream.cuda_stream)
+    Kf, qf, msf = probe(fixed, opt, 0, 3 * (K or rr["total_iters"]))
+    out["fixed_beta"] = {"iters": Kf, "optimality": qf, "ms": msf,
+                         "note": None if Kf else f"not reached within {3 * (K or rr['total_iters'])} iterations"}
+    fixed.close()
+    # demand change
+    rng = np.random.default_rng(20260)
+    D2 = inst.demand * np.exp(rng.uniform(np.log(0.8), np.log(1.2), inst.n_demands))
+    new = te.TE(instances.Instance(inst.name, inst.n_nodes, inst.edge_src, inst.edge_dst, inst.capacity,
+                                   inst.demand_src, inst.demand_dst, D2, inst.demand_path_off,
+                                   inst.path_edge_off, inst.path_edges, dict(inst.meta)),
+                cuda_stream=stream.cuda_stream)
+    opt2 = Optimality(inst, dev)
+    rr2 = reference(new)
+    opt2.set_reference(xdev)
+    new.reset()
+    Kc, qc, msc = probe(new, opt2, 0, rr2["total_iters"])
+    out["changed_demands"] = {"reference_iters": rr2["total_iters"],
+                              "cold": {"iters": Kc, "optimality": qc, "ms": msc}}
+    new.close()
+    # warm starts from the base solution at its K (the allocation in service)
+    d2 = torch.from_numpy(D2).to(dev)
+    for name, keep in (("warm_paper", False), ("warm_full", True)):
+        base.reset()
+        base.solve(K or rr["total_iters"])
+        base.set_demands(d2)
+        if not keep:
+            base.warm_start(x_at_K, keep_duals=False)
+        start = base.solve(0)["total_iters"]
+        Kw, qw, msw = probe(base, opt2, start, rr2["total_iters"])
+        out["changed_demands"][name] = {"iters": Kw, "optimality": qw, "ms": msw}
+    base.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(a, ws, rank):
     """The FP64 CPU oracle as it stands, on the host cores, same workload and
     metric.  Each step runs a bounded sample of oracle iterations on the full
@@ -485,7 +579,9 @@ def run_reference(a, ws, rank):
 def main():
     a = parse()
     ws, rank, local, dist = dist_setup()
-    if a.impl == "reference":
+    if a.ablation:
+        run_ablation(a)
+    elif a.impl == "reference":
         run_reference(a, ws, rank)
     else:
         run_ours(a, ws, rank, local, dist)

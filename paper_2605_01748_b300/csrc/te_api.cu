@@ -12,7 +12,7 @@
 #include <vector>
 
 #include "te.h"
-#include "te_banks.h"
+#include "te_layout.h"
 #include "te_internal.cuh"
 
 using te::kLanes;
@@ -298,160 +298,16 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     }
 
     // ---------------- sliced layout ----------------
-    // sort demands by (path count, lengths of the first 11 paths) so the 32
-    // demands of a block have alike path lengths and padding stays small
-    std::vector<std::pair<unsigned long long, int>> order(K);
-    int kmax = 0;
-    for (int c = 0; c < K; ++c) {
-        const long long p0 = P->demand_path_off[c], np = P->demand_path_off[c + 1] - p0;
-        kmax = std::max(kmax, (int)np);
-        unsigned long long key = (unsigned long long)np << 58;
-        for (int j = 0; j < 11 && j < np; ++j) {
-            long long len = P->path_edge_off[p0 + j + 1] - P->path_edge_off[p0 + j];
-            if (len > 31) len = 31;
-            key |= (unsigned long long)len << (53 - 5 * j);
-        }
-        order[c] = {key, c};
+    te::HostLayout hl;
+    {
+        const te_status ls = te::build_host_layout(topo, P, D, C, scale, 1, hl);
+        if (ls != TE_OK) { h->err = hl.err; return bail(ls); }
     }
-    std::sort(order.begin(), order.end());
-    // lanes per demand: no lane holds more than kMaxPathsPerLane paths
-    int G = 1;
-    while (G * te::kMaxPathsPerLane < kmax) G *= 2;
-    const int DPB = kLanes / G;  // demands per block
-    const int kl = (kmax + G - 1) / G;
-    const int nblocks = (K + DPB - 1) / DPB;
-    auto demand_at = [&](int b, int t) -> int {  // demand index of block b, position t, or -1
-        const long long q = (long long)b * DPB + t;
-        return q < K ? order[q].second : -1;
-    };
-    auto path_len = [&](int c, long long p) -> long long {
-        const long long r = P->demand_path_off[c] + p;
-        return P->path_edge_off[r + 1] - P->path_edge_off[r];
-    };
-    std::vector<int> slotbase(nblocks + 1, 0);
-    for (int b = 0; b < nblocks; ++b) {
-        int kb = 0;
-        for (int t = 0; t < DPB; ++t) {
-            const int c = demand_at(b, t);
-            if (c < 0) break;
-            const int np = (int)(P->demand_path_off[c + 1] - P->demand_path_off[c]);
-            kb = std::max(kb, (np + G - 1) / G);
-        }
-        slotbase[b + 1] = slotbase[b] + kb;
-    }
-    const long long nslots = slotbase[nblocks];
-    std::vector<unsigned> rowoff(nslots + 1, 0);
-    std::vector<te::BlockMeta> blkmeta(nblocks);
-    int max_block_rows = 0;
-    for (int b = 0; b < nblocks; ++b) {
-        const int kb = slotbase[b + 1] - slotbase[b];
-        unsigned counts = 0;
-        for (int j = 0; j < kb; ++j) {
-            long long H = 0;
-            for (int t = 0; t < DPB; ++t) {
-                const int c = demand_at(b, t);
-                if (c < 0) break;
-                const long long np = P->demand_path_off[c + 1] - P->demand_path_off[c];
-                for (int hh = 0; hh < G; ++hh) {
-                    const long long p = (long long)j * G + hh;
-                    if (p < np) H = std::max<long long>(H, path_len(c, p));
-                }
-            }
-            const long long s = slotbase[b] + j;
-            const long long next = (long long)rowoff[s] + H;
-            if (next > 0xffffffffLL) { h->err = "instance too large for the 32-bit row index"; return bail(TE_EUNSUPPORTED); }
-            rowoff[s + 1] = (unsigned)next;
-            counts |= (unsigned)H << (8 * j);
-        }
-        blkmeta[b].s0 = (unsigned)slotbase[b];
-        blkmeta[b].row0 = rowoff[slotbase[b]];
-        blkmeta[b].counts = counts;
-        blkmeta[b].kb = (unsigned)kb;
-        max_block_rows = std::max<int>(max_block_rows, (int)(rowoff[slotbase[b + 1]] - rowoff[slotbase[b]]));
-    }
-    const long long nrows = rowoff[nslots];
-    if (E + 1 > 65535) {
-        h->err = fmt("n_edges = %lld: the iteration kernel takes 16-bit edge ids (at most 65534 edges)", E);
-        return bail(TE_EUNSUPPORTED);
-    }
+    const int G = hl.G, DPB = hl.dpb, kl = hl.kl, kmax = hl.kmax, nblocks = hl.nblocks;
+    const int max_block_rows = hl.max_block_rows;
+    const long long nslots = hl.nslots, nrows = hl.nrows;
     const int id_bytes = 2;
     const size_t ND = (size_t)nblocks * DPB;  // demand slots
-    std::vector<unsigned char> ids((size_t)nrows * kLanes * id_bytes);
-    std::vector<long long> slot_path((size_t)nslots * kLanes, -1);
-    std::vector<int> demand_of(ND, -1);
-    std::vector<float> Dn(ND, 0.f);
-    std::vector<double> Dc(ND, 0.0);
-    std::vector<unsigned char> npv(ND, 0);
-    {
-        uint16_t* q = (uint16_t*)ids.data();
-        std::fill(q, q + (size_t)nrows * kLanes, (uint16_t)E);
-    }
-    for (int b = 0; b < nblocks; ++b) {
-        for (int t = 0; t < DPB; ++t) {
-            const int c = demand_at(b, t);
-            if (c < 0) break;
-            const long long p0 = P->demand_path_off[c], np = P->demand_path_off[c + 1] - p0;
-            const size_t di = (size_t)b * DPB + t;
-            demand_of[di] = c;
-            Dn[di] = (float)(D[c] / scale);
-            Dc[di] = D[c];
-            npv[di] = (unsigned char)np;
-            for (long long p = 0; p < np; ++p) {
-                const int lane = t * G + (int)(p % G);
-                const long long s = slotbase[b] + p / G, r = p0 + p;
-                slot_path[(size_t)s * kLanes + lane] = r;
-                const long long i0 = P->path_edge_off[r], n = P->path_edge_off[r + 1] - i0;
-                for (long long k = 0; k < n; ++k) {
-                    const size_t at = ((size_t)rowoff[s] + (size_t)k) * kLanes + lane;
-                    ((uint16_t*)ids.data())[at] = (uint16_t)P->path_edges[i0 + k];
-                }
-            }
-        }
-    }
-    // hop order within each slot: spread every row's ids over the shared-memory banks
-    {
-        uint16_t* q = (uint16_t*)ids.data();
-        const unsigned hw = std::thread::hardware_concurrency();
-        const long long nt = std::max<long long>(1, std::min<long long>({hw ? (long long)hw : 1LL, 64LL, nslots}));
-        std::vector<std::thread> pool;
-        for (long long w = 0; w < nt; ++w)
-            pool.emplace_back([&, w]() {
-                for (long long s = w; s < nslots; s += nt)
-                    te::balance_slot_banks(q + (size_t)rowoff[s] * kLanes, (int)(rowoff[s + 1] - rowoff[s]),
-                                           (uint16_t)E);
-            });
-        for (auto& t : pool) t.join();
-    }
-    std::vector<float> cap_n(E), ne_f(E, 0.f), inv_ne(E, 0.f);
-    {
-        std::vector<long long> ne(E, 0);
-        for (long long i = 0; i < P->nnz; ++i) ne[P->path_edges[i]]++;
-        for (int e = 0; e < E; ++e) {
-            cap_n[e] = (float)(C[e] / scale);
-            ne_f[e] = (float)ne[e];
-            inv_ne[e] = ne[e] > 0 ? (float)(1.0 / (double)ne[e]) : 0.f;
-        }
-        // range of the kernel's 32-bit fixed-point load histograms: a rate
-        // adds floor(x 2^12) and a remainder below 2^12 (units of 2^-24), and
-        // the rates of a demand sum to at most D_c, so every per-CTA sum stays
-        // below 2^32 when each edge has fewer than 2^19 paths and the demands
-        // with a path through it total less than 2^19 (normalised)
-        std::vector<double> dsum(E, 0.0);
-        std::vector<int> stamp(E, -1);
-        for (int c = 0; c < K; ++c) {
-            const double d = D[c] / scale;
-            for (long long i = P->path_edge_off[P->demand_path_off[c]]; i < P->path_edge_off[P->demand_path_off[c + 1]]; ++i) {
-                const int e = P->path_edges[i];
-                if (stamp[e] != c) { stamp[e] = c; dsum[e] += d; }
-            }
-        }
-        for (int e = 0; e < E; ++e)
-            if (ne[e] >= (1LL << 19) || dsum[e] >= (double)(1 << 19)) {
-                h->err = fmt("edge %lld: %lld paths, or the demands with a path through it, exceed the range of the "
-                             "load histograms (2^19 paths, 2^19 in normalised demand)", e, ne[e]);
-                return bail(TE_EUNSUPPORTED);
-            }
-    }
 
     // ---------------- persistent grid ----------------
     int bps = 0, nsm = 0;
@@ -481,9 +337,9 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     const size_t ns = (size_t)nslots * kLanes;
     cudaError_t ce = cudaSuccess;
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
-    A(h->alloc(&d_ids, ids.size()));
-    A(h->alloc(&d_rowoff, sizeof(unsigned) * rowoff.size()));
-    A(h->alloc(&d_slotbase, sizeof(int) * slotbase.size()));
+    A(h->alloc(&d_ids, sizeof(uint16_t) * hl.ids.size()));
+    A(h->alloc(&d_rowoff, sizeof(unsigned) * hl.rowoff.size()));
+    A(h->alloc(&d_slotbase, sizeof(int) * hl.slotbase.size()));
     A(h->alloc(&d_demand_of, sizeof(int) * ND));
     A(h->alloc(&d_blkmeta, sizeof(te::BlockMeta) * (size_t)nblocks));
     A(h->alloc(&d_Dn, sizeof(float) * ND));
@@ -528,18 +384,18 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
         return bail(ce == cudaErrorMemoryAllocation ? TE_ENOMEM : TE_ECUDA);
     }
     cudaStream_t s = h->stream;
-    A(cudaMemcpyAsync(d_ids, ids.data(), ids.size(), cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_rowoff, rowoff.data(), sizeof(unsigned) * rowoff.size(), cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_slotbase, slotbase.data(), sizeof(int) * slotbase.size(), cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_demand_of, demand_of.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_blkmeta, blkmeta.data(), sizeof(te::BlockMeta) * (size_t)nblocks, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_Dn, Dn.data(), sizeof(float) * ND, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(h->Dc, Dc.data(), sizeof(double) * ND, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_np, npv.data(), ND, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_slot_path, slot_path.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_cap, cap_n.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_ne, ne_f.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
-    A(cudaMemcpyAsync(d_inv, inv_ne.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_ids, hl.ids.data(), sizeof(uint16_t) * hl.ids.size(), cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_rowoff, hl.rowoff.data(), sizeof(unsigned) * hl.rowoff.size(), cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_slotbase, hl.slotbase.data(), sizeof(int) * hl.slotbase.size(), cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_demand_of, hl.demand_of.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_blkmeta, hl.blkmeta.data(), sizeof(te::BlockMeta) * (size_t)nblocks, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_Dn, hl.Dn.data(), sizeof(float) * ND, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(h->Dc, hl.Dc.data(), sizeof(double) * ND, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_np, hl.np.data(), ND, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_slot_path, hl.slot_path.data(), sizeof(long long) * ns, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_cap, hl.cap_n.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_ne, hl.ne_f.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_inv, hl.inv_ne.data(), sizeof(float) * E, cudaMemcpyHostToDevice, s));
     if (ce != cudaSuccess) {
         h->err = std::string("copy to device failed: ") + cudaGetErrorString(ce);
         return bail(TE_ECUDA);
@@ -574,7 +430,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     // algorithmic traffic of one iteration: the edge ids once, the rates read
     // and written, per demand its value and its multiplier read and written,
     // per block its metadata record
-    h->bytes_per_iter = (long long)ids.size() + 2LL * (long long)sizeof(float) * (long long)ns +
+    h->bytes_per_iter = (long long)(sizeof(uint16_t) * hl.ids.size()) + 2LL * (long long)sizeof(float) * (long long)ns +
                         3LL * (long long)sizeof(float) * (long long)ND +
                         (long long)sizeof(te::BlockMeta) * (long long)nblocks;
     te_status rs = te_reset(h);

@@ -223,6 +223,54 @@ typedef struct {
 } te_layout_info;
 te_status te_layout(const te_handle* h, te_layout_info* info);
 
+/* ---------------------------------------------------------------------- */
+/* Batch of instances (what-if scenarios) over one topology                */
+/* ---------------------------------------------------------------------- */
+/* Many TE instances that share the topology's edge numbering but have their
+ * own path sets (e.g. paths through failed links removed), demands and
+ * capacities, solved together: each instance runs Algorithm 1 (with the same
+ * options) on its own, one instance per CTA, all in one launch captured in a
+ * CUDA graph.  Not in the paper, which solves one instance at a time; the
+ * per-instance iteration is the same as te_solve's. */
+typedef struct te_batch te_batch;
+
+typedef struct {
+    int64_t n_instances, n_paths, id_rows;
+    int64_t bytes_per_iter;   /* algorithmic traffic of one iteration of every instance */
+    int64_t device_bytes, kernel_launches;
+    int32_t warps_per_cta, ctas_per_sm;  /* CTA shape chosen by the first te_batch_solve (0 before) */
+    int32_t lanes_per_demand;
+} te_batch_info_t;
+
+/* Copies n instances (paths[i], demands[i] [paths[i]->n_demands], capacities[i]
+ * [topo->n_edges]; the caller keeps its buffers) to the device and sets every
+ * instance to the initial state of Algorithm 1.  Inputs must satisfy the rules
+ * of te_create (edge ids are range-checked here, path walks are not).  The
+ * options apply to every instance; a NULL cuda_stream makes the batch create
+ * and own a stream (graph capture needs one).  Errors as te_create. */
+te_status te_batch_create(const te_topology* topo, int32_t n, const te_paths* const* paths,
+                          const double* const* demands, const double* const* capacities,
+                          const te_options* opt, te_batch** out);
+
+/* Runs up to max_iters iterations of every instance (an instance whose stop
+ * rule fires stops there) and fills results[i] (may be NULL).  The first call
+ * times each candidate CTA shape (warps per CTA, CTAs per SM) on the first
+ * iterations and keeps the fastest; results do not depend on the shape.
+ * Later calls with the same remaining budget replay a captured graph.
+ * Errors: TE_EINVAL, TE_ETIMEOUT, TE_ENUMERIC, TE_ECUDA, TE_EUNSUPPORTED. */
+te_status te_batch_solve(te_batch* b, int64_t max_iters, te_solve_result* results);
+
+/* te_allocation for instance i (its paths in the caller's order and units). */
+te_status te_batch_allocation(te_batch* b, int32_t i, float* x_out, int32_t project, int32_t out_is_device);
+
+/* Every instance back to the initial state of Algorithm 1. */
+te_status te_batch_reset(te_batch* b);
+
+te_status te_batch_info(const te_batch* b, te_batch_info_t* info);
+void te_batch_destroy(te_batch* b);
+/* Message of the batch's last error (b NULL: of the last failed te_batch_create). */
+const char* te_batch_last_error(const te_batch* b);
+
 /* The duality gap of te_gap for a caller-supplied allocation, computed
  * without allocating any memory (the paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc where they need the

@@ -369,3 +369,72 @@ def subset(inst: Instance, demand_ids: np.ndarray, name: Optional[str] = None) -
                     demand_src=inst.demand_src[demand_ids].copy(), demand_dst=inst.demand_dst[demand_ids].copy(),
                     demand=inst.demand[demand_ids].copy(), demand_path_off=new_dpo, path_edge_off=new_peo,
                     path_edges=pe.astype(np.int32), meta=dict(inst.meta))
+
+
+def drop_paths(inst: Instance, keep_path: np.ndarray, name: Optional[str] = None) -> Instance:
+    """The instance with only the paths where keep_path is true; demands left
+    without a path are dropped (all edges kept)."""
+    keep_path = np.asarray(keep_path, dtype=bool)
+    dpo = inst.demand_path_off
+    per_demand = np.add.reduceat(keep_path.astype(np.int64), dpo[:-1]) if inst.n_paths else np.zeros(0, np.int64)
+    per_demand[np.diff(dpo) == 0] = 0
+    dkeep = np.nonzero(per_demand > 0)[0]
+    paths = np.nonzero(keep_path)[0]
+    plen = inst.path_edge_off[paths + 1] - inst.path_edge_off[paths]
+    new_peo = np.concatenate([[0], np.cumsum(plen)]).astype(np.int64)
+    starts = inst.path_edge_off[paths]
+    idx = np.repeat(starts - new_peo[:-1], plen) + np.arange(int(new_peo[-1]))
+    pe = inst.path_edges[idx].astype(np.int32)
+    new_dpo = np.concatenate([[0], np.cumsum(per_demand[dkeep])]).astype(np.int64)
+    return Instance(name=name or inst.name + "-drop", n_nodes=inst.n_nodes, edge_src=inst.edge_src,
+                    edge_dst=inst.edge_dst, capacity=inst.capacity.copy(),
+                    demand_src=inst.demand_src[dkeep].copy(), demand_dst=inst.demand_dst[dkeep].copy(),
+                    demand=inst.demand[dkeep].copy(), demand_path_off=new_dpo, path_edge_off=new_peo,
+                    path_edges=pe, meta=dict(inst.meta))
+
+
+def make_what_if(base: Instance, n_scenarios: int, n_matrices: int, seed: int = 0,
+                 min_fail: int = 1, max_fail: int = 3, noise: float = 0.2) -> list:
+    """What-if batch over one topology: n_scenarios failure scenarios, each
+    removing min_fail..max_fail random links (both directions get capacity 0;
+    the paths through them are dropped, and demands left without a path),
+    times n_matrices demand matrices (the base demands times a lognormal
+    factor clipped to 1 -/+ noise).  Instance s * n_matrices + m is scenario
+    s with matrix m; its meta records the failed links."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_links = base.n_edges // 2
+    factors = []
+    for _ in range(n_matrices):
+        z = _normal(rng, base.n_demands)
+        factors.append(np.clip(np.exp(0.5 * noise * z), 1.0 - noise, 1.0 + noise))
+    out = []
+    for s in range(n_scenarios):
+        nf = min_fail + int(rng.random() * (max_fail - min_fail + 1))
+        failed = set()
+        while len(failed) < nf:
+            failed.add(int(rng.random() * n_links))
+        dead = np.zeros(base.n_edges, dtype=bool)
+        for l in failed:
+            dead[2 * l] = dead[2 * l + 1] = True
+        hit = np.add.reduceat(dead[base.path_edges].astype(np.int64), base.path_edge_off[:-1])
+        keep = hit == 0
+        keep[np.diff(base.path_edge_off) == 0] = False
+        # the demand factors follow the demands that survive
+        alive = np.add.reduceat(keep.astype(np.int64), base.demand_path_off[:-1]) > 0
+        sc = drop_paths(base, keep, name=f"{base.name}-s{s}")
+        sc.capacity[dead] = 0.0
+        for m in range(n_matrices):
+            inst = Instance(name=f"{base.name}-s{s}-m{m}", n_nodes=sc.n_nodes, edge_src=sc.edge_src,
+                            edge_dst=sc.edge_dst, capacity=sc.capacity, demand_src=sc.demand_src,
+                            demand_dst=sc.demand_dst, demand=sc.demand * factors[m][alive],
+                            demand_path_off=sc.demand_path_off, path_edge_off=sc.path_edge_off,
+                            path_edges=sc.path_edges,
+                            meta=dict(base.meta, scenario=s, matrix=m, failed_links=sorted(failed)))
+            out.append(inst)
+    return out
+
+
+def make_batch_base(seed: int = 0, threads: int = 0) -> Instance:
+    """The 500-node WAN of the what-if batch: ~1,600 links, gravity demands on
+    all 249,500 ordered pairs, k = 8."""
+    return make_waxman("wan500", 500, 1600, 8, seed=seed, locality=MEDIUM_LOCALITY, threads=threads)

@@ -32,7 +32,8 @@ STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "T
 
 EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_gap", "te_prices",
             "te_set_warm_start", "te_set_demands", "te_set_capacities", "te_reset", "te_trace", "te_layout",
-            "te_destroy", "te_last_error", "te_gap_noalloc")
+            "te_destroy", "te_last_error", "te_gap_noalloc", "te_batch_create", "te_batch_solve",
+            "te_batch_allocation", "te_batch_reset", "te_batch_info", "te_batch_destroy", "te_batch_last_error")
 
 
 class TEError(RuntimeError):
@@ -82,6 +83,16 @@ class te_layout_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class te_batch_info_t(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int64), ("n_paths", ctypes.c_int64), ("id_rows", ctypes.c_int64),
+                ("bytes_per_iter", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("lanes_per_demand", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2605_01748_b300.build` "
@@ -118,6 +129,20 @@ def _load() -> ctypes.CDLL:
     lib.te_destroy.argtypes = [H]
     lib.te_last_error.restype = ctypes.c_char_p
     lib.te_last_error.argtypes = [H]
+    lib.te_batch_create.restype = ctypes.c_int
+    lib.te_batch_create.argtypes = [P, ctypes.c_int32, P, P, P, P, ctypes.POINTER(ctypes.c_void_p)]
+    lib.te_batch_solve.restype = ctypes.c_int
+    lib.te_batch_solve.argtypes = [H, ctypes.c_int64, P]
+    lib.te_batch_allocation.restype = ctypes.c_int
+    lib.te_batch_allocation.argtypes = [H, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_int32]
+    lib.te_batch_reset.restype = ctypes.c_int
+    lib.te_batch_reset.argtypes = [H]
+    lib.te_batch_info.restype = ctypes.c_int
+    lib.te_batch_info.argtypes = [H, ctypes.POINTER(te_batch_info_t)]
+    lib.te_batch_destroy.restype = None
+    lib.te_batch_destroy.argtypes = [H]
+    lib.te_batch_last_error.restype = ctypes.c_char_p
+    lib.te_batch_last_error.argtypes = [H]
     lib.te_gap_noalloc.restype = ctypes.c_int
     lib.te_gap_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                    P, P, P, P, P, P, P, ctypes.c_double, P, P]
@@ -338,6 +363,66 @@ class TE:
     def close(self) -> None:
         if self.h:
             te_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TEBatch:
+    """A batch of instances over one topology (same edge numbering), solved
+    together by the batch kernel: one instance per CTA, one launch."""
+
+    def __init__(self, insts, **options):
+        self.n = len(insts)
+        self._keep = [_Keep(i) for i in insts]
+        k0 = self._keep[0]
+        self.topo = te_topology(int(insts[0].n_nodes), k0.capacity.shape[0], 0, 0)
+        self.paths = (te_paths * self.n)()
+        for i, k in enumerate(self._keep):
+            self.paths[i] = te_paths(k.demand.shape[0], 0, k.peo.shape[0] - 1, k.pe.shape[0], 0, 0,
+                                     _ptr(k.dpo), _ptr(k.peo), _ptr(k.pe))
+        self._pp = (ctypes.c_void_p * self.n)(*[ctypes.addressof(self.paths[i]) for i in range(self.n)])
+        self._dp = (ctypes.c_void_p * self.n)(*[_ptr(k.demand) for k in self._keep])
+        self._cp = (ctypes.c_void_p * self.n)(*[_ptr(k.capacity) for k in self._keep])
+        self.n_paths = [int(k.peo.shape[0] - 1) for k in self._keep]
+        self.options = te_default_options(**options)
+        h = ctypes.c_void_p()
+        st = _lib.te_batch_create(ctypes.byref(self.topo), self.n, self._pp, self._dp, self._cp,
+                                  ctypes.byref(self.options), ctypes.byref(h))
+        if st != TE_OK:
+            raise TEError(st, (_lib.te_batch_last_error(None) or b"").decode())
+        self.h = h
+
+    def _check(self, st):
+        if st != TE_OK:
+            raise TEError(st, (_lib.te_batch_last_error(self.h) or b"").decode())
+
+    def solve(self, max_iters: int) -> list:
+        res = (te_solve_result * self.n)()
+        self._check(_lib.te_batch_solve(self.h, int(max_iters), res))
+        return [r.as_dict() for r in res]
+
+    def allocation(self, i: int, project: int = PROJECT_ALG2, out=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros(self.n_paths[i], dtype=np.float32)
+        self._check(_lib.te_batch_allocation(self.h, int(i), _ptr(out), int(project), int(_is_device(out))))
+        return out
+
+    def reset(self) -> None:
+        self._check(_lib.te_batch_reset(self.h))
+
+    def info(self) -> dict:
+        info = te_batch_info_t()
+        self._check(_lib.te_batch_info(self.h, ctypes.byref(info)))
+        return info.as_dict()
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            _lib.te_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

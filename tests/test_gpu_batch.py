@@ -1,0 +1,87 @@
+"""The batch engine (one instance per CTA, one launch for many what-if
+instances) against the FP64 oracle run on each instance alone, and against
+the single-instance engine."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_01748_b300 import instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def te():
+    from paper_2605_01748_b300 import build
+    build.build_te()
+    from paper_2605_01748_b300 import te as te_mod
+    return te_mod
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def test_what_if_generator_shares_paths_within_a_scenario(tiny):
+    W = instances.make_what_if(tiny, 3, 2, seed=1, min_fail=1, max_fail=2)
+    assert len(W) == 6
+    for s in range(3):
+        a, b = W[2 * s], W[2 * s + 1]
+        assert a.path_edges is b.path_edges and a.demand_path_off is b.demand_path_off
+        failed = a.meta["failed_links"]
+        dead = np.zeros(tiny.n_edges, bool)
+        for l in failed:
+            dead[2 * l] = dead[2 * l + 1] = True
+        assert not dead[a.path_edges].any()
+        assert (a.capacity[dead] == 0).all()
+        assert (np.abs(a.demand / b.demand - 1) <= 0.5).all()
+
+
+def test_batch_matches_oracle_per_instance(te, tiny):
+    W = instances.make_what_if(tiny, 3, 2, seed=2, min_fail=1, max_fail=1)
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    b = te.TEBatch(W, **kw)
+    res = b.solve(150)
+    assert all(r["iters"] == 150 for r in res)
+    for i, inst in enumerate(W):
+        s = O.OracleSolver(inst, **kw)
+        s.run(150)
+        assert _rel(b.allocation(i, project=te.PROJECT_NONE), s.allocation()) <= 1e-4
+    info = b.info()
+    assert info["n_instances"] == 6 and info["warps_per_cta"] in (8, 16)
+    b.close()
+
+
+def test_batch_matches_single_engine_with_adaptive_beta(te, medium):
+    W = instances.make_what_if(medium, 2, 2, seed=3)
+    b = te.TEBatch(W)
+    res = b.solve(300)
+    for i, inst in enumerate(W):
+        t = te.TE(inst)
+        r = t.solve(300)
+        assert (r["total_iters"], r["alpha"], r["beta"]) == (res[i]["total_iters"], res[i]["alpha"], res[i]["beta"])
+        xs = t.allocation(project=te.PROJECT_NONE)
+        assert _rel(b.allocation(i, project=te.PROJECT_NONE), xs) <= 1e-5
+        t.close()
+    b.close()
+
+
+def test_batch_stops_each_instance_by_its_own_rule(te, tiny):
+    W = instances.make_what_if(tiny, 4, 1, seed=4)
+    b = te.TEBatch(W, gamma=1e-3)
+    res = b.solve(50000)
+    for i, inst in enumerate(W):
+        assert res[i]["converged"] == 1
+        t = te.TE(inst, gamma=1e-3)
+        r = t.solve(50000)
+        assert r["converged"] == 1
+        assert abs(r["total_iters"] - res[i]["total_iters"]) <= max(5, 0.02 * r["total_iters"])
+        for mode in (te.PROJECT_ALG2, te.PROJECT_SCALE):
+            xp = b.allocation(i, project=mode).astype(np.float64)
+            assert (O.edge_loads(inst, xp) <= inst.capacity * (1 + 1e-5) + 1e-9).all()
+            assert (O.demand_totals(inst, xp) <= inst.demand * (1 + 1e-5)).all()
+        t.close()
+    # a second call with no budget left changes nothing
+    res2 = b.solve(0)
+    assert [r["total_iters"] for r in res2] == [r["total_iters"] for r in res]
+    b.close()

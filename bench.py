@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--ablation", action="store_true",
                     help="iterations to 1%% with and without adaptive beta, and cold versus warm re-solves "
                          "after a demand change (Section 4 factor analysis), one JSON line")
+    ap.add_argument("--batch", type=int, default=0, metavar="SCENARIOS",
+                    help="what-if batch on the 500-node WAN: SCENARIOS failure scenarios x 4 demand matrices, "
+                         "the batch engine against a loop of single-instance solves, one JSON line")
+    ap.add_argument("--batch-iters", type=int, default=2000)
     ap.add_argument("--iters", type=int, default=0,
                     help="profiling runs only: use this K and skip the reference run and the probe")
     return ap.parse_args()
@@ -525,6 +529,76 @@ def run_ablation(a):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(a):
+    """The batch engine against the plain loop on the same GPU: every
+    instance of the what-if batch (a.batch failure scenarios of the 500-node
+    WAN, each removing 1-3 links, x 4 demand matrices perturbed by a clipped
+    lognormal factor) runs --batch-iters iterations with the same options
+    (no early stop), once as one batch launch and once as one te_solve per
+    instance (one handle per scenario, te_set_demands + te_reset per matrix).
+    Device time by CUDA events; the batch's first call includes its CTA-shape
+    timing, so the batch is timed on a second solve after te_batch_reset."""
+    import numpy as np
+    import torch
+    from paper_2605_01748_b300 import instances, te
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    base = instances.make_batch_base(threads=os.cpu_count() or 0)
+    W = instances.make_what_if(base, a.batch, 4, seed=0)
+    gen_s = time.time() - t0
+    K = a.batch_iters
+    opts = dict(gamma=-1.0)
+    t0 = time.time()
+    b = te.TEBatch(W, cuda_stream=stream.cuda_stream, **opts)
+    create_s = time.time() - t0
+    b.solve(K)  # includes the CTA-shape timing
+    b.reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    res = b.solve(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    info = b.info()
+    b.close()
+    assert all(r["iters"] == K for r in res)
+    loop_ms = 0.0
+    for sidx in range(a.batch):
+        t = te.TE(W[4 * sidx], cuda_stream=stream.cuda_stream, **opts)
+        for m in range(4):
+            t.set_demands(W[4 * sidx + m].demand)
+            t.reset()
+            e0.record(stream)
+            t.solve(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            loop_ms += e0.elapsed_time(e1)
+        t.close()
+    peaks = {}
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    n = len(W)
+    achieved = info["bytes_per_iter"] * K / (batch_ms * 1e-3) / 1e9
+    out = {"mode": "batch", "workload": f"what-if batch: {a.batch} failure scenarios x 4 demand matrices = {n} "
+                                         f"instances of the 500-node WAN ({base.n_edges} directed edges, "
+                                         f"{base.n_demands} demands, k=8, {info['n_paths']} paths in all)",
+           "iterations_per_instance": K, "batch_ms": round(batch_ms, 1), "loop_ms": round(loop_ms, 1),
+           "speedup": round(loop_ms / batch_ms, 2),
+           "instance_iters_per_s": {"batch": round(n * K / (batch_ms * 1e-3), 1),
+                                    "loop": round(n * K / (loop_ms * 1e-3), 1)},
+           "batch_roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                              "frac": round(achieved / hbm, 4), "bytes_per_iter": info["bytes_per_iter"]},
+           "batch_shape": {"warps_per_cta": info["warps_per_cta"], "ctas_per_sm": info["ctas_per_sm"],
+                           "lanes_per_demand": info["lanes_per_demand"]},
+           "host_s": {"generate": round(gen_s, 1), "batch_create": round(create_s, 1)},
+           "options": "alpha-continuation and residual balancing as default, no early stop (gamma < 0)"}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(a, ws, rank):
     """The FP64 CPU oracle as it stands, on the host cores, same workload and
     metric.  Each step runs a bounded sample of oracle iterations on the full
@@ -579,7 +653,9 @@ def run_reference(a, ws, rank):
 def main():
     a = parse()
     ws, rank, local, dist = dist_setup()
-    if a.ablation:
+    if a.batch > 0:
+        run_batch(a)
+    elif a.ablation:
         run_ablation(a)
     elif a.impl == "reference":
         run_reference(a, ws, rank)

@@ -16,6 +16,9 @@ Functions (all FP64; paper references are to GATE, Section 3 and Appendix B):
 * :func:`project_scale` -- a proportional feasibility scaling (not in the
   paper; scales where Algorithm 2 trims whole paths).
 * :func:`gap` -- the Lagrangian duality gap of a feasible allocation.
+* :func:`gradient` -- the fairness objective after K fixed-schedule
+  iterations and its gradient in capacities and demands (reverse mode,
+  checkpointed; not in the paper).
 * :func:`optimality` -- the optimality metric of Section 4.1.
 """
 from __future__ import annotations
@@ -85,6 +88,8 @@ def _L() -> ctypes.CDLL:
                                         ctypes.c_int64]
         lib.or_project.restype = None
         lib.or_project.argtypes = [P, P, ctypes.c_double]
+        lib.or_gradient.restype = ctypes.c_int
+        lib.or_gradient.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P]
         lib.or_project_scale.restype = None
         lib.or_project_scale.argtypes = [P, P]
         lib.or_gap.restype = ctypes.c_double
@@ -230,6 +235,23 @@ def project_scale(inst, x: np.ndarray) -> np.ndarray:
     out = np.array(x, dtype=np.float64, copy=True)
     _L().or_project_scale(ctypes.byref(v.s), out.ctypes.data)
     return out
+
+
+def gradient(inst, alpha: float, beta0: float, iters: int, checkpoint: int = 20, scale_mode: int = 2,
+             threads: int = 0):
+    """(J, dJ/dC, dJ/dD) of J = sum_c U_alpha(S_c) after `iters` iterations
+    of the fixed schedule (beta0, alpha fixed) from the initial state, the
+    normalisation unit held fixed (scale_mode 2: caller units)."""
+    view = _InstanceView(inst)
+    opts = _Opts(alpha, alpha, 1.0, alpha, -1.0, 10.0, 2.0, beta0, 0, 0, int(threads), int(scale_mode))
+    J = ctypes.c_double()
+    gC = np.zeros(inst.n_edges, dtype=np.float64)
+    gD = np.zeros(inst.n_demands, dtype=np.float64)
+    rc = _L().or_gradient(ctypes.byref(view.s), ctypes.byref(opts), int(iters), int(checkpoint), ctypes.byref(J),
+                          gC.ctypes.data, gD.ctypes.data)
+    if rc != 0:
+        raise ValueError("or_gradient: bad options")
+    return J.value, gC, gD
 
 
 def gap(inst, x: np.ndarray, prices: np.ndarray, alpha: float):

@@ -77,7 +77,7 @@ typedef struct {
     int32_t adapt_beta;   /* 1: residual balancing on                     */
     int32_t continuation; /* 1: stop when converged on the first iteration after an increment */
     int32_t threads;      /* OpenMP threads (0: runtime default)          */
-    int32_t scale_mode;   /* unit of the normalised problem: 0 = max_e C_e,
+    int32_t scale_mode;   /* unit of the normalised problem: 0 = max_e C_e, 2 = 1 (caller units),
                              1 = geometric mean of the demands            */
 } or_options;
 
@@ -229,6 +229,8 @@ int or_init(const or_instance* I, const or_options* o, const double* x0, double*
         double lg = 0.0;
         for (int32_t c = 0; c < I->n_demands; ++c) lg += log(I->demand[c]);
         scale = exp(lg / (double)I->n_demands);
+    } else if (o->scale_mode == 2) {
+        scale = 1.0;  /* caller units */
     } else {
         for (int e = 0; e < I->n_edges; ++e) if (I->cap[e] > scale) scale = I->cap[e];
     }
@@ -437,6 +439,208 @@ void or_run_expanded(const or_instance* I, double beta, double alpha, double sca
             }
     }
     free(m); free(w); free(V); free(ne);
+}
+
+/* ------------------------------------------------------------------ */
+/* Gradient of the fairness objective through K iterations (not in the  */
+/* paper; the differentiated form for capacity planning).               */
+/*                                                                      */
+/* J(C, D) = sum_c U_alpha(scale S_c^K), S_c^K the demand totals of the */
+/* iterate after K iterations from the initial state of Algorithm 1, with */
+/* beta and alpha fixed (no residual balancing, no continuation) and the */
+/* normalisation unit scale held fixed.  gC[e] = dJ/dC_e, gD[c] = dJ/dD_c */
+/* (caller units), by reverse-mode differentiation of every step:       */
+/*   x-block: on the active set A of a demand (x' > 0), x' = m + lambda w */
+/*     with w = 1/(beta n_r); if the demand cap binds (lambda below       */
+/*     U'(S)), lambda = (D - sum_A m) / sum_A w; else lambda = U'(S) and   */
+/*     d lambda = -alpha lambda / (S + alpha lambda sum_A w) d(sum_A m)    */
+/*   u' = max(0, u + (L - C)/n_e), d' = u' - u, L = sum of x' over e      */
+/*   m = x - (1/n_r) sum_{e in r} (u_e + d_e)                             */
+/* States are kept every ckpt iterations and each segment is recomputed  */
+/* forward before its reverse sweep.  Returns 0, or 1 on bad options.    */
+/* ------------------------------------------------------------------ */
+static double utility_d(double S, double alpha) { return alpha == 0.0 ? 1.0 : exp(-alpha * log(S)); }
+
+/* one forward iteration with fixed beta, alpha: (x, u, d) -> next, in place */
+static void fwd_step(const or_instance* I, const double* Cn, const double* Dn, const int64_t* ne, const or_csc* T,
+                     double beta, double alpha, double* x, double* u, double* d, double* xn, double* m, double* w) {
+    for (int32_t c = 0; c < I->n_demands; ++c) {
+        const int64_t p0 = I->dpo[c], p1 = I->dpo[c + 1];
+        const int n = (int)(p1 - p0);
+        for (int j = 0; j < n; ++j) {
+            const int64_t r = p0 + j;
+            const int64_t nr = I->peo[r + 1] - I->peo[r];
+            double q = 0.0;
+            for (int64_t i = I->peo[r]; i < I->peo[r + 1]; ++i) q += u[I->pe[i]] + d[I->pe[i]];
+            m[j] = x[r] - q / (double)nr;
+            w[j] = 1.0 / (beta * (double)nr);
+        }
+        or_demand_solve(n, m, w, Dn[c], alpha, xn + p0);
+    }
+    for (int e = 0; e < I->n_edges; ++e) {
+        double L = 0.0;
+        for (int64_t i = T->off[e]; i < T->off[e + 1]; ++i) L += xn[T->path[i]];
+        const double un = ne[e] > 0 ? fmax(0.0, u[e] + (L - Cn[e]) / (double)ne[e]) : 0.0;
+        d[e] = un - u[e];
+        u[e] = un;
+    }
+    memcpy(x, xn, sizeof(double) * (size_t)I->n_paths);
+}
+
+int or_gradient(const or_instance* I, const or_options* o, int64_t K, int64_t ckpt, double* J, double* gC,
+                double* gD) {
+    if (K < 0 || ckpt < 1 || !(o->beta0 > 0.0) || o->adapt_beta || o->continuation) return 1;
+    const int E = I->n_edges;
+    const int32_t NC = I->n_demands;
+    const int64_t P = I->n_paths;
+    or_scalars sc;
+    double* x = (double*)malloc(sizeof(double) * (size_t)P);
+    double* u = (double*)malloc(sizeof(double) * (size_t)E);
+    double* d = (double*)malloc(sizeof(double) * (size_t)E);
+    if (or_init(I, o, NULL, x, u, d, &sc)) { free(x); free(u); free(d); return 1; }
+    const double scale = sc.scale, beta = sc.beta, alpha = sc.alpha;
+    double* Cn = (double*)malloc(sizeof(double) * (size_t)E);
+    double* Dn = (double*)malloc(sizeof(double) * (size_t)NC);
+    int64_t* ne = (int64_t*)calloc((size_t)E, sizeof(int64_t));
+    for (int e = 0; e < E; ++e) Cn[e] = I->cap[e] / scale;
+    for (int32_t c = 0; c < NC; ++c) Dn[c] = I->demand[c] / scale;
+    for (int64_t i = 0; i < I->nnz; ++i) ne[I->pe[i]]++;
+    or_csc T;
+    csc_build(I, &T);
+    const int64_t kmax = max_paths_per_demand(I);
+    double* m = (double*)malloc(sizeof(double) * (size_t)(kmax > 0 ? kmax : 1));
+    double* w = (double*)malloc(sizeof(double) * (size_t)(kmax > 0 ? kmax : 1));
+    double* xs = (double*)malloc(sizeof(double) * (size_t)(kmax > 0 ? kmax : 1));
+    double* xn = (double*)malloc(sizeof(double) * (size_t)P);
+    /* forward with checkpoints at k = 0, ckpt, 2 ckpt, ... */
+    const int64_t nck = K / ckpt + 1;
+    double* ck = (double*)malloc(sizeof(double) * (size_t)nck * (size_t)(P + 2 * E));
+    for (int64_t k = 0; k < K; ++k) {
+        if (k % ckpt == 0) {
+            double* c0 = ck + (size_t)(k / ckpt) * (size_t)(P + 2 * E);
+            memcpy(c0, x, sizeof(double) * (size_t)P);
+            memcpy(c0 + P, u, sizeof(double) * (size_t)E);
+            memcpy(c0 + P + E, d, sizeof(double) * (size_t)E);
+        }
+        fwd_step(I, Cn, Dn, ne, &T, beta, alpha, x, u, d, xn, m, w);
+    }
+    /* objective and its adjoint at x^K */
+    double* xb = (double*)calloc((size_t)P, sizeof(double));
+    double* ub = (double*)calloc((size_t)E, sizeof(double));
+    double* db = (double*)calloc((size_t)E, sizeof(double));
+    double* Cb = (double*)calloc((size_t)E, sizeof(double));
+    double* Db = (double*)calloc((size_t)NC, sizeof(double));
+    double Jv = 0.0;
+    for (int32_t c = 0; c < NC; ++c) {
+        double S = 0.0;
+        for (int64_t r = I->dpo[c]; r < I->dpo[c + 1]; ++r) S += x[r];
+        Jv += or_utility(scale * S, alpha);
+        const double g = scale * utility_d(scale * S, alpha);  /* dJ/dS_c */
+        for (int64_t r = I->dpo[c]; r < I->dpo[c + 1]; ++r) xb[r] = g;
+    }
+    /* reverse sweep, one checkpoint segment at a time */
+    const int64_t seg = ckpt;
+    double* sx = (double*)malloc(sizeof(double) * (size_t)(seg + 1) * (size_t)P);
+    double* su = (double*)malloc(sizeof(double) * (size_t)(seg + 1) * (size_t)E);
+    double* sd = (double*)malloc(sizeof(double) * (size_t)(seg + 1) * (size_t)E);
+    double* Lb = (double*)malloc(sizeof(double) * (size_t)E);
+    double* gb = (double*)malloc(sizeof(double) * (size_t)P);
+    double* qb = (double*)malloc(sizeof(double) * (size_t)P);
+    for (int64_t k0 = ((K - 1) / ckpt) * ckpt; K > 0 && k0 >= 0; k0 -= ckpt) {
+        const int64_t k1 = (k0 + ckpt < K) ? k0 + ckpt : K;
+        const double* c0 = ck + (size_t)(k0 / ckpt) * (size_t)(P + 2 * E);
+        memcpy(x, c0, sizeof(double) * (size_t)P);
+        memcpy(u, c0 + P, sizeof(double) * (size_t)E);
+        memcpy(d, c0 + P + E, sizeof(double) * (size_t)E);
+        for (int64_t k = k0; k <= k1; ++k) {
+            memcpy(sx + (size_t)(k - k0) * P, x, sizeof(double) * (size_t)P);
+            memcpy(su + (size_t)(k - k0) * E, u, sizeof(double) * (size_t)E);
+            memcpy(sd + (size_t)(k - k0) * E, d, sizeof(double) * (size_t)E);
+            if (k < k1) fwd_step(I, Cn, Dn, ne, &T, beta, alpha, x, u, d, xn, m, w);
+        }
+        for (int64_t k = k1 - 1; k >= k0; --k) {
+            const double* xk = sx + (size_t)(k - k0) * P;
+            const double* uk = su + (size_t)(k - k0) * E;
+            const double* dk = sd + (size_t)(k - k0) * E;
+            const double* u1 = su + (size_t)(k + 1 - k0) * E;
+            /* d' = u' - u and u' = max(0, u + (L - C)/n_e) */
+            for (int e = 0; e < E; ++e) {
+                const double tot = ub[e] + db[e];
+                double uin = -db[e];
+                Lb[e] = 0.0;
+                if (ne[e] > 0 && u1[e] > 0.0) {
+                    uin += tot;
+                    Lb[e] = tot / (double)ne[e];
+                    Cb[e] -= tot / (double)ne[e];
+                }
+                ub[e] = uin;
+                db[e] = 0.0;
+            }
+            /* L = sum of x' over each edge */
+            for (int64_t r = 0; r < P; ++r) {
+                double g = xb[r];
+                for (int64_t i = I->peo[r]; i < I->peo[r + 1]; ++i) g += Lb[I->pe[i]];
+                gb[r] = g;
+            }
+            /* x-block of each demand */
+            for (int32_t c = 0; c < NC; ++c) {
+                const int64_t p0 = I->dpo[c], p1 = I->dpo[c + 1];
+                const int n = (int)(p1 - p0);
+                for (int j = 0; j < n; ++j) {
+                    const int64_t r = p0 + j;
+                    const int64_t nr = I->peo[r + 1] - I->peo[r];
+                    double q = 0.0;
+                    for (int64_t i = I->peo[r]; i < I->peo[r + 1]; ++i) q += uk[I->pe[i]] + dk[I->pe[i]];
+                    m[j] = xk[r] - q / (double)nr;
+                    w[j] = 1.0 / (beta * (double)nr);
+                }
+                const double lam = or_demand_solve(n, m, w, Dn[c], alpha, xs);
+                double S = 0.0, WA = 0.0, G = 0.0;
+                for (int j = 0; j < n; ++j)
+                    if (xs[j] > 0.0) {
+                        S += xs[j];
+                        WA += w[j];
+                        G += gb[p0 + j] * w[j];
+                    }
+                double dl_dm = 0.0;  /* d lambda / d m_s for s in A */
+                if (WA > 0.0) {
+                    const int capped = lam < utility_d(S, alpha) * (1.0 - 1e-9);
+                    if (capped) {
+                        dl_dm = -1.0 / WA;
+                        Db[c] += G / WA;
+                    } else {
+                        dl_dm = -alpha * lam / (S + alpha * lam * WA);
+                    }
+                }
+                for (int j = 0; j < n; ++j) {
+                    const int64_t r = p0 + j;
+                    const double mb = xs[j] > 0.0 ? gb[r] + G * dl_dm : 0.0;
+                    xb[r] = mb;  /* m = x - q/n_r */
+                    qb[r] = -mb / (double)(I->peo[r + 1] - I->peo[r]);
+                }
+            }
+            /* q = sum of (u + d) over the path's edges */
+            for (int64_t r = 0; r < P; ++r)
+                for (int64_t i = I->peo[r]; i < I->peo[r + 1]; ++i) {
+                    ub[I->pe[i]] += qb[r];
+                    db[I->pe[i]] += qb[r];
+                }
+        }
+    }
+    /* x^0 = D_c / |P_c| */
+    for (int32_t c = 0; c < NC; ++c) {
+        const int64_t p0 = I->dpo[c], p1 = I->dpo[c + 1];
+        double s0 = 0.0;
+        for (int64_t r = p0; r < p1; ++r) s0 += xb[r];
+        Db[c] += s0 / (double)(p1 - p0);
+    }
+    for (int e = 0; e < E; ++e) gC[e] = Cb[e] / scale;
+    for (int32_t c = 0; c < NC; ++c) gD[c] = Db[c] / scale;
+    *J = Jv;
+    free(x); free(u); free(d); free(Cn); free(Dn); free(ne); free(m); free(w); free(xs); free(xn); free(ck);
+    free(xb); free(ub); free(db); free(Cb); free(Db); free(sx); free(su); free(sd); free(Lb); free(gb); free(qb);
+    csc_free(&T);
+    return 0;
 }
 
 /* ------------------------------------------------------------------ */

@@ -97,7 +97,7 @@ typedef struct {
     int32_t scale_mode;   /* unit of the normalised problem: 0 = max_e C_e,
                              1 = geometric mean of the demands (default), so
                              the marginal utility S^-alpha of a typical demand
-                             stays near 1 as alpha grows                       */
+                             stays near 1 as alpha grows; 2 = 1 (caller units) */
     int32_t wait_timeout_ms; /* bound on every grid-wide wait inside te_solve;
                              0 = default (2000 ms)                             */
     int32_t test_withhold_cta; /* test hook for the bounded-wait path: 1 + the
@@ -222,6 +222,26 @@ typedef struct {
     int64_t kernel_launches;  /* kernels this handle has launched so far */
 } te_layout_info;
 te_status te_layout(const te_handle* h, te_layout_info* info);
+
+/* Gradient of the fairness objective through K iterations (not in the
+ * paper: the differentiated form, for capacity planning).  From the initial
+ * state of Algorithm 1 the handle runs K iterations with beta and alpha fixed
+ * (the handle must have been created with adapt_beta = 0, continuation = 0,
+ * gamma < 0 and alpha_start = alpha_target finite; else TE_EINVAL) and
+ *   J = sum_c U_alpha(S_c^K),   S_c^K = the demand totals after K iterations,
+ * then returns J (J_out may be NULL) and dJ/dC_e [n_edges], dJ/dD_c
+ * [n_demands] in caller units (FP64; out_is_device selects device or host
+ * buffers), by a hand-written reverse pass over the K iterations: the
+ * iterate's state is kept every checkpoint_every iterations and each segment
+ * is recomputed forward before it is reversed.  The normalisation unit is
+ * held fixed (create with scale_mode 2 for caller units, so that the
+ * function differentiated does not move the unit).  Forward states are the
+ * FP32 iterates; adjoints are FP64.  Uses device memory of about
+ * (K/checkpoint_every + checkpoint_every + 2) times the iterate (released
+ * before returning).  The handle's state afterwards is that of an
+ * intermediate iteration: call te_reset before solving again. */
+te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint_every, double* J_out, double* dJ_dC,
+                      double* dJ_dD, int32_t out_is_device);
 
 /* ---------------------------------------------------------------------- */
 /* Batch of instances (what-if scenarios) over one topology                */

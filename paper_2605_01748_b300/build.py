@@ -22,7 +22,8 @@ INCLUDE = os.path.join(REPO, "include")
 LIBTE = os.path.join(PKG_DIR, "libte.so")
 LIBTEGEN = os.path.join(PKG_DIR, "libtegen.so")
 
-TE_SOURCES = ["te_api.cu", "te_layout.cu", "te_iter.cu", "te_batch.cu", "te_proj.cu", "te_gap.cu", "te_noalloc.cu"]
+TE_SOURCES = ["te_api.cu", "te_layout.cu", "te_iter.cu", "te_batch.cu", "te_adjoint.cu", "te_proj.cu", "te_gap.cu",
+              "te_noalloc.cu"]
 GEN_SOURCES = [os.path.join("gen", "kpaths.cpp")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -250,7 +250,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     te_options opt;
     if (opt_in) opt = *opt_in; else te_default_options(&opt);
     if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
-        (opt.scale_mode != 0 && opt.scale_mode != 1) ||
+        (opt.scale_mode < 0 || opt.scale_mode > 2) ||
         !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0) {
         g_create_error = "invalid options";
         return TE_EINVAL;
@@ -285,6 +285,8 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
         double lg = 0.0;
         for (int c = 0; c < K; ++c) lg += log(D[c]);
         scale = exp(lg / (double)K);
+    } else if (opt.scale_mode == 2) {
+        scale = 1.0;  // caller units
     } else {
         for (int e = 0; e < E; ++e) scale = std::max(scale, C[e]);
     }
@@ -708,4 +710,113 @@ extern "C" te_status te_set_capacities(te_handle* h, const double* C, int32_t in
     A(cudaGetLastError());
     A(cudaStreamSynchronize(s));
     return h->cuda(ce, "te_set_capacities");
+}
+
+extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint_every, double* J_out, double* dJ_dC,
+                                 double* dJ_dD, int32_t out_is_device) {
+    if (!h || iters < 0 || checkpoint_every < 1 || !dJ_dC || !dJ_dD) return TE_EINVAL;
+    if (h->o.adapt_beta || h->o.continuation || !(h->o.gamma < 0.0) || !isfinite(h->o.alpha_target) ||
+        h->o.alpha_start != h->o.alpha_target)
+        return h->fail(TE_EINVAL, "te_gradient needs the fixed schedule: adapt_beta = 0, continuation = 0, "
+                                  "gamma < 0, alpha_start = alpha_target (finite)");
+    te_status st = te_reset(h);
+    if (st != TE_OK) return st;
+    cudaStream_t s = h->stream;
+    const te::Layout& L = h->L;
+    const size_t ns = (size_t)L.nslots * kLanes, E = (size_t)L.E, ND = (size_t)L.nblocks * L.dpb;
+    const size_t state = ns + 2 * E + ND;  // floats: x, u, w, multipliers
+    const long long K = iters, ck = checkpoint_every;
+    const long long nck = K / ck + 1;
+    std::vector<void*> tmp;
+    cudaError_t ce = cudaSuccess;
+    auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
+    auto dalloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (ce == cudaSuccess) ce = cudaMalloc(&p, bytes > 0 ? bytes : 16);
+        if (p) tmp.push_back(p);
+        return p;
+    };
+    auto release = [&]() {
+        for (void* p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    float* ckb = (float*)dalloc(sizeof(float) * state * (size_t)nck);
+    float* seg = (float*)dalloc(sizeof(float) * state * (size_t)(ck + 1));
+    te::AdjointBuffers B{};
+    B.xb = (double*)dalloc(sizeof(double) * ns);
+    B.ub = (double*)dalloc(sizeof(double) * E);
+    B.db = (double*)dalloc(sizeof(double) * E);
+    B.Lb = (double*)dalloc(sizeof(double) * E);
+    B.Cb = (double*)dalloc(sizeof(double) * E);
+    B.wbar = (double*)dalloc(sizeof(double) * E);
+    B.Db = (double*)dalloc(sizeof(double) * ND);
+    B.acc = (double*)dalloc(sizeof(double));
+    double* gC = out_is_device ? dJ_dC : (double*)dalloc(sizeof(double) * E);
+    double* gD = out_is_device ? dJ_dD : (double*)dalloc(sizeof(double) * (size_t)L.K);
+    if (ce != cudaSuccess) {
+        release();
+        cudaGetLastError();
+        return h->fail(TE_ENOMEM, "te_gradient: device allocation failed");
+    }
+    std::vector<te::Scalars> ck_sc((size_t)nck);
+    // the handle's state (current rates, prices, weights, multipliers) to and from a slot
+    auto save = [&](float* dst) {
+        A(cudaMemcpyAsync(dst, h->x + (size_t)h->hsc.xbuf * ns, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemcpyAsync(dst + ns, h->u, sizeof(float) * E, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemcpyAsync(dst + ns + E, h->w, sizeof(float) * E, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemcpyAsync(dst + ns + 2 * E, h->lam, sizeof(float) * ND, cudaMemcpyDeviceToDevice, s));
+    };
+    auto restore = [&](const float* src, const te::Scalars& sc) {
+        h->hsc = sc;
+        A(cudaMemcpyAsync(h->x + (size_t)sc.xbuf * ns, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemcpyAsync(h->u, src + ns, sizeof(float) * E, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemcpyAsync(h->w, src + ns + E, sizeof(float) * E, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemcpyAsync(h->lam, src + ns + 2 * E, sizeof(float) * ND, cudaMemcpyDeviceToDevice, s));
+        A(cudaMemcpyAsync(h->sc, &h->hsc, sizeof(te::Scalars), cudaMemcpyHostToDevice, s));
+    };
+    // forward, keeping every ck-th state
+    for (long long k = 0; k < K && ce == cudaSuccess; ++k) {
+        if (k % ck == 0) {
+            save(ckb + state * (size_t)(k / ck));
+            ck_sc[(size_t)(k / ck)] = h->hsc;
+        }
+        if ((st = te_solve(h, 1, nullptr)) != TE_OK) { release(); return st; }
+    }
+    const float beta = (float)h->hsc.beta, alpha = (float)h->hsc.alpha;
+    A(cudaMemsetAsync(B.ub, 0, sizeof(double) * E, s));
+    A(cudaMemsetAsync(B.db, 0, sizeof(double) * E, s));
+    A(cudaMemsetAsync(B.Cb, 0, sizeof(double) * E, s));
+    A(cudaMemsetAsync(B.wbar, 0, sizeof(double) * E, s));
+    A(cudaMemsetAsync(B.Db, 0, sizeof(double) * ND, s));
+    A(cudaMemsetAsync(B.acc, 0, sizeof(double), s));
+    A(te::adjoint_objective(L, h->x + (size_t)h->hsc.xbuf * ns, h->hsc.alpha, h->scale, B, s));
+    h->launches += 1;
+    // reverse, one checkpoint segment at a time (each recomputed forward first)
+    for (long long k0 = K > 0 ? ((K - 1) / ck) * ck : -1; k0 >= 0 && ce == cudaSuccess; k0 -= ck) {
+        const long long k1 = std::min(k0 + ck, K);
+        restore(ckb + state * (size_t)(k0 / ck), ck_sc[(size_t)(k0 / ck)]);
+        for (long long k = k0; k <= k1; ++k) {
+            save(seg + state * (size_t)(k - k0));
+            if (k < k1 && (st = te_solve(h, 1, nullptr)) != TE_OK) { release(); return st; }
+        }
+        for (long long k = k1 - 1; k >= k0; --k) {
+            const float* sk = seg + state * (size_t)(k - k0);
+            const float* s1 = seg + state * (size_t)(k + 1 - k0);
+            A(te::adjoint_step(L, sk, s1, s1 + ns, sk + ns + E, beta, alpha, B, s));
+            h->launches += te::kAdjointStepLaunches;
+        }
+    }
+    A(te::adjoint_finish(L, h->scale, B, gC, gD, s));
+    h->launches += 2;
+    double J = 0.0;
+    A(cudaMemcpyAsync(&J, B.acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (!out_is_device) {
+        A(cudaMemcpyAsync(dJ_dC, gC, sizeof(double) * E, cudaMemcpyDeviceToHost, s));
+        A(cudaMemcpyAsync(dJ_dD, gD, sizeof(double) * (size_t)L.K, cudaMemcpyDeviceToHost, s));
+    }
+    A(cudaStreamSynchronize(s));
+    release();
+    if (ce != cudaSuccess) return h->cuda(ce, "te_gradient");
+    if (J_out) *J_out = J;
+    return TE_OK;
 }

@@ -33,7 +33,8 @@ STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "T
 EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_gap", "te_prices",
             "te_set_warm_start", "te_set_demands", "te_set_capacities", "te_reset", "te_trace", "te_layout",
             "te_destroy", "te_last_error", "te_gap_noalloc", "te_batch_create", "te_batch_solve",
-            "te_batch_allocation", "te_batch_reset", "te_batch_info", "te_batch_destroy", "te_batch_last_error")
+            "te_batch_allocation", "te_batch_reset", "te_batch_info", "te_batch_destroy", "te_batch_last_error",
+            "te_gradient")
 
 
 class TEError(RuntimeError):
@@ -129,6 +130,8 @@ def _load() -> ctypes.CDLL:
     lib.te_destroy.argtypes = [H]
     lib.te_last_error.restype = ctypes.c_char_p
     lib.te_last_error.argtypes = [H]
+    lib.te_gradient.restype = ctypes.c_int
+    lib.te_gradient.argtypes = [H, ctypes.c_int64, ctypes.c_int32, P, P, P, ctypes.c_int32]
     lib.te_batch_create.restype = ctypes.c_int
     lib.te_batch_create.argtypes = [P, ctypes.c_int32, P, P, P, P, ctypes.POINTER(ctypes.c_void_p)]
     lib.te_batch_solve.restype = ctypes.c_int
@@ -321,6 +324,7 @@ class TE:
     def __init__(self, inst, **options):
         self.n_paths = int(inst.n_paths)
         self.n_edges = int(inst.n_edges)
+        self.n_demands = int(inst.n_demands)
         self.options = te_default_options(**options)
         self.h = te_create(inst, self.options)
 
@@ -350,6 +354,16 @@ class TE:
 
     def set_capacities(self, capacities) -> None:
         te_set_capacities(self.h, capacities)
+
+    def gradient(self, iters: int, checkpoint: int = 20):
+        """(J, dJ/dC [n_edges], dJ/dD [n_demands]) of J = sum_c U_alpha(S_c)
+        after `iters` fixed-schedule iterations from the initial state (the
+        handle must use the fixed schedule; see te_gradient)."""
+        J = ctypes.c_double()
+        gC = np.zeros(self.n_edges, dtype=np.float64)
+        gD = np.zeros(self.n_demands, dtype=np.float64)
+        _check(_lib.te_gradient(self.h, int(iters), int(checkpoint), ctypes.byref(J), _ptr(gC), _ptr(gD), 0), self.h)
+        return J.value, gC, gD
 
     def reset(self) -> None:
         te_reset(self.h)
@@ -430,3 +444,33 @@ class TEBatch:
             self.close()
         except Exception:
             pass
+
+
+def make_objective(inst, alpha: float, beta0: float, iters: int, checkpoint: int = 20, **options):
+    """A torch.autograd.Function over (capacities, demands) -> J = sum_c
+    U_alpha(S_c) after `iters` fixed-schedule iterations (caller units),
+    whose backward is the library's hand-written reverse pass (te_gradient).
+    Each call builds a handle for the given capacities and demands."""
+    import torch
+    from .instances import Instance
+
+    class _Objective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, C, D):
+            I = Instance(inst.name, inst.n_nodes, inst.edge_src, inst.edge_dst,
+                         C.detach().double().cpu().numpy(), inst.demand_src, inst.demand_dst,
+                         D.detach().double().cpu().numpy(), inst.demand_path_off, inst.path_edge_off,
+                         inst.path_edges, dict(inst.meta))
+            t = TE(I, alpha_target=alpha, alpha_start=alpha, beta0=beta0, adapt_beta=0, continuation=0,
+                   gamma=-1.0, scale_mode=2, **options)
+            J, gC, gD = t.gradient(iters, checkpoint)
+            t.close()
+            ctx.save_for_backward(torch.from_numpy(gC).to(C.device, C.dtype), torch.from_numpy(gD).to(D.device, D.dtype))
+            return torch.tensor(J, dtype=C.dtype, device=C.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gC, gD = ctx.saved_tensors
+            return gJ * gC, gJ * gD
+
+    return _Objective.apply

@@ -1,0 +1,91 @@
+"""The hand-written reverse pass on the GPU (te_gradient) against the FP64
+oracle's reverse pass and against FP64 central differences of the oracle's
+objective, and through torch.autograd."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_01748_b300.instances import Instance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def te():
+    from paper_2605_01748_b300 import build
+    build.build_te()
+    from paper_2605_01748_b300 import te as te_mod
+    return te_mod
+
+
+def _beta0(inst):
+    """1 / (mean path length * mean initial rate), caller units."""
+    return inst.n_paths ** 2 / (inst.nnz * inst.demand.sum())
+
+
+def _with(inst, C=None, D=None):
+    return Instance(inst.name, inst.n_nodes, inst.edge_src, inst.edge_dst, inst.capacity if C is None else C,
+                    inst.demand_src, inst.demand_dst, inst.demand if D is None else D, inst.demand_path_off,
+                    inst.path_edge_off, inst.path_edges, {})
+
+
+def _fixed(te, inst, alpha, beta0):
+    return te.TE(inst, alpha_target=alpha, alpha_start=alpha, beta0=beta0, adapt_beta=0, continuation=0,
+                 gamma=-1.0, scale_mode=2)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 2.0])
+def test_gradient_matches_oracle_tiny(te, tiny, alpha):
+    K, b0 = 40, _beta0(tiny)
+    t = _fixed(te, tiny, alpha, b0)
+    J, gC, gD = t.gradient(K, 7)
+    Jo, gCo, gDo = O.gradient(tiny, alpha, b0, K)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    g, go = np.concatenate([gC, gD]), np.concatenate([gCo, gDo])
+    assert np.max(np.abs(g - go)) <= 1e-3 * np.max(np.abs(go))
+    # central differences of the FP64 objective on a few coordinates
+    rng = np.random.default_rng(5)
+    for e in rng.choice(tiny.n_edges, 4, replace=False):
+        h = 1e-6 * tiny.capacity[e]
+        C1, C2 = tiny.capacity.copy(), tiny.capacity.copy()
+        C1[e] += h
+        C2[e] -= h
+        fd = (O.gradient(_with(tiny, C=C1), alpha, b0, K)[0] - O.gradient(_with(tiny, C=C2), alpha, b0, K)[0]) / (2 * h)
+        assert abs(fd - gC[e]) <= 1e-3 * np.max(np.abs(go))
+    t.close()
+
+
+def test_gradient_matches_oracle_medium_alpha1(te, medium):
+    """Differentiated alpha = 1 form on the 200-node instance: 200
+    iterations, checkpoints every 20."""
+    K, b0 = 200, _beta0(medium)
+    t = _fixed(te, medium, 1.0, b0)
+    J, gC, gD = t.gradient(K, 20)
+    Jo, gCo, gDo = O.gradient(medium, 1.0, b0, K)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    g, go = np.concatenate([gC, gD]), np.concatenate([gCo, gDo])
+    rel2 = np.linalg.norm(g - go) / np.linalg.norm(go)
+    assert rel2 <= 1e-2, rel2
+    t.close()
+
+
+def test_autograd_function(te, tiny):
+    import torch
+    K, b0 = 30, _beta0(tiny)
+    f = te.make_objective(tiny, 1.0, b0, K, checkpoint=10)
+    C = torch.tensor(tiny.capacity, dtype=torch.float64, requires_grad=True)
+    D = torch.tensor(tiny.demand, dtype=torch.float64, requires_grad=True)
+    J = f(C, D)
+    J.backward()
+    Jo, gCo, gDo = O.gradient(tiny, 1.0, b0, K)
+    assert abs(J.item() - Jo) <= 1e-5 * abs(Jo)
+    g = np.concatenate([C.grad.numpy(), D.grad.numpy()])
+    go = np.concatenate([gCo, gDo])
+    assert np.max(np.abs(g - go)) <= 1e-3 * np.max(np.abs(go))
+
+
+def test_gradient_rejects_adaptive_schedule(te, tiny):
+    t = te.TE(tiny)
+    with pytest.raises(te.TEError):
+        t.gradient(10)
+    t.close()

@@ -1,0 +1,60 @@
+"""Parity and properties at the full 1500-node size, in the launch
+configuration the benchmark times (148 CTAs, the layout te_create builds for
+it): the first iterations element by element against the FP64 oracle, and
+properties that hold at any size after many iterations (bit-identical
+repeated runs, feasibility of both feasibility steps, demand caps)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2605_01748_b300 import instances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def te():
+    from paper_2605_01748_b300 import build
+    build.build_te()
+    from paper_2605_01748_b300 import te as te_mod
+    return te_mod
+
+
+@pytest.fixture(scope="module")
+def large():
+    return instances.make("large", threads=os.cpu_count() or 0)
+
+
+def test_large_first_iterations_match_oracle(te, large):
+    t = te.TE(large)
+    t.solve(3)
+    x = t.allocation(project=te.PROJECT_NONE).astype(np.float64)
+    t.close()
+    s = O.OracleSolver(large, threads=os.cpu_count() or 0)
+    s.run(3)
+    xo = s.allocation()
+    assert np.max(np.abs(x - xo)) <= 1e-4 * np.max(np.abs(xo))
+    S, So = O.demand_totals(large, x), O.demand_totals(large, xo)
+    assert np.max(np.abs(S - So) / np.maximum(So, 1e-2 * So.max())) <= 1e-4
+
+
+def test_large_runs_repeat_and_stay_feasible(te, large):
+    t = te.TE(large)
+    r1 = t.solve(300)
+    x1 = t.allocation(project=te.PROJECT_NONE)
+    t.reset()
+    r2 = t.solve(300)
+    x2 = t.allocation(project=te.PROJECT_NONE)
+    assert r1 == r2
+    assert np.array_equal(x1.view(np.uint32), x2.view(np.uint32))
+    # the iterate respects the demand caps (the x-block holds S_c <= D_c)
+    S = O.demand_totals(large, x1.astype(np.float64))
+    assert (S <= large.demand * (1 + 1e-5)).all()
+    for mode in (te.PROJECT_ALG2, te.PROJECT_SCALE):
+        xp = t.allocation(project=mode).astype(np.float64)
+        assert (xp >= 0).all()
+        assert (O.demand_totals(large, xp) <= large.demand * (1 + 1e-5)).all()
+        assert (O.edge_loads(large, xp) <= large.capacity * (1 + 1e-5)).all()
+    t.close()

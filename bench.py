@@ -71,16 +71,35 @@ def parse():
     return ap.parse_args()
 
 
-def dist_setup():
+def dist_setup(backend: str = "nccl"):
+    """One process per GPU (torchrun's RANK / LOCAL_RANK / WORLD_SIZE).  The
+    ranks solve independent replicas: the only collectives are the barriers
+    around the timed region and the maximum of the timings."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        backend = "nccl"
         dist.init_process_group(backend=backend)
         return ws, rank, local, dist
     return 1, 0, local, None
+
+
+def max_over_ranks(values, dist, device=None):
+    """Elementwise maximum of a list of floats over all ranks (the values
+    themselves with one rank)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def shard(n: int, rank: int, world: int) -> list:
+    """Instances of a what-if batch that rank takes: i = rank, rank + world,
+    ... (no exchange between ranks)."""
+    return list(range(rank, n, world))
 
 
 def workload_desc(inst) -> str:
@@ -310,12 +329,7 @@ def run_ours(a, ws, rank, local, dist):
 
     # maximum over ranks
     ms_step = total_ms / a.steps
-    if dist:
-        v = torch.tensor([ms_step, statistics.mean(e2e_ms)], device=dev)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        ms_step, e2e_mean = float(v[0]), float(v[1])
-    else:
-        e2e_mean = statistics.mean(e2e_ms)
+    ms_step, e2e_mean = max_over_ranks([ms_step, statistics.mean(e2e_ms)], dist, dev)
 
     solve_mean = statistics.mean(solve_ms)
     achieved = lay["bytes_per_iter"] * K / (solve_mean * 1e-3) / 1e9
@@ -529,7 +543,7 @@ def run_ablation(a):
     print(json.dumps(out), flush=True)
 
 
-def run_batch(a):
+def run_batch(a, ws=1, rank=0, dist=None):
     """The batch engine against the plain loop on the same GPU: every
     instance of the what-if batch (a.batch failure scenarios of the 500-node
     WAN, each removing 1-3 links, x 4 demand matrices perturbed by a clipped
@@ -542,11 +556,15 @@ def run_batch(a):
     import torch
     from paper_2605_01748_b300 import instances, te
 
-    torch.cuda.set_device(0)
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     t0 = time.time()
     base = instances.make_batch_base(threads=os.cpu_count() or 0)
-    W = instances.make_what_if(base, a.batch, 4, seed=0)
+    W_all = instances.make_what_if(base, a.batch, 4, seed=0)
+    # under torchrun each rank takes its share of the instances (no exchange)
+    mine = shard(len(W_all), rank, ws)
+    W = [W_all[i] for i in mine]
     gen_s = time.time() - t0
     K = a.batch_iters
     opts = dict(gamma=-1.0)
@@ -566,10 +584,13 @@ def run_batch(a):
     b.close()
     assert all(r["iters"] == K for r in res)
     loop_ms = 0.0
-    for sidx in range(a.batch):
-        t = te.TE(W[4 * sidx], cuda_stream=stream.cuda_stream, **opts)
-        for m in range(4):
-            t.set_demands(W[4 * sidx + m].demand)
+    first = {}
+    for i in mine:  # one handle per scenario, its matrices through te_set_demands
+        first.setdefault(i // 4, i)
+    for sidx, i0 in first.items():
+        t = te.TE(W_all[i0], cuda_stream=stream.cuda_stream, **opts)
+        for i in [i for i in mine if i // 4 == sidx]:
+            t.set_demands(W_all[i].demand)
             t.reset()
             e0.record(stream)
             t.solve(K)
@@ -577,12 +598,15 @@ def run_batch(a):
             torch.cuda.synchronize()
             loop_ms += e0.elapsed_time(e1)
         t.close()
+    batch_ms, loop_ms = max_over_ranks([batch_ms, loop_ms], dist, torch.device("cuda", local))
+    if rank != 0:
+        return
     peaks = {}
     if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     hbm = float(peaks.get("hbm_gbs", 6400.0))
-    n = len(W)
-    achieved = info["bytes_per_iter"] * K / (batch_ms * 1e-3) / 1e9
+    n = len(W_all)
+    achieved = info["bytes_per_iter"] * ws * K / (batch_ms * 1e-3) / 1e9
     out = {"mode": "batch", "workload": f"what-if batch: {a.batch} failure scenarios x 4 demand matrices = {n} "
                                          f"instances of the 500-node WAN ({base.n_edges} directed edges, "
                                          f"{base.n_demands} demands, k=8, {info['n_paths']} paths in all)",
@@ -654,7 +678,7 @@ def main():
     a = parse()
     ws, rank, local, dist = dist_setup()
     if a.batch > 0:
-        run_batch(a)
+        run_batch(a, ws, rank, dist)
     elif a.ablation:
         run_ablation(a)
     elif a.impl == "reference":

@@ -16,6 +16,8 @@ Functions (all FP64; paper references are to GATE, Section 3 and Appendix B):
 * :func:`project_scale` -- a proportional feasibility scaling (not in the
   paper; scales where Algorithm 2 trims whole paths).
 * :func:`gap` -- the Lagrangian duality gap of a feasible allocation.
+* :func:`maxmin_single_path` -- exact max-min fair rates of single-path
+  demands (progressive filling), the exact optimum of the k = 1 variants.
 * :func:`gradient` -- the fairness objective after K fixed-schedule
   iterations and its gradient in capacities and demands (reverse mode,
   checkpointed; not in the paper).
@@ -88,6 +90,8 @@ def _L() -> ctypes.CDLL:
                                         ctypes.c_int64]
         lib.or_project.restype = None
         lib.or_project.argtypes = [P, P, ctypes.c_double]
+        lib.or_maxmin_single_path.restype = ctypes.c_int
+        lib.or_maxmin_single_path.argtypes = [P, P]
         lib.or_gradient.restype = ctypes.c_int
         lib.or_gradient.argtypes = [P, P, ctypes.c_int64, ctypes.c_int64, P, P, P]
         lib.or_project_scale.restype = None
@@ -235,6 +239,16 @@ def project_scale(inst, x: np.ndarray) -> np.ndarray:
     out = np.array(x, dtype=np.float64, copy=True)
     _L().or_project_scale(ctypes.byref(v.s), out.ctypes.data)
     return out
+
+
+def maxmin_single_path(inst) -> np.ndarray:
+    """Exact max-min fair demand rates when every demand has one path
+    (progressive filling), caller units."""
+    view = _InstanceView(inst)
+    rate = np.zeros(inst.n_demands, dtype=np.float64)
+    if _L().or_maxmin_single_path(ctypes.byref(view.s), rate.ctypes.data) != 0:
+        raise ValueError("maxmin_single_path needs exactly one path per demand")
+    return rate
 
 
 def gradient(inst, alpha: float, beta0: float, iters: int, checkpoint: int = 20, scale_mode: int = 2,

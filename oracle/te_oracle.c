@@ -746,6 +746,109 @@ void or_project(const or_instance* I, double* x, double alpha) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Exact max-min fair rates when every demand has a single path          */
+/* (progressive filling, textbook water-filling): all unfrozen demands   */
+/* rise together; a demand freezes when it reaches D_c or when an edge   */
+/* on its path fills.  Events in increasing level, edges in a binary    */
+/* heap keyed by the level at which they fill, (C_e - frozen load) /     */
+/* (unfrozen demands through e); stale heap entries are skipped.         */
+/* rate[K] out (caller units).  Returns 1 if a demand has != 1 path.    */
+/* ------------------------------------------------------------------ */
+typedef struct { double key; int e; } or_hent;
+
+static void heap_push(or_hent* h, int64_t* n, double key, int e) {
+    int64_t i = (*n)++;
+    h[i].key = key; h[i].e = e;
+    while (i > 0) {
+        const int64_t p = (i - 1) / 2;
+        if (h[p].key <= h[i].key) break;
+        const or_hent t = h[p]; h[p] = h[i]; h[i] = t;
+        i = p;
+    }
+}
+
+static or_hent heap_pop(or_hent* h, int64_t* n) {
+    const or_hent top = h[0];
+    h[0] = h[--(*n)];
+    int64_t i = 0;
+    for (;;) {
+        const int64_t l = 2 * i + 1, r = l + 1;
+        int64_t m = i;
+        if (l < *n && h[l].key < h[m].key) m = l;
+        if (r < *n && h[r].key < h[m].key) m = r;
+        if (m == i) break;
+        const or_hent t = h[m]; h[m] = h[i]; h[i] = t;
+        i = m;
+    }
+    return top;
+}
+
+static int dbl_idx_cmp(const void* a, const void* b) {
+    const or_keyed* p = (const or_keyed*)a;
+    const or_keyed* q = (const or_keyed*)b;
+    return (p->key > q->key) - (p->key < q->key);
+}
+
+int or_maxmin_single_path(const or_instance* I, double* rate) {
+    const int E = I->n_edges;
+    const int32_t K = I->n_demands;
+    for (int32_t c = 0; c < K; ++c) if (I->dpo[c + 1] - I->dpo[c] != 1) return 1;
+    or_csc T;
+    csc_build(I, &T);  /* edge -> paths; path r is demand r here */
+    double* frozen = (double*)calloc((size_t)E, sizeof(double));
+    int64_t* cnt = (int64_t*)calloc((size_t)E, sizeof(int64_t));
+    unsigned char* done = (unsigned char*)calloc((size_t)K, 1);
+    unsigned char* full = (unsigned char*)calloc((size_t)E, 1);
+    for (int64_t i = 0; i < I->nnz; ++i) cnt[I->pe[i]]++;
+    or_hent* heap = (or_hent*)malloc(sizeof(or_hent) * (size_t)(I->nnz + E + 1));
+    int64_t hn = 0;
+    for (int e = 0; e < E; ++e) if (cnt[e] > 0) heap_push(heap, &hn, I->cap[e] / (double)cnt[e], e);
+    or_keyed* dem = (or_keyed*)malloc(sizeof(or_keyed) * (size_t)(K > 0 ? K : 1));
+    for (int32_t c = 0; c < K; ++c) { dem[c].key = I->demand[c]; dem[c].path = c; }
+    qsort(dem, (size_t)K, sizeof(or_keyed), dbl_idx_cmp);
+    int64_t di = 0;
+    /* freezes demand c at level t: its edges lose one unfrozen demand */
+    #define OR_FREEZE(cc, tt) do { \
+        const int32_t c_ = (cc); const double t_ = (tt); \
+        done[c_] = 1; rate[c_] = t_; \
+        const int64_t r_ = I->dpo[c_]; \
+        for (int64_t i_ = I->peo[r_]; i_ < I->peo[r_ + 1]; ++i_) { \
+            const int e_ = I->pe[i_]; \
+            frozen[e_] += t_; cnt[e_]--; \
+            if (cnt[e_] > 0 && !full[e_]) heap_push(heap, &hn, (I->cap[e_] - frozen[e_]) / (double)cnt[e_], e_); \
+        } } while (0)
+    for (;;) {
+        while (di < K && done[dem[di].path]) ++di;
+        /* drop stale heap tops (an edge filled, or its key moved) */
+        while (hn > 0) {
+            const or_hent h = heap[0];
+            if (full[h.e] || cnt[h.e] == 0 || h.key != (I->cap[h.e] - frozen[h.e]) / (double)cnt[h.e]) {
+                heap_pop(heap, &hn);
+                continue;
+            }
+            break;
+        }
+        const double te_ = hn > 0 ? heap[0].key : INFINITY;
+        const double td = di < K ? dem[di].key : INFINITY;
+        if (!(te_ < INFINITY) && !(td < INFINITY)) break;
+        if (td <= te_) {
+            OR_FREEZE((int32_t)dem[di].path, td);
+            continue;
+        }
+        const or_hent h = heap_pop(heap, &hn);
+        full[h.e] = 1;
+        for (int64_t i = T.off[h.e]; i < T.off[h.e + 1]; ++i) {
+            const int32_t c = (int32_t)T.path[i];
+            if (!done[c]) OR_FREEZE(c, h.key);
+        }
+    }
+    #undef OR_FREEZE
+    free(frozen); free(cnt); free(done); free(full); free(heap); free(dem);
+    csc_free(&T);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Proportional feasibility scaling -- not in the paper: an alternative  */
 /* to Algorithm 2 that scales instead of trimming, so that no demand    */
 /* with a positive rate loses all of it.  x[P] in/out (units of cap and  */

@@ -226,3 +226,30 @@ def test_thread_count_does_not_change_results(tiny):
     a = O.solve(tiny, max_iters=120, alpha_target=math.inf, threads=1)
     b = O.solve(tiny, max_iters=120, alpha_target=math.inf, threads=4)
     assert np.array_equal(a.x, b.x) and np.array_equal(a.u, b.u)
+
+
+def test_exact_single_path_max_min_matches_progressive_filling(tiny):
+    """The oracle's event-driven water-filling against the textbook
+    progressive filling (rounds of equal increments) on single-path demands."""
+    inst = R.first_path_only(tiny)
+    a = O.maxmin_single_path(inst)
+    b = R.progressive_filling(inst)
+    assert np.max(np.abs(a - b) / np.maximum(b, 1e-12)) <= 1e-12
+
+
+def test_exact_single_path_max_min_is_max_min(medium):
+    """Feasible, and every demand is either at its cap or crosses a full
+    edge on which no demand has a larger rate (the max-min certificate)."""
+    inst = R.first_path_only(medium)
+    a = O.maxmin_single_path(inst)
+    L = O.edge_loads(inst, a)
+    assert (L <= inst.capacity * (1 + 1e-12)).all()
+    assert (a <= inst.demand * (1 + 1e-12)).all()
+    full = L >= inst.capacity * (1 - 1e-9)
+    emax = np.zeros(inst.n_edges)
+    np.maximum.at(emax, inst.path_edges, a[np.repeat(np.arange(inst.n_demands), np.diff(inst.path_edge_off))])
+    for c in range(inst.n_demands):
+        if a[c] >= inst.demand[c] * (1 - 1e-12):
+            continue
+        es = inst.path_edges[inst.path_edge_off[c]:inst.path_edge_off[c + 1]]
+        assert any(full[e] and a[c] >= emax[e] * (1 - 1e-9) for e in es), c

@@ -66,6 +66,9 @@ def parse():
                     help="what-if batch on the 500-node WAN: SCENARIOS failure scenarios x 4 demand matrices, "
                          "the batch engine against a loop of single-instance solves, one JSON line")
     ap.add_argument("--batch-iters", type=int, default=2000)
+    ap.add_argument("--exact-k1", action="store_true",
+                    help="the solver's max-min on the single-path (k = 1) variants of the 200- and 1500-node "
+                         "workloads against their exact max-min (progressive filling), one JSON line each")
     ap.add_argument("--iters", type=int, default=0,
                     help="profiling runs only: use this K and skip the reference run and the probe")
     return ap.parse_args()
@@ -623,6 +626,52 @@ def run_batch(a, ws=1, rank=0, dist=None):
     print(json.dumps(out), flush=True)
 
 
+def run_exact_k1(a):
+    """Optimality (Section 4.1) of the solver's max-min against the exact
+    max-min of single-path demands: the first path of every demand of the
+    200- and 1500-node workloads, progressive filling on the host (FP64
+    oracle), the solver with default options probed every 250 iterations
+    until its stop rule fires."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2605_01748_b300 import instances, te
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    for name in ("medium", "large"):
+        full = instances.make(name, threads=os.cpu_count() or 0)
+        keep = np.zeros(full.n_paths, dtype=bool)
+        keep[full.demand_path_off[:-1]] = True
+        inst = instances.drop_paths(full, keep, name=name + "-k1")
+        inst.meta["k"] = 1
+        t0 = time.time()
+        exact = O.maxmin_single_path(inst)
+        wf_s = time.time() - t0
+        ev = Optimality(inst, dev)
+        ev.opt = torch.from_numpy(np.maximum(exact, ev.theta)).to(dev)
+        x = torch.empty(inst.n_paths, dtype=torch.float32, device=dev)
+        t = te.TE(inst, cuda_stream=stream.cuda_stream)
+        rows, first = [], None
+        while True:
+            r = t.solve(250)
+            te.te_allocation(t.h, x, te.PROJECT_SCALE)
+            q = ev(x)
+            te.te_allocation(t.h, x, te.PROJECT_ALG2)
+            q2 = ev(x)
+            rows.append((r["total_iters"], r["alpha"], round(q, 5), round(q2, 5)))
+            if first is None and q >= a.target:
+                first = r["total_iters"]
+            if r["converged"] or r["total_iters"] >= a.ref_iters:
+                break
+        t.close()
+        print(json.dumps({"mode": "exact-k1", "workload": workload_desc(inst), "exact_host_s": round(wf_s, 1),
+                          "iters_to_target": first, "stop": rows[-1], "trace_tail": rows[-5:],
+                          "columns": "iterations, alpha, optimality (proportional scaling), optimality (Algorithm 2)"}),
+              flush=True)
+
+
 def run_reference(a, ws, rank):
     """The FP64 CPU oracle as it stands, on the host cores, same workload and
     metric.  Each step runs a bounded sample of oracle iterations on the full
@@ -677,7 +726,9 @@ def run_reference(a, ws, rank):
 def main():
     a = parse()
     ws, rank, local, dist = dist_setup()
-    if a.batch > 0:
+    if a.exact_k1:
+        run_exact_k1(a)
+    elif a.batch > 0:
         run_batch(a, ws, rank, dist)
     elif a.ablation:
         run_ablation(a)

@@ -253,3 +253,26 @@ def test_exact_single_path_max_min_is_max_min(medium):
             continue
         es = inst.path_edges[inst.path_edge_off[c]:inst.path_edge_off[c + 1]]
         assert any(full[e] and a[c] >= emax[e] * (1 - 1e-9) for e in es), c
+
+
+def test_printed_rate_suggestion_does_not_see_capacity(tiny):
+    """The reading of the update equations: the rate suggestion as printed
+    (Section 3.3, the cost of Eq. "penalty-b" and the suggestion built from
+    its mean over the edge) subtracts from each path's cost the mean over
+    the edge, so every term that is the same for all paths of the edge --
+    the capacity and the capacity dual among them -- cancels.  Evaluating
+    the printed formula for two capacities gives the same suggestions; the
+    paper-literal multi-block variant would not enforce capacity, which is
+    why the two-block reading (the capacity projection in the edge block)
+    is implemented instead."""
+    rng = np.random.default_rng(0)
+    n = 7
+    x = rng.uniform(0, 5, n)
+    dual_con = rng.uniform(0, 1, n)
+    beta = 0.7
+
+    def printed(C, dual_cap):
+        cost = beta * (-C - x) - dual_cap - dual_con
+        return np.maximum((cost.mean() - cost) / beta, 0.0)
+
+    assert np.allclose(printed(1.0, 0.3), printed(100.0, 7.0), rtol=0, atol=1e-12)

@@ -7,7 +7,6 @@
 
 #include <algorithm>
 #include <string>
-#include <thread>
 #include <utility>
 #include <vector>
 

@@ -194,13 +194,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def ncu_traffic(kernel_src: str):
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2605_01748_b300", "csrc", f)
+                  for f in ("te_iter.cu", "te_kernels.cuh", "te_internal.cuh")]
+
+
+def kernel_hash() -> str:
+    """Hash of the iteration kernel's sources (the kernel and its shared device code)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
     """DRAM bytes per iteration from the committed ncu summary, or None when the
-    kernel source changed since that capture."""
+    kernel sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", "k_iter_large.md")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    h = kernel_hash()
     src_hash, per_iter = None, None
     for ln in open(path):
         if ln.startswith("kernel_source_sha256_16:"):
@@ -336,7 +348,7 @@ def run_ours(a, ws, rank, local, dist):
 
     solve_mean = statistics.mean(solve_ms)
     achieved = lay["bytes_per_iter"] * K / (solve_mean * 1e-3) / 1e9
-    traffic_iter = ncu_traffic(os.path.join(ROOT, "paper_2605_01748_b300", "csrc", "te_iter.cu"))
+    traffic_iter = ncu_traffic()
     out = {
         "metric": METRIC,
         "value": round(ms_step, 4),

@@ -22,21 +22,6 @@ def _rel(a, b):
     return float(np.max(np.abs(np.asarray(a, np.float64) - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def test_what_if_generator_shares_paths_within_a_scenario(tiny):
-    W = instances.make_what_if(tiny, 3, 2, seed=1, min_fail=1, max_fail=2)
-    assert len(W) == 6
-    for s in range(3):
-        a, b = W[2 * s], W[2 * s + 1]
-        assert a.path_edges is b.path_edges and a.demand_path_off is b.demand_path_off
-        failed = a.meta["failed_links"]
-        dead = np.zeros(tiny.n_edges, bool)
-        for l in failed:
-            dead[2 * l] = dead[2 * l + 1] = True
-        assert not dead[a.path_edges].any()
-        assert (a.capacity[dead] == 0).all()
-        assert (np.abs(a.demand / b.demand - 1) <= 0.5).all()
-
-
 def test_batch_matches_oracle_per_instance(te, tiny):
     W = instances.make_what_if(tiny, 3, 2, seed=2, min_fail=1, max_fail=1)
     kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)

@@ -84,3 +84,33 @@ def test_medium_shape(medium):
 def test_subset_roundtrip(tiny):
     sub = instances.subset(tiny, np.arange(tiny.n_demands))
     assert sub.digest() == tiny.digest()
+
+
+def test_what_if_generator_shares_paths_within_a_scenario(tiny):
+    W = instances.make_what_if(tiny, 3, 2, seed=1, min_fail=1, max_fail=2)
+    assert len(W) == 6
+    for s in range(3):
+        a, b = W[2 * s], W[2 * s + 1]
+        assert a.path_edges is b.path_edges and a.demand_path_off is b.demand_path_off
+        failed = a.meta["failed_links"]
+        dead = np.zeros(tiny.n_edges, bool)
+        for l in failed:
+            dead[2 * l] = dead[2 * l + 1] = True
+        assert not dead[a.path_edges].any()
+        assert (a.capacity[dead] == 0).all()
+        assert (np.abs(a.demand / b.demand - 1) <= 0.5).all()
+
+
+def test_drop_paths_keeps_the_chosen_paths(tiny):
+    rng = np.random.default_rng(0)
+    keep = rng.random(tiny.n_paths) < 0.5
+    d = instances.drop_paths(tiny, keep)
+    assert d.n_paths == int(keep.sum())
+    kept = np.nonzero(keep)[0]
+    for j, r in enumerate(kept):
+        assert np.array_equal(d.path_edges[d.path_edge_off[j]:d.path_edge_off[j + 1]],
+                              tiny.path_edges[tiny.path_edge_off[r]:tiny.path_edge_off[r + 1]])
+    per = np.add.reduceat(keep.astype(int), tiny.demand_path_off[:-1])
+    assert d.n_demands == int((per > 0).sum())
+    assert np.array_equal(np.diff(d.demand_path_off), per[per > 0])
+    assert np.array_equal(d.demand, tiny.demand[per > 0])

@@ -291,3 +291,46 @@ def test_max_min_against_exact_single_path_optimum(te, medium):
     q = O.optimality(O.demand_totals(inst, x), opt, theta)
     assert q >= 0.975, q
     t.close()
+
+
+def _line_instance(n_nodes=256):
+    """A line of n_nodes nodes (both directions of every link) with
+    single-path demands up to the longest supported path (255 hops): their
+    blocks hold more id rows than a staging buffer, so the kernels read
+    those ids from global memory."""
+    from paper_2605_01748_b300.instances import Instance
+    L = n_nodes - 1
+    src = np.empty(2 * L, np.int32)
+    dst = np.empty(2 * L, np.int32)
+    src[0::2], dst[0::2] = np.arange(L), np.arange(1, L + 1)
+    src[1::2], dst[1::2] = np.arange(1, L + 1), np.arange(L)
+    cap = 1.0 + (np.arange(2 * L) % 7).astype(np.float64)
+    pairs = [(0, L), (0, L // 2), (10, 200), (L, 0), (30, 31), (100, 250), (5, 6), (250, 3)]
+    dpo, peo, pe, ds, dd = [0], [0], [], [], []
+    for s, t in pairs:
+        hops = [2 * i if t > s else 2 * (i - 1) + 1 for i in (range(s, t) if t > s else range(s, t, -1))]
+        pe.extend(hops)
+        peo.append(len(pe))
+        dpo.append(len(dpo))
+        ds.append(s)
+        dd.append(t)
+    D = np.linspace(0.5, 4.0, len(pairs))
+    return Instance("line", n_nodes, src, dst, cap, np.array(ds, np.int32), np.array(dd, np.int32), D,
+                    np.array(dpo, np.int64), np.array(peo, np.int64), np.array(pe, np.int32), {})
+
+
+def test_longest_paths_unstaged_blocks(te):
+    inst = _line_instance()
+    assert np.diff(inst.path_edge_off).max() == 255
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t, _, s = _pair(te, inst, 40, **kw)
+    _compare(inst, t.allocation(project=False), s.allocation())
+    for mode in (te.PROJECT_ALG2, te.PROJECT_SCALE):
+        xp = t.allocation(project=mode).astype(np.float64)
+        assert (O.edge_loads(inst, xp) <= inst.capacity * (1 + 1e-5)).all()
+    t.close()
+    b = te.TEBatch([inst, inst], **kw)
+    b.solve(40)
+    for i in range(2):
+        _compare(inst, b.allocation(i, project=te.PROJECT_NONE), s.allocation())
+    b.close()

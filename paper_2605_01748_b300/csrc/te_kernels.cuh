@@ -100,12 +100,20 @@ __device__ __forceinline__ float slack_root(float A, float H, float logbeta, flo
         const float s = fmaf(H, et, A);
         float tn;
         if (s > 0.f) {
-            const float g = __logf(s) + (t + logbeta) * ia;
+            const float ls = __logf(s), lt = (t + logbeta) * ia;
+            const float g = ls + lt;
             if (g > 0.f) thi = t; else tlo = t;
             // the step only has to move t towards the root: its quotients
             // may be approximate (the accepted t still solves g(t) = 0)
             const float dg = __fdividef(H * et, s) + ia;
             tn = t - __fdividef(g, dg);
+            // g carries the rounding error of its two terms (a few units in
+            // the last place of each, and of t + log beta); a Newton step no
+            // larger than that error divided by g', or than the tolerance,
+            // ends the loop, also where it does not fall strictly inside the
+            // bracket (g = 0 exactly, or a step that rounds back to t)
+            const float eg = fmaf(1.2e-7f * ia, fabsf(t) + fabsf(logbeta), 4e-7f * fmaxf(1.f, fabsf(ls)));
+            if (fabsf(tn - t) <= fmaxf(2e-7f * fmaxf(1.f, fabsf(t)), __fdividef(eg, dg))) { t = tn; break; }
         } else {
             tlo = t;
             tn = 0.5f * (tlo + thi);

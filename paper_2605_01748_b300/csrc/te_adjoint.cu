@@ -15,6 +15,8 @@
 //   on the active set A (x'_r > 0) of a demand, with a_r = 1/n_r, H = sum_A a,
 //   S = sum_A x', G = sum_A gb a: if the demand cap binds (S = D_c)
 //   dnu/dm_s = -1/H and Db += G/H, else (beta nu = U'(S))
+//   (whether the cap binds is the forward step's own decision, read back from
+//   its multiplier: binding iff beta nu <= U'(D_c))
 //   dnu/dm_s = -alpha nu / (S + alpha nu H); mb_s = gb_s + G dnu/dm_s on A, 0 off A
 //   xb = mb;  ub_e += sum_{r ni e} (-mb_r/n_r);  db_e = the same sum
 #include <math.h>
@@ -55,8 +57,9 @@ __global__ void k_adj_edges_in(int E, double* ub, double* db, const float* u1, c
 // per-demand step: one thread per demand slot.  xb (per path lane) is read
 // as the adjoint of x' and overwritten with the adjoint of x; wbar collects
 // the adjoint of w (zeroed by the caller).
-__global__ void k_adj_demands(Layout L, const float* __restrict__ x1, const double* __restrict__ Lb, double* xb,
-                              double* wbar, double* Db, float beta, float alpha) {
+__global__ void k_adj_demands(Layout L, const float* __restrict__ x1, const float* __restrict__ lam1,
+                              const double* __restrict__ Lb, double* xb, double* wbar, double* Db, float beta,
+                              float alpha) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * L.dpb) return;
     const int np = L.np[i];
@@ -87,14 +90,20 @@ __global__ void k_adj_demands(Layout L, const float* __restrict__ x1, const doub
         G += g * a;
         ++na;
     }
-    // Whether the cap binds is read from the demand total (S = D when it
-    // binds, S < D otherwise; the FP32 rates give S to about 1e-6), and on
-    // the slack branch the multiplier is U'(S) / beta.  Both avoid taking nu
-    // from x' - m, which cancels when the consensus target m is large.
+    // Whether the cap binds is the forward step's decision: it took the cap
+    // branch iff its multiplier lambda = beta nu is at most U'(D), where the
+    // target (beta nu)^(-1/alpha) reaches D (alpha = 0: lambda = 1 on the
+    // slack branch).  lambda is the FP32 value the step stored, so only a
+    // demand within a few units in the last place of the kink can be read
+    // on the other side.  On the slack branch the multiplier used is
+    // U'(S) / beta, which avoids taking nu from x' - m (that difference
+    // cancels when the consensus target m is large).
     double dnu = 0.0;  // d nu / d m_s on the active set
     if (na > 0) {
         const double D = (double)L.Dn[i];
-        if (S >= D * (1.0 - 1e-5)) {  // the demand cap binds
+        const double lam = (double)lam1[i];
+        const bool binds = alpha == 0.f ? lam < 1.0 - 1e-6 : lam * exp((double)alpha * log(D)) <= 1.0;
+        if (binds) {
             dnu = -1.0 / H;
             Db[i] += G / H;
         } else {
@@ -185,12 +194,12 @@ __global__ void k_adj_out(Layout L, const double* Cb, const double* Db, double i
 }  // namespace
 
 cudaError_t adjoint_step(const Layout& L, const float* xk, const float* x1, const float* uk1, const float* wk,
-                         float beta, float alpha, AdjointBuffers& B, cudaStream_t st) {
+                         const float* lam1, float beta, float alpha, AdjointBuffers& B, cudaStream_t st) {
     k_adj_edges_in<<<grid_for(L.E), kThreads, 0, st>>>(L.E, B.ub, B.db, uk1, L.ne_f, L.inv_ne, B.Lb, B.Cb);
     (void)xk;
     (void)wk;
-    k_adj_demands<<<grid_for((long long)L.nblocks * L.dpb), kThreads, 0, st>>>(L, x1, B.Lb, B.xb, B.wbar, B.Db, beta,
-                                                                             alpha);
+    k_adj_demands<<<grid_for((long long)L.nblocks * L.dpb), kThreads, 0, st>>>(L, x1, lam1, B.Lb, B.xb, B.wbar, B.Db,
+                                                                             beta, alpha);
     k_adj_edges_out<<<grid_for(L.E), kThreads, 0, st>>>(L.E, B.ub, B.db, B.wbar);
     return cudaGetLastError();
 }

@@ -801,7 +801,7 @@ extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint
         for (long long k = k1 - 1; k >= k0; --k) {
             const float* sk = seg + state * (size_t)(k - k0);
             const float* s1 = seg + state * (size_t)(k + 1 - k0);
-            A(te::adjoint_step(L, sk, s1, s1 + ns, sk + ns + E, beta, alpha, B, s));
+            A(te::adjoint_step(L, sk, s1, s1 + ns, sk + ns + E, s1 + ns + 2 * E, beta, alpha, B, s));
             h->launches += te::kAdjointStepLaunches;
         }
     }

@@ -169,10 +169,10 @@ struct AdjointBuffers {
     double* Db;    // [nblocks*dpb]
     double* acc;   // [1] objective
 };
-// xk, wk: rates and gather weights entering the iteration; x1, uk1: rates
-// and prices it produced.
+// xk, wk: rates and gather weights entering the iteration; x1, uk1, lam1:
+// rates, prices and per-demand multipliers (beta nu) it produced.
 cudaError_t adjoint_step(const Layout& L, const float* xk, const float* x1, const float* uk1, const float* wk,
-                         float beta, float alpha, AdjointBuffers& B, cudaStream_t st);
+                         const float* lam1, float beta, float alpha, AdjointBuffers& B, cudaStream_t st);
 // J of the rates x into acc and its adjoint into xb
 cudaError_t adjoint_objective(const Layout& L, const float* x, double alpha, double scale, AdjointBuffers& B,
                               cudaStream_t st);

@@ -55,17 +55,23 @@ def test_gradient_matches_oracle_tiny(te, tiny, alpha):
     t.close()
 
 
-def test_gradient_matches_oracle_medium_alpha1(te, medium):
-    """Differentiated alpha = 1 form on the 200-node instance: 200
-    iterations, checkpoints every 20."""
-    K, b0 = 200, _beta0(medium)
-    t = _fixed(te, medium, 1.0, b0)
+@pytest.mark.parametrize("alpha,K", [(1.0, 200), (2.0, 100)])
+def test_gradient_matches_oracle_medium(te, medium, alpha, K):
+    """Differentiated form on the 200-node instance, checkpoints every 20.
+    The forward pass runs in FP32 and the oracle's in FP64, so the two
+    trajectories part at the level of FP32 rounding; the adjoint takes every
+    branch (active path, binding cap, positive price) from the forward pass's
+    own FP32 state.  Measured: rel2 about 1e-6, largest element error about
+    3e-5 of the largest gradient entry."""
+    b0 = _beta0(medium)
+    t = _fixed(te, medium, alpha, b0)
     J, gC, gD = t.gradient(K, 20)
-    Jo, gCo, gDo = O.gradient(medium, 1.0, b0, K)
-    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    Jo, gCo, gDo = O.gradient(medium, alpha, b0, K)
+    assert abs(J - Jo) <= 1e-6 * abs(Jo)
     g, go = np.concatenate([gC, gD]), np.concatenate([gCo, gDo])
     rel2 = np.linalg.norm(g - go) / np.linalg.norm(go)
-    assert rel2 <= 1e-2, rel2
+    assert rel2 <= 1e-4, rel2
+    assert np.max(np.abs(g - go)) <= 1e-3 * np.max(np.abs(go))
     t.close()
 
 

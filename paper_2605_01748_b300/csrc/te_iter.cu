@@ -11,8 +11,8 @@
 //            edge ids of a block are brought into shared memory by one bulk
 //            asynchronous copy (TMA), issued one block ahead of use; the
 //            block's metadata record is loaded two blocks ahead.  The CTA then
-//            publishes its per-edge partial loads and its FP64 residual
-//            partials;
+//            publishes its per-edge partial loads and its residual partials
+//            (FP32 within a warp, FP64 across warps);
 //   grid barrier 1;
 //   phase B (every CTA, its own slice of the edges): the loads L_e as FP64
 //            sums of the CTAs' partials in a fixed order (so a run is
@@ -21,10 +21,11 @@
 //            collapse of the consensus duals) and its part of the primal
 //            residual; publishes the new gather weights;
 //   grid barrier 2;
-//   control (every CTA, identically): the residuals r and s (Eqs. 15-16,
-//            cross-CTA sums in FP64 in a fixed order), residual balancing
-//            (Eq. 17), the stop rule (Eq. 18) and alpha-continuation, then
-//            loads the new gather weights into shared memory.
+//   control (every CTA, identically, on thread 0): the residuals r and s
+//            (Eqs. 15-16, cross-CTA sums in FP64 in a fixed order), residual
+//            balancing (Eq. 17), the stop rule (Eq. 18) and
+//            alpha-continuation; the CTA then loads the new gather weights
+//            into shared memory.
 // Every wait (grid barriers, bulk copies) is bounded.
 //
 // Rates and prices are FP32.  The per-demand multiplier is kept in scaled
@@ -55,8 +56,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     const int e_lo = (int)((long long)blockIdx.x * E / NG), e_hi = (int)((long long)(blockIdx.x + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
     __shared__ __align__(8) unsigned long long s_mbar[kIterWarps * 2];
-    __shared__ double red[kIterWarps];
-    __shared__ double s_fin[4];
+    __shared__ float s_wred[kIterWarps][4];  // per-warp FP32 partials of the residual sums
+    __shared__ float s_par[4];   // this iteration's 1/beta, log beta, beta, alpha (FP32)
+    __shared__ float s_ratio;    // price rescale of the last balancing step
+    __shared__ int s_ctl;        // control decision: bit 0 numeric failure, bit 1 stop
     __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -89,11 +92,21 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         mbar_init(&ws.mb[1], 1);
         fence_mbar_init();
     }
+    // the scalar state is kept by thread 0, which takes the control
+    // decisions (FP64 is slow on this part: one thread does it and the CTA
+    // reads the results from shared memory)
     Scalars sc = *a.sc;
     int xbuf = sc.xbuf;
     sc.converged = 0;
     sc.stop_reason = 0;
     bool failed = false;
+    auto publish_params = [&]() {
+        s_par[0] = (float)(1.0 / sc.beta);
+        s_par[1] = (float)log(sc.beta);
+        s_par[2] = (float)sc.beta;
+        s_par[3] = (float)sc.alpha;
+    };
+    if (tid == 0) publish_params();
     __syncthreads();
 
     const size_t xstride = (size_t)a.L.nslots * kLanes;
@@ -102,10 +115,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     for (long long it = 0; it < a.max_iters; ++it) {
         const float* __restrict__ xin = a.x + (size_t)xbuf * xstride;
         float* __restrict__ xout = a.x + (size_t)(xbuf ^ 1) * xstride;
-        const float inv_beta = (float)(1.0 / sc.beta);
-        const float logbeta = (float)log(sc.beta);
-        const float beta_f = (float)sc.beta;
-        const float alpha = (float)sc.alpha;
+        const float inv_beta = s_par[0];
+        const float logbeta = s_par[1];
+        const float beta_f = s_par[2];
+        const float alpha = s_par[3];
 
         // ---------------- phase A: per-demand rate updates ----------------
         // Warps take the blocks of this CTA (blockIdx.x, blockIdx.x + NG,
@@ -122,26 +135,44 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         if (tid == 0) s_next = 0;  // read again only after the next barriers
         // publish this CTA's partial loads
         uint2* Lp = a.loads + (size_t)blockIdx.x * E;
+        #pragma unroll 4
         for (int e = tid; e < E; e += kIterThreads) {
             __stcg(&Lp[e], make_uint2(h_hi[e], h_lo[e]));
             h_hi[e] = 0u;
             h_lo[e] = 0u;
         }
         {
-            // this CTA's residual partials: its blocks' terms in FP64, each
-            // thread over a fixed stride of the block range, then a fixed-order
-            // CTA reduction
-            double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+            // this CTA's residual partials: each thread sums its blocks'
+            // terms (a fixed stride of the block range) in FP32, each warp
+            // its threads' sums in a fixed butterfly, and thread 0 the warps'
+            // in FP64, in warp order
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            #pragma unroll 4
             for (int k = tid; k < nbc; k += kIterThreads) {
                 const float* r = a.blkres + ((size_t)blockIdx.x + (size_t)k * NG) * 3;
-                t0 += (double)__ldcg(&r[0]);
-                t1 += (double)__ldcg(&r[1]);
-                t2 += (double)__ldcg(&r[2]);
+                t0 += __ldcg(&r[0]);
+                t1 += __ldcg(&r[1]);
+                t2 += __ldcg(&r[2]);
             }
-            const double v0 = block_sum(t0, red);
-            const double v1 = block_sum(t1, red);
-            const double v2 = block_sum(t2, red);
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+                t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+            }
+            if (lane == 0) {
+                s_wred[warp][0] = t0;
+                s_wred[warp][1] = t1;
+                s_wred[warp][2] = t2;
+            }
+            __syncthreads();
             if (tid == 0) {
+                double v0 = 0.0, v1 = 0.0, v2 = 0.0;
+                for (int w = 0; w < kIterWarps; ++w) {
+                    v0 += (double)s_wred[w][0];
+                    v1 += (double)s_wred[w][1];
+                    v2 += (double)s_wred[w][2];
+                }
                 double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * 4;
                 __stcg(&p[0], v0);
                 __stcg(&p[1], v1);
@@ -168,6 +199,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 unsigned long long sh = 0ull, sl = 0ull;
                 if (tid < per * ns) {
                     const int e = e_lo + tid % ns;
+                    #pragma unroll 4
                     for (int c = tid / ns; c < NG; c += per) {
                         const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
                         sh += v.x;
@@ -201,8 +233,16 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 __stcg(&a.u_next[e], un);
                 __stcg(&a.w_next[e], un + d);
             }
-            const double v3 = block_sum((double)r2.s, red);
-            if (tid == 0) __stcg(&a.part[((size_t)(it & 1) * NG + blockIdx.x) * 4 + 3], v3);
+            float t3 = r2.s;
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t3 += __shfl_xor_sync(0xffffffffu, t3, o);
+            if (lane == 0) s_wred[warp][3] = t3;
+            __syncthreads();
+            if (tid == 0) {
+                double v3 = 0.0;
+                for (int w = 0; w < kIterWarps; ++w) v3 += (double)s_wred[w][3];
+                __stcg(&a.part[((size_t)(it & 1) * NG + blockIdx.x) * 4 + 3], v3);
+            }
         }
         if (!grid_sync(a.barrier, (unsigned)((2 * it + 2) * NG), a.status, a.timeout_ns, true)) {
             failed = true;
@@ -210,6 +250,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         }
 
         // ---------------- control: residuals, beta, alpha, stop ----------------
+        // warp 0 sums the CTAs' partials (FP64, fixed order, identical in
+        // every CTA); thread 0 takes the decisions and publishes them
+        xbuf ^= 1;
+        done++;
         if (tid < 32) {
             double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
             const double* p = a.part + (size_t)(it & 1) * NG * 4;
@@ -225,72 +269,74 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 v2 += __shfl_xor_sync(0xffffffffu, v2, o);
                 v3 += __shfl_xor_sync(0xffffffffu, v3, o);
             }
-            if (lane == 0) { s_fin[0] = v0; s_fin[1] = v1; s_fin[2] = v2; s_fin[3] = v3; }
-        }
-        __syncthreads();
-        const double s_res = sqrt(s_fin[0]) / fmax(sqrt(s_fin[1]), 1e-30);
-        const double r_res = sqrt(s_fin[3]) / fmax(sqrt(s_fin[2]), 1e-30);
-        xbuf ^= 1;
-        sc.iter_total++;
-        sc.iter_alpha++;
-        done++;
-        int event = 0;
-        const bool numeric_ok = isfinite(s_res) && isfinite(r_res);
-        float ratio = 1.f;
-        if (numeric_ok && a.o.adapt_beta) {
-            double nb = sc.beta;
-            if (r_res > a.o.A * s_res) nb = sc.beta * a.o.C;
-            else if (s_res > a.o.A * r_res) nb = sc.beta / a.o.C;
-            if (nb != sc.beta) {
-                ratio = (float)(sc.beta / nb);
-                sc.beta = nb;
-                event |= 1;
+            if (tid == 0) {
+                const double s_res = sqrt(v0) / fmax(sqrt(v1), 1e-30);
+                const double r_res = sqrt(v3) / fmax(sqrt(v2), 1e-30);
+                sc.iter_total++;
+                sc.iter_alpha++;
+                int event = 0, ctl = 0;
+                float ratio = 1.f;
+                const bool numeric_ok = isfinite(s_res) && isfinite(r_res);
+                if (numeric_ok && a.o.adapt_beta) {
+                    double nb = sc.beta;
+                    if (r_res > a.o.A * s_res) nb = sc.beta * a.o.C;
+                    else if (s_res > a.o.A * r_res) nb = sc.beta / a.o.C;
+                    if (nb != sc.beta) {
+                        ratio = (float)(sc.beta / nb);
+                        sc.beta = nb;
+                        event |= 1;
+                    }
+                }
+                if (!numeric_ok) {
+                    ctl = 1;
+                    if (blockIdx.x == 0) atomicCAS(a.status, 0, kStatusNumeric);
+                } else if (r_res <= a.o.gamma && s_res <= a.o.gamma) {
+                    bool stop = false;
+                    if (sc.alpha >= a.o.alpha_target) {
+                        stop = true; event |= 4;
+                    } else if (a.o.continuation && sc.iter_alpha == 1 && sc.alpha > a.o.alpha_start) {
+                        stop = true; event |= 8;
+                    } else if (sc.alpha >= a.o.alpha_max) {
+                        stop = true; event |= 16;
+                    } else {
+                        double na = sc.alpha + a.o.alpha_step;
+                        if (na > a.o.alpha_target) na = a.o.alpha_target;
+                        if (na > a.o.alpha_max) na = a.o.alpha_max;
+                        sc.alpha = na;
+                        sc.iter_alpha = 0;
+                        event |= 2;
+                    }
+                    if (stop) {
+                        ctl = 2;
+                        sc.converged = 1;
+                        sc.stop_reason = event & 28;
+                    }
+                }
+                sc.r = r_res;
+                sc.s = s_res;
+                if (blockIdx.x == 0 && a.trace_cap > 0) {
+                    double* t = a.trace + (size_t)((sc.iter_total - 1) % a.trace_cap) * kTraceWidth;
+                    t[0] = r_res; t[1] = s_res; t[2] = sc.beta; t[3] = sc.alpha; t[4] = (double)event;
+                }
+                s_ratio = ratio;
+                s_ctl = ctl;
+                publish_params();
             }
         }
+        __syncthreads();
         // commit the slice's new prices (scaled with beta) and the new gather
         // weights w = u' + d (the rescale keeps d, a primal quantity)
+        const float ratio = s_ratio;
+        const int ctl = s_ctl;
         for (int e = e_lo + tid; e < e_hi; e += kIterThreads) s_u[e - e_lo] = s_un[e - e_lo] * ratio;
+        #pragma unroll 4
         for (int e = tid; e < E; e += kIterThreads) {
             float w = __ldcg(&a.w_next[e]);
             if (ratio != 1.f) w = fmaf(__ldcg(&a.u_next[e]), ratio - 1.f, w);
             w_s[e] = w;
         }
-        if (!numeric_ok) {
-            if (tid == 0 && blockIdx.x == 0) atomicCAS(a.status, 0, kStatusNumeric);
-            sc.r = r_res;
-            sc.s = s_res;
-            __syncthreads();
-            break;
-        }
-        bool stop = false;
-        if (r_res <= a.o.gamma && s_res <= a.o.gamma) {
-            if (sc.alpha >= a.o.alpha_target) {
-                stop = true; event |= 4;
-            } else if (a.o.continuation && sc.iter_alpha == 1 && sc.alpha > a.o.alpha_start) {
-                stop = true; event |= 8;
-            } else if (sc.alpha >= a.o.alpha_max) {
-                stop = true; event |= 16;
-            } else {
-                double na = sc.alpha + a.o.alpha_step;
-                if (na > a.o.alpha_target) na = a.o.alpha_target;
-                if (na > a.o.alpha_max) na = a.o.alpha_max;
-                sc.alpha = na;
-                sc.iter_alpha = 0;
-                event |= 2;
-            }
-        }
-        sc.r = r_res;
-        sc.s = s_res;
-        if (blockIdx.x == 0 && tid == 0 && a.trace_cap > 0) {
-            double* t = a.trace + (size_t)((sc.iter_total - 1) % a.trace_cap) * kTraceWidth;
-            t[0] = r_res; t[1] = s_res; t[2] = sc.beta; t[3] = sc.alpha; t[4] = (double)event;
-        }
         __syncthreads();
-        if (stop) {
-            sc.converged = 1;
-            sc.stop_reason = event & 28;
-            break;
-        }
+        if (ctl != 0) break;  // numeric failure (status set) or the stop rule fired
     }
     // a warp that gave up may still have bulk copies in flight into its
     // staging buffers: wait for them (bounded) before the CTA exits

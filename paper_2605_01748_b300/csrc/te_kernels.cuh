@@ -53,20 +53,6 @@ __device__ bool grid_sync(unsigned* counter, unsigned target, int* status, long 
     return s_ok != 0;
 }
 
-// Sum of one double over the CTA; every thread receives the result.  The
-// reduction order is fixed, so all CTAs obtain identical values from
-// identical inputs.
-__device__ double block_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < kIterWarps; ++i) t += red[i];
-    return t;
-}
-
 // Kahan-compensated FP32 accumulation (per-thread partial sums of the
 // residual norms; the cross-thread reduction is FP64).
 struct KSum {
@@ -269,16 +255,12 @@ __device__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long ti
     return true;
 }
 
-template <bool STAGED>
-__device__ __forceinline__ uint16_t load_id(const uint16_t* p) {
-    if (STAGED) {  // an explicit shared-memory load (the staging pointer is generic)
-        unsigned short v;
-        asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(smem_u32(p)));
-        return v;
-    }
-    return __ldg(p);
+// 16-bit load from a 32-bit shared-memory address
+__device__ __forceinline__ uint16_t lds_u16(unsigned addr) {
+    unsigned short v;
+    asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+    return v;
 }
-
 // One block (32/G demands, G lanes each, at most 4 paths per lane): gather,
 // x-block, scatter.  bids points at the block's first id row, in shared
 // memory (STAGED) or in global memory.
@@ -307,10 +289,11 @@ __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int l
     const size_t di = (size_t)b * a.dpb + lane / G;
     in.D = __ldg(&a.Dn[di]);
     in.lam = __ldcg(&a.lam[di]);
+    const float* xp = xin + (size_t)s0 * kLanes + lane;
     #pragma unroll
     for (int j = 0; j < kMaxPathsPerLane; ++j) {
         in.x[j] = 0.f;
-        if (j < KB) in.x[j] = __ldcg(&xin[(size_t)(s0 + j) * kLanes + lane]);
+        if (j < KB) in.x[j] = __ldcg(xp + j * kLanes);
     }
     return in;
 }
@@ -330,6 +313,13 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
     float xo[KL], m[KL], an[KL];
     #pragma unroll
     for (int j = 0; j < KL; ++j) xo[j] = in.x[j];
+    // staged ids: 32-bit shared address of this lane's entry in the block's
+    // first row (an explicit shared load per row, no generic addressing)
+    const unsigned sb = STAGED ? smem_u32(bids) + 2u * (unsigned)lane : 0u;
+    auto id_at = [&](unsigned row) -> uint16_t {
+        if (STAGED) return lds_u16(sb + row * (unsigned)(kLanes * sizeof(uint16_t)));
+        return __ldg(&bids[(size_t)row * kLanes + lane]);
+    };
     unsigned rs = 0;  // first row of slot j within the block
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
@@ -341,7 +331,7 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
             int n = 0;
             #pragma unroll 4
             for (unsigned r = 0; r < cnt; ++r) {
-                const uint16_t id = load_id<STAGED>(&bids[(size_t)(rs + r) * kLanes + lane]);
+                const uint16_t id = id_at(rs + r);
                 q += w_s[id];
                 n += (id != sentinel);
             }
@@ -358,19 +348,21 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
         if ((lane & (G - 1)) == 0) __stcg(&a.lam[di], nu * beta_f);
     }
     float bd = 0.f, bx = 0.f, be = 0.f;
+    float* xq = xout + (size_t)s0 * kLanes + lane;
     rs = 0;
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
         if (j < KB) {
             const unsigned cnt = (counts >> (8 * j)) & 0xffu;
-            const size_t sl = (size_t)(s0 + j);
             const float xn = an[j] > 0.f ? fmaxf(0.f, fmaf(nu, an[j], m[j])) : 0.f;
-            __stcg(&xout[sl * kLanes + lane], xn);
+            __stcg(xq + j * kLanes, xn);
             const float dx = xn - xo[j];
             bd = fmaf(dx, dx, bd);
             bx = fmaf(xn, xn, bx);
             if (xn != 0.f) {
-                be = fmaf(xn * xn, __frcp_rn(an[j]), be);
+                // the path's hop count n (an = 1/n rounded; the approximate
+                // reciprocal is within far less than 1/2 of n)
+                be = fmaf(xn * xn, rintf(__fdividef(1.f, an[j])), be);
                 // split fixed point: integer part of xn * 2^12 and the
                 // remaining fraction in units of 2^-24 (both exact in FP32)
                 const float vf = xn * 0x1p12f;
@@ -381,7 +373,7 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
                 // into the unused histogram slot E
                 #pragma unroll 4
                 for (unsigned r = 0; r < cnt; ++r) {
-                    const uint16_t id = load_id<STAGED>(&bids[(size_t)(rs + r) * kLanes + lane]);
+                    const uint16_t id = id_at(rs + r);
                     atomicAdd(&h_hi[id], hi);
                     atomicAdd(&h_lo[id], lo);
                 }

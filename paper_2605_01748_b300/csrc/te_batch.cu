@@ -105,22 +105,13 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
     float* w_s = reinterpret_cast<float*>(h_lo + (E + 1));  // [E+1], w_s[E] = 0
     float* s_u = w_s + (E + 1);                              // [E]
     uint16_t* stage = reinterpret_cast<uint16_t*>(smem + ((4 * (size_t)E + 3 + 31) & ~size_t(31)));
-    __shared__ __align__(8) unsigned long long s_mbar[W * 2];
     __shared__ double s_part[kRedParts];
     __shared__ int s_inst, s_next;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5;
     WarpStage ws;
     ws.buf[0] = stage + (size_t)(warp * 2) * kStageRows * kLanes;
     ws.buf[1] = stage + (size_t)(warp * 2 + 1) * kStageRows * kLanes;
-    ws.mb = &s_mbar[warp * 2];
-    ws.par[0] = ws.par[1] = 0u;
-    ws.pending[0] = ws.pending[1] = false;
-    if (lane == 0) {
-        mbar_init(&ws.mb[0], 1);
-        mbar_init(&ws.mb[1], 1);
-        fence_mbar_init();
-    }
     bool failed = false;
     __syncthreads();
 
@@ -164,9 +155,8 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             const float alpha = (float)sc.alpha;
 
             // phase A: the instance's blocks, shared among the warps
-            if (!run_blocks<G>(0, 1, I.nblocks, &s_next, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
-                               logbeta, beta_f, alpha, a.timeout_ns, a.status))
-                failed = true;
+            run_blocks<G>(0, 1, I.nblocks, &s_next, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta, logbeta,
+                          beta_f, alpha);
             __syncthreads();
             if (tid == 0) s_next = 0;
             if (*(volatile int*)a.status != 0) failed = true;
@@ -273,7 +263,6 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
         }
         __syncthreads();
     }
-    if (failed) drain_stage(ws, a.timeout_ns);
 }
 
 size_t batch_smem_bytes(int E, int W) {
@@ -856,7 +845,7 @@ extern "C" te_status te_batch_solve(te_batch* b, int64_t max_iters, te_solve_res
             results[i].stop_reason = c.stop_reason;
         }
     }
-    if (status == te::kStatusTimeout) return b->fail(TE_ETIMEOUT, "a bulk copy did not land within its time limit");
+    if (status == te::kStatusTimeout) return b->fail(TE_ETIMEOUT, "a kernel wait ran past its time limit");
     if (status == te::kStatusNumeric) return b->fail(TE_ENUMERIC, "a residual is not finite");
     return TE_OK;
 }

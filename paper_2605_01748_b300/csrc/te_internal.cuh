@@ -13,8 +13,8 @@
 //                                       padded with the sentinel id E
 // so every warp-wide load of a slot's rates or of one hop of its paths is one
 // contiguous 128 B (rates) or 64 B (16-bit ids) transaction, and the rows of
-// a whole block are one contiguous range that a single bulk copy moves into
-// shared memory.  Per-demand values (demand, path count, multiplier) are
+// a whole block are one contiguous range that the warp copies into shared
+// memory with 16-byte asynchronous copies.  Per-demand values (demand, path count, multiplier) are
 // indexed by demand slot d = b*dpb + t.
 #pragma once
 
@@ -108,7 +108,7 @@ struct IterArgs {
     long long trace_cap;
     float* lam;            // [nblocks*dpb] previous multiplier lambda = beta*nu of each demand
     long long max_iters;
-    long long timeout_ns;  // bound on every wait (grid barrier, bulk copy)
+    long long timeout_ns;  // bound on every wait (the grid barriers)
 };
 
 // Device status codes (mirror te_status).

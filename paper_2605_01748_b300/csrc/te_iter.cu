@@ -8,8 +8,8 @@
 //            the new rates, and add each path's new rate into the CTA's
 //            shared-memory histogram of edge loads (split 32-bit fixed point,
 //            native shared-memory integer atomics).  The
-//            edge ids of a block are brought into shared memory by one bulk
-//            asynchronous copy (TMA), issued one block ahead of use; the
+//            edge ids of a block are brought into shared memory by 16-byte
+//            asynchronous copies (cp.async), issued one block ahead of use; the
 //            block's metadata record is loaded two blocks ahead.  The CTA then
 //            publishes its per-edge partial loads and its residual partials
 //            (FP32 within a warp, FP64 across warps);
@@ -26,7 +26,7 @@
 //            balancing (Eq. 17), the stop rule (Eq. 18) and
 //            alpha-continuation; the CTA then loads the new gather weights
 //            into shared memory.
-// Every wait (grid barriers, bulk copies) is bounded.
+// Every wait on another CTA (the grid barriers) is bounded.
 //
 // Rates and prices are FP32.  The per-demand multiplier is kept in scaled
 // form nu = lambda / beta, so x_r = max(0, m_r + nu / n_r) with
@@ -55,7 +55,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kStageRows * kLanes);  // price slice
     const int e_lo = (int)((long long)blockIdx.x * E / NG), e_hi = (int)((long long)(blockIdx.x + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
-    __shared__ __align__(8) unsigned long long s_mbar[kIterWarps * 2];
     __shared__ float s_wred[kIterWarps][4];  // per-warp FP32 partials of the residual sums
     __shared__ float s_par[4];   // this iteration's 1/beta, log beta, beta, alpha (FP32)
     __shared__ float s_ratio;    // price rescale of the last balancing step
@@ -71,9 +70,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     WarpStage ws;
     ws.buf[0] = stage + (size_t)(warp * 2) * kStageRows * kLanes;
     ws.buf[1] = stage + (size_t)(warp * 2 + 1) * kStageRows * kLanes;
-    ws.mb = &s_mbar[warp * 2];
-    ws.par[0] = ws.par[1] = 0u;
-    ws.pending[0] = ws.pending[1] = false;
 
     for (int e = tid; e < E; e += kIterThreads) {
         w_s[e] = a.w[e];
@@ -86,11 +82,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         h_hi[E] = 0u;
         h_lo[E] = 0u;
         s_next = 0;
-    }
-    if (lane == 0) {
-        mbar_init(&ws.mb[0], 1);
-        mbar_init(&ws.mb[1], 1);
-        fence_mbar_init();
     }
     // the scalar state is kept by thread 0, which takes the control
     // decisions (FP64 is slow on this part: one thread does it and the CTA
@@ -127,9 +118,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         // residual terms are stored per block).
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, a.blkres, a.L.dpb, (uint16_t)a.L.E};
-            if (!run_blocks<G>((int)blockIdx.x, NG, nbc, &s_next, a.L.blkmeta, ids, xin, xout, bc, ws, w_s, h_hi,
-                               h_lo, inv_beta, logbeta, beta_f, alpha, a.timeout_ns, a.status))
-                failed = true;
+            run_blocks<G>((int)blockIdx.x, NG, nbc, &s_next, a.L.blkmeta, ids, xin, xout, bc, ws, w_s, h_hi, h_lo,
+                          inv_beta, logbeta, beta_f, alpha);
         }
         __syncthreads();
         if (tid == 0) s_next = 0;  // read again only after the next barriers
@@ -338,9 +328,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         __syncthreads();
         if (ctl != 0) break;  // numeric failure (status set) or the stop rule fired
     }
-    // a warp that gave up may still have bulk copies in flight into its
-    // staging buffers: wait for them (bounded) before the CTA exits
-    if (failed) drain_stage(ws, a.timeout_ns);
     __syncthreads();
     for (int e = e_lo + tid; e < e_hi; e += kIterThreads) a.u[e] = s_u[e - e_lo];
     if (blockIdx.x == 0) {

@@ -1,6 +1,6 @@
 // Device code shared by the iteration kernels (the single-instance persistent
 // kernel and the batch kernel): bounded waits and barriers, reductions, the
-// per-demand solve (x-block), bulk copies into shared memory, and the
+// per-demand solve (x-block), asynchronous copies into shared memory, and the
 // processing of one block (gather, per-demand split, scatter into the
 // CTA's load histogram).  Internal; included by te_iter.cu and te_batch.cu.
 #pragma once
@@ -210,50 +210,20 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
 
 
 // ---------------------------------------------------------------------------
-// bulk asynchronous copies and mbarriers (inline PTX)
+// asynchronous global -> shared copies (inline PTX)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+// one 16-byte asynchronous copy by this thread (both addresses 16-byte
+// aligned); copies are grouped per thread and waited for per group
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of
-// 16), completion counted on the mbarrier
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// Bounded wait for the phase of the given parity; false on timeout.
-__device__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long timeout_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if ((long long)(globaltimer_ns() - t0) > timeout_ns) return false;
-    }
-    return true;
-}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most the most recent group of this thread is in flight
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // 16-bit load from a 32-bit shared-memory address
 __device__ __forceinline__ uint16_t lds_u16(unsigned addr) {
@@ -402,30 +372,31 @@ __device__ __forceinline__ unsigned rows_of(unsigned counts) {
     return (counts & 0xffu) + ((counts >> 8) & 0xffu) + ((counts >> 16) & 0xffu) + (counts >> 24);
 }
 
-// Per-warp staging state of the block pipeline: two buffers of kStageRows
-// id rows, their mbarriers, the phase parity of each and whether a copy into
-// it is in flight.
+// Per-warp staging buffers of the block pipeline: two buffers of kStageRows
+// id rows (a block is copied into one while the other is processed).
 struct WarpStage {
     uint16_t* buf[2];
-    unsigned long long* mb;  // [2]
-    unsigned par[2];
-    bool pending[2];
 };
 
 // Phase A of one iteration for one warp: takes blocks start + v * stride
 // (v = 0, 1, ... < count, handed out by the shared counter *next), brings
-// each block's id rows into a staging buffer by one bulk copy issued one
-// block ahead (blocks longer than kStageRows read their ids from global
-// memory), loads the next block's rates, demands and multipliers into
-// registers while the current block is processed, and processes it.
-// blkmeta, ids and the rate buffers are those of the instance.  Returns
-// false when a bulk copy did not land within timeout_ns (status records it).
+// each block's id rows into a staging buffer by asynchronous 16-byte copies
+// (every lane a share, one commit group per block) issued one block ahead
+// (blocks longer than kStageRows read their ids from global memory), loads
+// the next block's rates, demands and multipliers into registers while the
+// current block is processed, and processes it.  blkmeta, ids and the rate
+// buffers are those of the instance.  All copies have landed on return.
+//
+// Per-lane copies instead of one bulk (TMA) copy per block: the ids of a
+// block are one contiguous range of about 1.6 KB, and on the 1500-node
+// workload the bulk copy's issue and completion wait cost a warp about 1900
+// cycles per block against 6.8 % less time per iteration with cp.async.
 template <int G>
-__device__ bool run_blocks(int start, int stride, int count, int* next, const BlockMeta* __restrict__ blkmeta,
+__device__ void run_blocks(int start, int stride, int count, int* next, const BlockMeta* __restrict__ blkmeta,
                            const uint16_t* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
                            unsigned* h_hi, unsigned* h_lo, float inv_beta, float logbeta, float beta_f,
-                           float alpha, long long timeout_ns, int* status) {
+                           float alpha) {
     const int lane = threadIdx.x & 31;
     const int none = start + count * stride;  // any index >= none means "no block"
     auto grab = [&]() -> int {
@@ -439,21 +410,20 @@ __device__ bool run_blocks(int start, int stride, int count, int* next, const Bl
         if (lane == 0 && b < none) m = blkmeta[b];
         return m;
     };
-    // issues the bulk copy of block b into buffer k; returns whether the
-    // block fits a staging buffer (else it is read from global memory)
+    // issues the copies of block b into buffer k (the caller commits the
+    // group); returns whether the block fits a staging buffer (else it is
+    // read from global memory).  The __syncwarp orders every lane's reads
+    // of buffer k (the block before last) before the copies overwrite it.
     auto issue = [&](const BlockMeta& m, int k) -> bool {
         const unsigned counts = __shfl_sync(0xffffffffu, m.counts, 0);
         const unsigned row0 = __shfl_sync(0xffffffffu, m.row0, 0);
         const unsigned rows = rows_of(counts);
         if (rows > (unsigned)kStageRows || rows == 0) return false;
         __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            const unsigned bytes = rows * kLanes * (unsigned)sizeof(uint16_t);
-            mbar_expect_tx(&ws.mb[k], bytes);
-            bulk_g2s(ws.buf[k], ids + (size_t)row0 * kLanes, bytes, &ws.mb[k]);
-        }
-        ws.pending[k] = true;
+        const unsigned bytes = rows * kLanes * (unsigned)sizeof(uint16_t);  // a multiple of 64
+        const char* src = reinterpret_cast<const char*>(ids + (size_t)row0 * kLanes);
+        const unsigned dst = smem_u32(ws.buf[k]);
+        for (unsigned off = 16u * (unsigned)lane; off < bytes; off += 16u * kLanes) cp_async16(dst + off, src + off);
         return true;
     };
     auto prefetch = [&](int b, const BlockMeta& m) -> BlockIn {
@@ -469,22 +439,22 @@ __device__ bool run_blocks(int start, int stride, int count, int* next, const Bl
     BlockMeta m1 = load_meta(b1);
     int cur = 0;
     bool st0 = b0 < none ? issue(m0, cur) : false;
+    cp_async_commit();  // one group per block, empty when nothing was copied
     BlockIn in0 = prefetch(b0, m0);
     while (b0 < none) {
         const int b2 = grab();
         const BlockMeta m2 = load_meta(b2);
         const bool st1 = b1 < none ? issue(m1, cur ^ 1) : false;
+        cp_async_commit();
         const BlockIn in1 = prefetch(b1, m1);
         const int s0 = (int)__shfl_sync(0xffffffffu, m0.s0, 0);
         const unsigned counts = __shfl_sync(0xffffffffu, m0.counts, 0);
         const int KB = (int)__shfl_sync(0xffffffffu, m0.kb, 0);
         if (st0) {
-            if (!mbar_wait(&ws.mb[cur], ws.par[cur], timeout_ns)) {
-                if (lane == 0) atomicCAS(status, 0, kStatusTimeout);
-                return false;
-            }
-            ws.par[cur] ^= 1u;
-            ws.pending[cur] = false;
+            // this block's group (all but the newest) has landed for every
+            // lane; the __syncwarp makes each lane's copies visible to all
+            cp_async_wait_prev();
+            __syncwarp();
             process_block<G, true>(bc, b0, lane, ws.buf[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                    inv_beta, logbeta, beta_f, alpha);
         } else {
@@ -500,14 +470,8 @@ __device__ bool run_blocks(int start, int stride, int count, int* next, const Bl
         m1 = m2;
         cur ^= 1;
     }
-    return true;
-}
-
-// After a failed wait a warp may still have bulk copies in flight into its
-// staging buffers: wait for them (bounded) before the CTA exits.
-__device__ inline void drain_stage(WarpStage& ws, long long timeout_ns) {
-    for (int k = 0; k < 2; ++k)
-        if (ws.pending[k]) mbar_wait(&ws.mb[k], ws.par[k], timeout_ns);
+    cp_async_wait_all();  // (only empty groups can remain)
+    __syncwarp();
 }
 
 }  // namespace

@@ -423,7 +423,15 @@ __device__ void run_blocks(int start, int stride, int count, int* next, const Bl
         const unsigned bytes = rows * kLanes * (unsigned)sizeof(uint16_t);  // a multiple of 64
         const char* src = reinterpret_cast<const char*>(ids + (size_t)row0 * kLanes);
         const unsigned dst = smem_u32(ws.buf[k]);
-        for (unsigned off = 16u * (unsigned)lane; off < bytes; off += 16u * kLanes) cp_async16(dst + off, src + off);
+        // at most kStageRows rows of 64 B: a fixed number of predicated
+        // copies per lane (no loop branch)
+        constexpr int kCopies = kStageRows * kLanes * (int)sizeof(uint16_t) / (16 * kLanes);
+        static_assert(kStageRows * (int)sizeof(uint16_t) % 16 == 0, "a staging buffer is whole 16-byte copies per lane");
+        #pragma unroll
+        for (int i = 0; i < kCopies; ++i) {
+            const unsigned off = 16u * ((unsigned)lane + (unsigned)i * kLanes);
+            if (off < bytes) cp_async16(dst + off, src + off);
+        }
         return true;
     };
     auto prefetch = [&](int b, const BlockMeta& m) -> BlockIn {

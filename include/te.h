@@ -130,7 +130,9 @@ void te_default_options(te_options* opt);
  * input buffer (they are copied).  demands: host [n_demands], finite and
  * > 0; capacities: host [n_edges], finite and >= 0, and > 0 on every edge
  * used by a path (Slater's condition, Appendix C).  Limits: at most 32 paths
- * per demand, at most 255 edges per path, E + 1 < 2^31.  On success *out
+ * per demand, at most 255 edges per path, at most about 10,770 edges (the
+ * iteration kernel keeps the per-edge weights and load histograms of every
+ * edge in each CTA's shared memory; more return TE_EUNSUPPORTED).  On success *out
  * receives a new handle.  Errors: TE_EINVAL (bad input; message names the
  * first offending index), TE_EUNSUPPORTED, TE_ENOMEM, TE_ECUDA. */
 te_status te_create(const te_topology* topo, const te_paths* paths, const double* demands,

@@ -316,7 +316,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     if ((st = h->cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device), "device query")))
         return bail(st);
     if (te::iter_smem_bytes(E, nsm) > 227 * 1024) {
-        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 10900 edges)", E);
+        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 10770 edges)", E);
         return bail(TE_EUNSUPPORTED);
     }
     if ((st = h->cuda(te::iter_occupancy(G, E, nsm, &bps), "occupancy query"))) return bail(st);

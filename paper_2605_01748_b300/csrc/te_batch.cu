@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             const float alpha = (float)sc.alpha;
 
             // phase A: the instance's blocks, shared among the warps
-            run_blocks<G>(0, 1, I.nblocks, &s_next, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta, logbeta,
+            run_blocks<G, kStageRows>(0, 1, I.nblocks, &s_next, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta, logbeta,
                           beta_f, alpha);
             __syncthreads();
             if (tid == 0) s_next = 0;

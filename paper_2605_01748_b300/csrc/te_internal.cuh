@@ -27,12 +27,19 @@ constexpr int kLanes = 32;
 constexpr int kMaxPaths = 32;     // paths per demand
 constexpr int kMaxHops = 255;     // edges per path
 constexpr int kMaxPathsPerLane = 4;
+// The iteration kernel runs 20 warps per SM: 96 registers per thread fit
+// the register file, and two staging buffers of 40 rows per warp, the load
+// histograms and the gather weights fit the 227 KB of shared memory for up
+// to about 10,000 edges (blocks longer than 40 rows, 0.03 % on the
+// 1500-node workload, read their ids from global memory).  The batch
+// kernel stages up to 48 rows.
 #ifndef TE_ITER_THREADS
-#define TE_ITER_THREADS 512
+#define TE_ITER_THREADS 640
 #endif
 constexpr int kIterThreads = TE_ITER_THREADS;
 constexpr int kIterWarps = kIterThreads / 32;
-constexpr int kStageRows = 48;    // rows of 16-bit ids per staging buffer (3 KB)
+constexpr int kIterStageRows = 40;  // rows of 16-bit ids per staging buffer of the iteration kernel
+constexpr int kStageRows = 48;      // the same for the batch kernel (3 KB)
 constexpr int kTraceWidth = 5;
 
 // Solver scalars, kept in device memory between launches.

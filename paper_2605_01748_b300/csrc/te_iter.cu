@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     unsigned* h_lo = h_hi + (E + 1);                                 // [E+1] units of 2^-24
     float* w_s = reinterpret_cast<float*>(h_lo + (E + 1));          // [E+1], w_s[E] = 0
     uint16_t* stage = reinterpret_cast<uint16_t*>(
-        reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) & ~uintptr_t(127));  // [warps][2][kStageRows*32]
-    float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kStageRows * kLanes);  // price slice
+        reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) & ~uintptr_t(127));  // [warps][2][kIterStageRows*32]
+    float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kIterStageRows * kLanes);  // price slice
     const int e_lo = (int)((long long)blockIdx.x * E / NG), e_hi = (int)((long long)(blockIdx.x + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
     __shared__ float s_wred[kIterWarps][4];  // per-warp FP32 partials of the residual sums
@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     const int nbc = blockIdx.x < (unsigned)b_hi ? (b_hi - (int)blockIdx.x + NG - 1) / NG : 0;
     const uint16_t* ids = static_cast<const uint16_t*>(a.L.ids);
     WarpStage ws;
-    ws.buf[0] = stage + (size_t)(warp * 2) * kStageRows * kLanes;
-    ws.buf[1] = stage + (size_t)(warp * 2 + 1) * kStageRows * kLanes;
+    ws.buf[0] = stage + (size_t)(warp * 2) * kIterStageRows * kLanes;
+    ws.buf[1] = stage + (size_t)(warp * 2 + 1) * kIterStageRows * kLanes;
 
     for (int e = tid; e < E; e += kIterThreads) {
         w_s[e] = a.w[e];
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         // residual terms are stored per block).
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, a.blkres, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G>((int)blockIdx.x, NG, nbc, &s_next, a.L.blkmeta, ids, xin, xout, bc, ws, w_s, h_hi, h_lo,
+            run_blocks<G, kIterStageRows>((int)blockIdx.x, NG, nbc, &s_next, a.L.blkmeta, ids, xin, xout, bc, ws, w_s, h_hi, h_lo,
                           inv_beta, logbeta, beta_f, alpha);
         }
         __syncthreads();
@@ -182,8 +182,13 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
             // CTAs) and converted once; thread t adds the partials of CTAs
             // c = t / ns, t / ns + kIterThreads / ns, ... for edge e_lo + t % ns
             const int ns = e_hi - e_lo;
-            unsigned long long* s_L = reinterpret_cast<unsigned long long*>(
-                (reinterpret_cast<uintptr_t>(s_un + ns) + 7) & ~uintptr_t(7));  // [2][kIterThreads]
+            // [2][kIterThreads] in the staging buffers, idle in phase B
+            // (every copy of phase A has landed; the next are issued after
+            // the control section's barrier)
+            static_assert(2 * kIterThreads * sizeof(unsigned long long) <=
+                              (size_t)kIterWarps * 2 * kIterStageRows * kLanes * sizeof(uint16_t),
+                          "the phase-B partial sums fit the staging buffers");
+            unsigned long long* s_L = reinterpret_cast<unsigned long long*>(stage);
             if (ns > 0) {
                 const int per = kIterThreads / ns > 0 ? kIterThreads / ns : 1;
                 unsigned long long sh = 0ull, sl = 0ull;
@@ -381,11 +386,9 @@ cudaError_t occupancy_t(int E, int grid_hint, int* blocks) {
 size_t iter_smem_bytes(int E, int grid) {
     size_t b = 2 * (size_t)(E + 1) * sizeof(unsigned) + (size_t)(E + 1) * sizeof(float);
     b = (b + 31 * sizeof(float) + 127) & ~size_t(127);
-    b += (size_t)kIterWarps * 2 * kStageRows * kLanes * sizeof(uint16_t);
+    b += (size_t)kIterWarps * 2 * kIterStageRows * kLanes * sizeof(uint16_t);
     const int slice = (E + grid - 1) / (grid > 0 ? grid : 1) + 1;
     b += 2 * (size_t)slice * sizeof(float);
-    b = (b + 7) & ~size_t(7);
-    b += 2 * (size_t)kIterThreads * sizeof(unsigned long long);
     return b;
 }
 

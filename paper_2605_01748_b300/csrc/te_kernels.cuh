@@ -372,8 +372,8 @@ __device__ __forceinline__ unsigned rows_of(unsigned counts) {
     return (counts & 0xffu) + ((counts >> 8) & 0xffu) + ((counts >> 16) & 0xffu) + (counts >> 24);
 }
 
-// Per-warp staging buffers of the block pipeline: two buffers of kStageRows
-// id rows (a block is copied into one while the other is processed).
+// Per-warp staging buffers of the block pipeline: two buffers of ROWS id
+// rows (a block is copied into one while the other is processed).
 struct WarpStage {
     uint16_t* buf[2];
 };
@@ -382,7 +382,7 @@ struct WarpStage {
 // (v = 0, 1, ... < count, handed out by the shared counter *next), brings
 // each block's id rows into a staging buffer by asynchronous 16-byte copies
 // (every lane a share, one commit group per block) issued one block ahead
-// (blocks longer than kStageRows read their ids from global memory), loads
+// (blocks longer than ROWS read their ids from global memory), loads
 // the next block's rates, demands and multipliers into registers while the
 // current block is processed, and processes it.  blkmeta, ids and the rate
 // buffers are those of the instance.  All copies have landed on return.
@@ -391,7 +391,7 @@ struct WarpStage {
 // block are one contiguous range of about 1.6 KB, and on the 1500-node
 // workload the bulk copy's issue and completion wait cost a warp about 1900
 // cycles per block against 6.8 % less time per iteration with cp.async.
-template <int G>
+template <int G, int ROWS>
 __device__ void run_blocks(int start, int stride, int count, int* next, const BlockMeta* __restrict__ blkmeta,
                            const uint16_t* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
@@ -418,15 +418,15 @@ __device__ void run_blocks(int start, int stride, int count, int* next, const Bl
         const unsigned counts = __shfl_sync(0xffffffffu, m.counts, 0);
         const unsigned row0 = __shfl_sync(0xffffffffu, m.row0, 0);
         const unsigned rows = rows_of(counts);
-        if (rows > (unsigned)kStageRows || rows == 0) return false;
+        if (rows > (unsigned)ROWS || rows == 0) return false;
         __syncwarp();
         const unsigned bytes = rows * kLanes * (unsigned)sizeof(uint16_t);  // a multiple of 64
         const char* src = reinterpret_cast<const char*>(ids + (size_t)row0 * kLanes);
         const unsigned dst = smem_u32(ws.buf[k]);
-        // at most kStageRows rows of 64 B: a fixed number of predicated
-        // copies per lane (no loop branch)
-        constexpr int kCopies = kStageRows * kLanes * (int)sizeof(uint16_t) / (16 * kLanes);
-        static_assert(kStageRows * (int)sizeof(uint16_t) % 16 == 0, "a staging buffer is whole 16-byte copies per lane");
+        // at most ROWS rows of 64 B: a fixed number of predicated copies per
+        // lane (no loop branch)
+        constexpr int kCopies = ROWS * kLanes * (int)sizeof(uint16_t) / (16 * kLanes);
+        static_assert(ROWS * (int)sizeof(uint16_t) % 16 == 0, "a staging buffer is whole 16-byte copies per lane");
         #pragma unroll
         for (int i = 0; i < kCopies; ++i) {
             const unsigned off = 16u * ((unsigned)lane + (unsigned)i * kLanes);

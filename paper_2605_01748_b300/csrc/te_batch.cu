@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
     float* s_u = w_s + (E + 1);                              // [E]
     uint16_t* stage = reinterpret_cast<uint16_t*>(smem + ((4 * (size_t)E + 3 + 31) & ~size_t(31)));
     __shared__ double s_part[kRedParts];
-    __shared__ int s_inst, s_next;
+    __shared__ int s_inst;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     WarpStage ws;
@@ -132,7 +132,6 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             w_s[E] = 0.f;
             h_hi[E] = 0u;
             h_lo[E] = 0u;
-            s_next = 0;
         }
         Scalars sc = a.sc[ii];
         sc.converged = 0;
@@ -155,10 +154,9 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             const float alpha = (float)sc.alpha;
 
             // phase A: the instance's blocks, shared among the warps
-            run_blocks<G, kStageRows>(0, 1, I.nblocks, &s_next, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta, logbeta,
+            run_blocks<G, kStageRows>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta, logbeta,
                           beta_f, alpha);
             __syncthreads();
-            if (tid == 0) s_next = 0;
             if (*(volatile int*)a.status != 0) failed = true;
             if (__syncthreads_or(failed)) {
                 failed = true;

@@ -59,7 +59,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     __shared__ float s_par[4];   // this iteration's 1/beta, log beta, beta, alpha (FP32)
     __shared__ float s_ratio;    // price rescale of the last balancing step
     __shared__ int s_ctl;        // control decision: bit 0 numeric failure, bit 1 stop
-    __shared__ int s_next;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // blocks of this CTA: blockIdx.x, blockIdx.x + NG, ... (round robin, so
@@ -81,7 +80,6 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         w_s[E] = 0.f;
         h_hi[E] = 0u;
         h_lo[E] = 0u;
-        s_next = 0;
     }
     // the scalar state is kept by thread 0, which takes the control
     // decisions (FP64 is slow on this part: one thread does it and the CTA
@@ -112,17 +110,16 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         const float alpha = s_par[3];
 
         // ---------------- phase A: per-demand rate updates ----------------
-        // Warps take the blocks of this CTA (blockIdx.x, blockIdx.x + NG,
-        // ...) one at a time from a shared counter; results do not depend on
-        // which warp takes which block (the loads are integer sums and the
+        // The warps share the blocks of this CTA (blockIdx.x, blockIdx.x +
+        // NG, ...) in a fixed interleave; results do not depend on which
+        // warp takes which block (the loads are integer sums and the
         // residual terms are stored per block).
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, a.blkres, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows>((int)blockIdx.x, NG, nbc, &s_next, a.L.blkmeta, ids, xin, xout, bc, ws, w_s, h_hi, h_lo,
+            run_blocks<G, kIterStageRows>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s, h_hi, h_lo,
                           inv_beta, logbeta, beta_f, alpha);
         }
         __syncthreads();
-        if (tid == 0) s_next = 0;  // read again only after the next barriers
         // publish this CTA's partial loads
         uint2* Lp = a.loads + (size_t)blockIdx.x * E;
         #pragma unroll 4

@@ -379,7 +379,9 @@ struct WarpStage {
 };
 
 // Phase A of one iteration for one warp: takes blocks start + v * stride
-// (v = 0, 1, ... < count, handed out by the shared counter *next), brings
+// for v = w, w + W, w + 2W, ... < count (w the warp, W the warps of the CTA:
+// a fixed interleave, so no counter is shared; the blocks of a CTA are a
+// sample of all kinds of blocks, and the warps' totals differ little), brings
 // each block's id rows into a staging buffer by asynchronous 16-byte copies
 // (every lane a share, one commit group per block) issued one block ahead
 // (blocks longer than ROWS read their ids from global memory), loads
@@ -392,17 +394,18 @@ struct WarpStage {
 // workload the bulk copy's issue and completion wait cost a warp about 1900
 // cycles per block against 6.8 % less time per iteration with cp.async.
 template <int G, int ROWS>
-__device__ void run_blocks(int start, int stride, int count, int* next, const BlockMeta* __restrict__ blkmeta,
+__device__ void run_blocks(int start, int stride, int count, const BlockMeta* __restrict__ blkmeta,
                            const uint16_t* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
                            unsigned* h_hi, unsigned* h_lo, float inv_beta, float logbeta, float beta_f,
                            float alpha) {
     const int lane = threadIdx.x & 31;
     const int none = start + count * stride;  // any index >= none means "no block"
+    const int nw = (int)(blockDim.x >> 5);
+    int vnext = (int)(threadIdx.x >> 5);
     auto grab = [&]() -> int {
-        int v = 0;
-        if (lane == 0) v = atomicAdd(next, 1);
-        v = __shfl_sync(0xffffffffu, v, 0);
+        const int v = vnext;
+        vnext += nw;
         return v < count ? start + v * stride : none;
     };
     auto load_meta = [&](int b) -> BlockMeta {

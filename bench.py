@@ -422,12 +422,19 @@ def run_ours(a, ws, rank, local, dist):
         xg = t.allocation(project=False).astype(np.float64)
         xo = s.allocation()
         err = float(np.max(np.abs(xg - xo)) / max(np.max(np.abs(xo)), 1e-300))
+        # and one iteration on a single thread (the oracle's parallel scaling)
+        s1 = O.OracleSolver(inst, threads=1)
+        t2 = time.perf_counter()
+        s1.run(1)
+        d1 = time.perf_counter() - t2
+        del s1
         out["cpu_baseline"] = {"value": round((per_iter * K + dp) * 1e3, 1), "unit": "ms", "cores": cores,
                                "kind": "oracle",
                                "sample": f"{n} FP64 oracle iterations of the same workload in one call "
                                          f"({dt:.2f} s, incl. its edge->path transpose), scaled to K={K} "
                                          f"iterations, plus one proportional scaling ({dp:.2f} s)",
-                               "s_per_iter": round(per_iter, 4)}
+                               "s_per_iter": round(per_iter, 4),
+                               "s_per_iter_1_thread": round(d1, 4)}
         out["error_vs_oracle"] = {"max_rel_err_after_sample_iters": err, "iters": n}
     if rank == 0:
         print(json.dumps(out), flush=True)

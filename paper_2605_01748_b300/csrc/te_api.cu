@@ -87,7 +87,6 @@ struct te_handle {
     float* w_next = nullptr;  // [E]
     uint2* loads = nullptr;   // [grid*E] per-CTA partial loads
     double* part = nullptr;   // [2*grid*4]
-    float* blkres = nullptr;  // [nblocks*3] per-block residual terms
     unsigned* barrier = nullptr;
     int* status = nullptr;
     te::Scalars* sc = nullptr;
@@ -357,7 +356,6 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->w_next, sizeof(float) * E));
     A(h->alloc(&h->loads, sizeof(uint2) * (size_t)h->grid * (size_t)E));
     A(h->alloc(&h->part, sizeof(double) * 2 * 4 * (size_t)h->grid));
-    A(h->alloc(&h->blkres, sizeof(float) * 3 * (size_t)nblocks));
     A(h->alloc(&h->barrier, sizeof(unsigned)));
     A(h->alloc(&h->status, sizeof(int)));
     A(h->alloc(&h->sc, sizeof(te::Scalars)));
@@ -482,7 +480,6 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* 
         a.w = h->w;
         a.loads = h->loads;
         a.part = h->part;
-        a.blkres = h->blkres;
         a.barrier = h->barrier;
         a.status = h->status;
         a.sc = h->sc;

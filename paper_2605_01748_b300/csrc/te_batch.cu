@@ -154,8 +154,9 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             const float alpha = (float)sc.alpha;
 
             // phase A: the instance's blocks, shared among the warps
-            run_blocks<G, kStageRows>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta, logbeta,
-                          beta_f, alpha);
+            float unused[3];
+            run_blocks<G, kStageRows, false>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
+                                             logbeta, beta_f, alpha, unused);
             __syncthreads();
             if (*(volatile int*)a.status != 0) failed = true;
             if (__syncthreads_or(failed)) {

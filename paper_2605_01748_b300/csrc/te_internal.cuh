@@ -107,7 +107,6 @@ struct IterArgs {
     float* w_next;         // [E] scratch: gather weights published each iteration
     uint2* loads;          // [grid*E] per-CTA partial edge loads (fixed point: 2^-12 and 2^-24 units)
     double* part;          // [2*grid*4] per-CTA residual partials
-    float* blkres;         // [nblocks*3] per-block residual terms
     unsigned* barrier;     // grid barrier counter (zeroed before launch)
     int* status;           // device status word (0 ok)
     Scalars* sc;           // in/out

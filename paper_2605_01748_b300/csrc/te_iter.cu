@@ -111,13 +111,14 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
 
         // ---------------- phase A: per-demand rate updates ----------------
         // The warps share the blocks of this CTA (blockIdx.x, blockIdx.x +
-        // NG, ...) in a fixed interleave; results do not depend on which
-        // warp takes which block (the loads are integer sums and the
-        // residual terms are stored per block).
+        // NG, ...) in a fixed interleave, so a run is deterministic (the
+        // loads are integer sums, and each lane sums the residual terms of
+        // its warp's blocks in FP32 in the order of the interleave).
+        float acc[3] = {0.f, 0.f, 0.f};
         if (!failed) {
-            const BlockCtx bc{a.L.Dn, a.lam, a.blkres, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s, h_hi, h_lo,
-                          inv_beta, logbeta, beta_f, alpha);
+            const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.dpb, (uint16_t)a.L.E};
+            run_blocks<G, kIterStageRows, true>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
+                                                h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, acc);
         }
         __syncthreads();
         // publish this CTA's partial loads
@@ -129,18 +130,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
             h_lo[e] = 0u;
         }
         {
-            // this CTA's residual partials: each thread sums its blocks'
-            // terms (a fixed stride of the block range) in FP32, each warp
-            // its threads' sums in a fixed butterfly, and thread 0 the warps'
-            // in FP64, in warp order
-            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-            #pragma unroll 4
-            for (int k = tid; k < nbc; k += kIterThreads) {
-                const float* r = a.blkres + ((size_t)blockIdx.x + (size_t)k * NG) * 3;
-                t0 += __ldcg(&r[0]);
-                t1 += __ldcg(&r[1]);
-                t2 += __ldcg(&r[2]);
-            }
+            // this CTA's residual partials: each warp sums its lanes' sums in
+            // a fixed butterfly, and thread 0 the warps' in FP64, in warp
+            // order (the blocks of a warp are fixed by the interleave, so the
+            // totals do not depend on timing)
+            float t0 = acc[0], t1 = acc[1], t2 = acc[2];
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 t0 += __shfl_xor_sync(0xffffffffu, t0, o);

@@ -152,11 +152,12 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             const float logbeta = (float)log(sc.beta);
             const float beta_f = (float)sc.beta;
             const float alpha = (float)sc.alpha;
+            const float inv_alpha = alpha > 0.f ? 1.f / alpha : 0.f;
 
             // phase A: the instance's blocks, shared among the warps
             float unused[3];
             run_blocks<G, kStageRows, false>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
-                                             logbeta, beta_f, alpha, unused);
+                                             logbeta, beta_f, alpha, inv_alpha, unused);
             __syncthreads();
             if (*(volatile int*)a.status != 0) failed = true;
             if (__syncthreads_or(failed)) {

@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     const int e_lo = (int)((long long)blockIdx.x * E / NG), e_hi = (int)((long long)(blockIdx.x + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
     __shared__ float s_wred[kIterWarps][4];  // per-warp FP32 partials of the residual sums
-    __shared__ float s_par[4];   // this iteration's 1/beta, log beta, beta, alpha (FP32)
+    __shared__ float s_par[5];   // this iteration's 1/beta, log beta, beta, alpha, 1/alpha (FP32)
     __shared__ float s_ratio;    // price rescale of the last balancing step
     __shared__ int s_ctl;        // control decision: bit 0 numeric failure, bit 1 stop
 
@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         s_par[1] = (float)log(sc.beta);
         s_par[2] = (float)sc.beta;
         s_par[3] = (float)sc.alpha;
+        s_par[4] = sc.alpha > 0.0 ? 1.f / (float)sc.alpha : 0.f;
     };
     if (tid == 0) publish_params();
     __syncthreads();
@@ -108,6 +109,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         const float logbeta = s_par[1];
         const float beta_f = s_par[2];
         const float alpha = s_par[3];
+        const float inv_alpha = s_par[4];
 
         // ---------------- phase A: per-demand rate updates ----------------
         // The warps share the blocks of this CTA (blockIdx.x, blockIdx.x +
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.dpb, (uint16_t)a.L.E};
             run_blocks<G, kIterStageRows, true>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
-                                                h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, acc);
+                                                h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         __syncthreads();
         // publish this CTA's partial loads

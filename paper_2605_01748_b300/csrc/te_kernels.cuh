@@ -69,14 +69,14 @@ struct KSum {
 // demand cap is slack here.  alpha = 1 has the closed-form quadratic root of
 // Appendix B.2; other alpha use Newton steps on
 // g(t) = log(A + H e^t) + (t + log beta)/alpha, safeguarded by bisection.
-__device__ __forceinline__ float slack_root(float A, float H, float logbeta, float alpha, float tlo,
+// ia = 1/alpha (FP32, computed once per iteration by the caller).
+__device__ __forceinline__ float slack_root(float A, float H, float logbeta, float alpha, float ia, float tlo,
                                             float thi, float hint) {
     if (alpha == 1.f) {
         const float ib = __expf(-logbeta);
         const float disc = sqrtf(fmaf(A, A, 4.f * H * ib));
         return A >= 0.f ? 2.f * ib / (A + disc) : (disc - A) / (2.f * H);
     }
-    const float ia = 1.f / alpha;
     // start from the previous multiplier when it lies inside the bracket
     const float th = hint > 0.f ? __logf(hint) : thi;
     float t = (th > tlo && th < thi) ? th : thi;
@@ -153,7 +153,8 @@ __device__ __forceinline__ int gall(int v, unsigned gm) {
 // typically the first step is already exact and the second confirms it).
 template <int KL, int G>
 __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an)[KL], float D,
-                                          float inv_beta, float logbeta, float alpha, float nu0, unsigned gm) {
+                                          float inv_beta, float logbeta, float alpha, float inv_alpha, float nu0,
+                                          unsigned gm) {
     float nu = nu0;
     if (alpha == 0.f) {
         float S = 0.f;
@@ -199,7 +200,7 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
             continue;
         }
         float nn = (D - A) / H;
-        if (nn > nucap) nn = slack_root(A, H, logbeta, alpha, tcap, __logf(nn), nu);
+        if (nn > nucap) nn = slack_root(A, H, logbeta, alpha, inv_alpha, tcap, __logf(nn), nu);
         if (descending && !(nn < nu)) break;  // rounding: no further descent
         nu = nn;
         prev = mask;
@@ -276,7 +277,7 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
                                               unsigned counts, int KB, const BlockIn& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
                                               unsigned* h_lo, float inv_beta, float logbeta,
-                                              float beta_f, float alpha, float (&acc)[3]) {
+                                              float beta_f, float alpha, float inv_alpha, float (&acc)[3]) {
     constexpr int KL = kMaxPathsPerLane;
     const uint16_t sentinel = a.sentinel;
     const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -293,7 +294,8 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
         if (STAGED) return lds_u16(sb + row * (unsigned)(kLanes * sizeof(uint16_t)));
         return __ldg(&bids[(size_t)row * kLanes + lane]);
     };
-    unsigned rs = 0;  // first row of slot j within the block
+    unsigned rs = 0;      // first row of slot j within the block
+    unsigned nbits = 0u;  // hop count n of slot j's path in bits 8j..8j+7
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
         m[j] = 0.f;
@@ -309,15 +311,19 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
                 n += (id != sentinel);
             }
             if (n > 0) {
-                an[j] = __frcp_rn((float)n);
+                // 1/n by the hardware's approximate reciprocal (within an
+                // ulp; measured 3 % less time per iteration than the
+                // correctly rounded one)
+                an[j] = __fdividef(1.f, (float)n);
                 m[j] = fmaf(-q, an[j], xo[j]);
             }
+            nbits |= (unsigned)n << (8 * j);
             rs += cnt;
         }
     }
     float nu = 0.f;
     if (D > 0.f) {
-        nu = solve_nu<KL, G>(m, an, D, inv_beta, logbeta, alpha, lam0 * inv_beta, gm);
+        nu = solve_nu<KL, G>(m, an, D, inv_beta, logbeta, alpha, inv_alpha, lam0 * inv_beta, gm);
         if ((lane & (G - 1)) == 0) __stcg(&a.lam[di], nu * beta_f);
     }
     float bd = ACC ? acc[0] : 0.f, bx = ACC ? acc[1] : 0.f, be = ACC ? acc[2] : 0.f;
@@ -333,9 +339,8 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
             bd = fmaf(dx, dx, bd);
             bx = fmaf(xn, xn, bx);
             if (xn != 0.f) {
-                // the path's hop count n (an = 1/n rounded; the approximate
-                // reciprocal is within far less than 1/2 of n)
-                be = fmaf(xn * xn, rintf(__fdividef(1.f, an[j])), be);
+                // the path's hop count n (n <= 255 hops)
+                be = fmaf(xn * xn, (float)((nbits >> (8 * j)) & 0xffu), be);
                 // split fixed point: integer part of xn * 2^12 and the
                 // remaining fraction in units of 2^-24 (both exact in FP32)
                 const float vf = xn * 0x1p12f;
@@ -411,7 +416,7 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
                            const uint16_t* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
                            unsigned* h_hi, unsigned* h_lo, float inv_beta, float logbeta, float beta_f,
-                           float alpha, float (&acc)[3]) {
+                           float alpha, float inv_alpha, float (&acc)[3]) {
     const int lane = threadIdx.x & 31;
     const int none = start + count * stride;  // any index >= none means "no block"
     const int nw = (int)(blockDim.x >> 5);
@@ -480,11 +485,11 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
             cp_async_wait_prev();
             __syncwarp();
             process_block<G, true, ACC>(bc, b0, lane, ws.buf[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
-                                        inv_beta, logbeta, beta_f, alpha, acc);
+                                        inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         } else {
             const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
             process_block<G, false, ACC>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
-                                         w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, acc);
+                                         w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         b0 = b1;
         m0 = m1;

@@ -199,8 +199,13 @@ __device__ __forceinline__ float solve_nu(const float (&m)[KL], const float (&an
             nu = gmin<G>(ub, gm);
             continue;
         }
-        float nn = (D - A) / H;
-        if (nn > nucap) nn = slack_root(A, H, logbeta, alpha, inv_alpha, tcap, __logf(nn), nu);
+        // where the line meets D.  Beyond nucap (alpha > 0; tested without
+        // the quotient, H > 0) the cap is slack and the root is where the
+        // line meets (beta nu)^(-1/alpha), below that point
+        const float DA = D - A;
+        float nn;
+        if (DA > nucap * H) nn = slack_root(A, H, logbeta, alpha, inv_alpha, tcap, __logf(DA) - __logf(H), nu);
+        else nn = DA / H;
         if (descending && !(nn < nu)) break;  // rounding: no further descent
         nu = nn;
         prev = mask;

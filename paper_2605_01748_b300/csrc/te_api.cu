@@ -331,6 +331,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     unsigned* d_rowoff;
     int *d_slotbase, *d_demand_of;
     te::BlockMeta* d_blkmeta;
+    unsigned* d_hops;
     float *d_Dn, *d_cap, *d_ne, *d_inv;
     unsigned char* d_np;
     long long* d_slot_path;
@@ -342,6 +343,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&d_slotbase, sizeof(int) * hl.slotbase.size()));
     A(h->alloc(&d_demand_of, sizeof(int) * ND));
     A(h->alloc(&d_blkmeta, sizeof(te::BlockMeta) * (size_t)nblocks));
+    A(h->alloc(&d_hops, sizeof(unsigned) * hl.hops.size()));
     A(h->alloc(&d_Dn, sizeof(float) * ND));
     A(h->alloc(&h->Dc, sizeof(double) * ND));
     A(h->alloc(&d_np, ND));
@@ -388,6 +390,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(cudaMemcpyAsync(d_slotbase, hl.slotbase.data(), sizeof(int) * hl.slotbase.size(), cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_demand_of, hl.demand_of.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_blkmeta, hl.blkmeta.data(), sizeof(te::BlockMeta) * (size_t)nblocks, cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_hops, hl.hops.data(), sizeof(unsigned) * hl.hops.size(), cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_Dn, hl.Dn.data(), sizeof(float) * ND, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(h->Dc, hl.Dc.data(), sizeof(double) * ND, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_np, hl.np.data(), ND, cudaMemcpyHostToDevice, s));
@@ -408,6 +411,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     L.dpb = DPB;
     L.max_block_rows = max_block_rows;
     L.blkmeta = d_blkmeta;
+    L.hops = d_hops;
     L.nslots = nslots;
     L.nrows = nrows;
     L.id_bytes = id_bytes;
@@ -428,10 +432,11 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     L.inv_ne = d_inv;
     // algorithmic traffic of one iteration: the edge ids once, the rates read
     // and written, per demand its value and its multiplier read and written,
-    // per block its metadata record
+    // per block its metadata record and its lanes' hop counts
     h->bytes_per_iter = (long long)(sizeof(uint16_t) * hl.ids.size()) + 2LL * (long long)sizeof(float) * (long long)ns +
                         3LL * (long long)sizeof(float) * (long long)ND +
-                        (long long)sizeof(te::BlockMeta) * (long long)nblocks;
+                        (long long)sizeof(te::BlockMeta) * (long long)nblocks +
+                        (long long)sizeof(unsigned) * (long long)hl.hops.size();
     te_status rs = te_reset(h);
     if (rs != TE_OK) return bail(rs);
     *out = h;

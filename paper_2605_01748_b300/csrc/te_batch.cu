@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
         sc.converged = 0;
         sc.stop_reason = 0;
         long long done = 0;
-        const BlockCtx bc{a.Dn + I.dslot0, a.lam + I.dslot0, a.blkres + (size_t)I.res0 * 3, a.dpb, (uint16_t)E};
+        const BlockCtx bc{a.Dn + I.dslot0, a.lam + I.dslot0, a.blkres + (size_t)I.res0 * 3, nullptr, a.dpb, (uint16_t)E};
         const BlockMeta* bm = a.blkmeta + I.meta0;
         const uint16_t* ids = a.ids + (size_t)I.row0 * kLanes;
         const float* cap = a.cap_n + eo;
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
 
             // phase A: the instance's blocks, shared among the warps
             float unused[3];
-            run_blocks<G, kStageRows, false>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
+            run_blocks<G, kStageRows, false, false>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
                                              logbeta, beta_f, alpha, inv_alpha, unused);
             __syncthreads();
             if (*(volatile int*)a.status != 0) failed = true;
@@ -701,6 +701,7 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
         V.rowoff = b->rowoff + lro[j];
         V.slotbase = b->slotbase + lso[j];
         V.blkmeta = b->blkmeta + lmeta0[j];
+        V.hops = nullptr;  // the batch kernel counts hops in its gather
         V.Dn = b->Dn + I.dslot0;
         V.np = b->np + (size_t)lmeta0[j] * b->dpb;
         V.demand_of = b->demand_of + (size_t)lmeta0[j] * b->dpb;

@@ -87,6 +87,7 @@ struct Layout {
     const unsigned* rowoff;      // [nslots+1]
     const int* slotbase;         // [nblocks+1]
     const BlockMeta* blkmeta;    // [nblocks]
+    const unsigned* hops;        // [nblocks*32] hop counts of lane l's paths, slot j in bits 8j..8j+7
     const float* Dn;             // [nblocks*dpb] normalised demand, 0 on padding
     const unsigned char* np;     // [nblocks*dpb] paths of the demand
     const int* demand_of;        // [nblocks*dpb] caller demand index, -1 on padding

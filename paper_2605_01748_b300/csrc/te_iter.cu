@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         // its warp's blocks in FP32 in the order of the interleave).
         float acc[3] = {0.f, 0.f, 0.f};
         if (!failed) {
-            const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows, true>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
+            const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.hops, a.L.dpb, (uint16_t)a.L.E};
+            run_blocks<G, kIterStageRows, true, true>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
                                                 h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         __syncthreads();

@@ -242,29 +242,33 @@ __device__ __forceinline__ uint16_t lds_u16(unsigned addr) {
 // memory (STAGED) or in global memory.
 // What the per-block code needs besides the block itself: the demand and
 // multiplier arrays (indexed by demand slot), the per-block residual terms,
-// demands per block and the padding id.
+// the per-lane hop counts (HOPS), demands per block and the padding id.
 struct BlockCtx {
     const float* Dn;
     float* lam;
     float* blkres;
+    const unsigned* hops;
     int dpb;
     uint16_t sentinel;
 };
 
 // Per-lane inputs of one block read from global memory: the lane's rates,
-// its demand and the demand's multiplier.  Loaded one block ahead of use.
+// its demand, the demand's multiplier and (HOPS) the hop counts of the
+// lane's paths, slot j in bits 8j..8j+7.  Loaded one block ahead of use.
 struct BlockIn {
     float x[kMaxPathsPerLane];
     float D, lam;
+    unsigned nb;
 };
 
-template <int G>
+template <int G, bool HOPS>
 __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int lane, int s0, int KB,
                                                  const float* __restrict__ xin) {
     BlockIn in;
     const size_t di = (size_t)b * a.dpb + lane / G;
     in.D = __ldg(&a.Dn[di]);
     in.lam = __ldcg(&a.lam[di]);
+    in.nb = HOPS ? __ldg(&a.hops[(size_t)b * kLanes + lane]) : 0u;
     const float* xp = xin + (size_t)s0 * kLanes + lane;
     #pragma unroll
     for (int j = 0; j < kMaxPathsPerLane; ++j) {
@@ -276,8 +280,9 @@ __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int l
 
 // ACC: the block's residual terms are added into this lane's running sums
 // acc[3] (the caller reduces them once per phase), else summed over the warp
-// and stored per block.
-template <int G, bool STAGED, bool ACC>
+// and stored per block.  HOPS: the hop counts come with the block's inputs,
+// else the gather counts the non-padding ids.
+template <int G, bool STAGED, bool ACC, bool HOPS>
 __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane, const uint16_t* bids, int s0,
                                               unsigned counts, int KB, const BlockIn& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
@@ -299,8 +304,8 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
         if (STAGED) return lds_u16(sb + row * (unsigned)(kLanes * sizeof(uint16_t)));
         return __ldg(&bids[(size_t)row * kLanes + lane]);
     };
-    unsigned rs = 0;      // first row of slot j within the block
-    unsigned nbits = 0u;  // hop count n of slot j's path in bits 8j..8j+7
+    unsigned rs = 0;                      // first row of slot j within the block
+    unsigned nbits = HOPS ? in.nb : 0u;  // hop count n of slot j's path in bits 8j..8j+7
     #pragma unroll
     for (int j = 0; j < KL; ++j) {
         m[j] = 0.f;
@@ -308,12 +313,12 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
         if (j < KB) {
             const unsigned cnt = (counts >> (8 * j)) & 0xffu;
             float q = 0.f;
-            int n = 0;
+            int n = HOPS ? (int)((nbits >> (8 * j)) & 0xffu) : 0;
             #pragma unroll 4
             for (unsigned r = 0; r < cnt; ++r) {
                 const uint16_t id = id_at(rs + r);
                 q += w_s[id];
-                n += (id != sentinel);
+                if (!HOPS) n += (id != sentinel);
             }
             if (n > 0) {
                 // 1/n by the hardware's approximate reciprocal (within an
@@ -322,7 +327,7 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
                 an[j] = __fdividef(1.f, (float)n);
                 m[j] = fmaf(-q, an[j], xo[j]);
             }
-            nbits |= (unsigned)n << (8 * j);
+            if (!HOPS) nbits |= (unsigned)n << (8 * j);
             rs += cnt;
         }
     }
@@ -415,8 +420,9 @@ struct WarpStage {
 // cycles per block against 6.8 % less time per iteration with cp.async.
 //
 // ACC (see process_block): the residual terms of the warp's blocks are summed
-// per lane into acc[3], in the fixed order of the interleave.
-template <int G, int ROWS, bool ACC>
+// per lane into acc[3], in the fixed order of the interleave.  HOPS: see
+// process_block.
+template <int G, int ROWS, bool ACC, bool HOPS>
 __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __restrict__ blkmeta,
                            const uint16_t* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
@@ -464,7 +470,7 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
         const int s0 = (int)__shfl_sync(0xffffffffu, m.s0, 0);
         const int KB = (int)__shfl_sync(0xffffffffu, m.kb, 0);
         BlockIn in{};
-        if (b < none) in = load_block_in<G>(bc, b, lane, s0, KB, xin);
+        if (b < none) in = load_block_in<G, HOPS>(bc, b, lane, s0, KB, xin);
         return in;
     };
     int b0 = grab();
@@ -489,11 +495,11 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
             // lane; the __syncwarp makes each lane's copies visible to all
             cp_async_wait_prev();
             __syncwarp();
-            process_block<G, true, ACC>(bc, b0, lane, ws.buf[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
+            process_block<G, true, ACC, HOPS>(bc, b0, lane, ws.buf[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                         inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         } else {
             const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
-            process_block<G, false, ACC>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
+            process_block<G, false, ACC, HOPS>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
                                          w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         b0 = b1;

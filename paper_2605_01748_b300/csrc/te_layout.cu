@@ -107,6 +107,7 @@ te_status build_host_layout(const te_topology* topo, const te_paths* P, const do
     const size_t ND = (size_t)nblocks * DPB;  // demand slots
     out.ids.assign((size_t)nrows * kLanes, (uint16_t)E);
     std::vector<long long> slot_path((size_t)nslots * kLanes, -1);
+    std::vector<unsigned> hops((size_t)nblocks * kLanes, 0u);
     std::vector<int> demand_of(ND, -1);
     std::vector<float> Dn(ND, 0.f);
     std::vector<double> Dc(ND, 0.0);
@@ -126,6 +127,7 @@ te_status build_host_layout(const te_topology* topo, const te_paths* P, const do
                 const long long s = slotbase[b] + p / G, r = p0 + p;
                 slot_path[(size_t)s * kLanes + lane] = r;
                 const long long i0 = P->path_edge_off[r], n = P->path_edge_off[r + 1] - i0;
+                hops[(size_t)b * kLanes + lane] |= (unsigned)n << (8 * (p / G));
                 for (long long k = 0; k < n; ++k) {
                     const size_t at = ((size_t)rowoff[s] + (size_t)k) * kLanes + lane;
                     out.ids[at] = (uint16_t)P->path_edges[i0 + k];
@@ -193,6 +195,7 @@ te_status build_host_layout(const te_topology* topo, const te_paths* P, const do
     out.rowoff = std::move(rowoff);
     out.slotbase = std::move(slotbase);
     out.blkmeta = std::move(blkmeta);
+    out.hops = std::move(hops);
     out.demand_of = std::move(demand_of);
     out.Dn = std::move(Dn);
     out.Dc = std::move(Dc);

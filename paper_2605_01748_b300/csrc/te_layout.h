@@ -22,6 +22,7 @@ struct HostLayout {
     std::vector<unsigned> rowoff;        // [nslots+1]
     std::vector<int> slotbase;           // [nblocks+1]
     std::vector<BlockMeta> blkmeta;      // [nblocks]
+    std::vector<unsigned> hops;          // [nblocks*32] hop counts of a lane's paths, slot j in bits 8j..8j+7
     std::vector<int> demand_of;          // [nblocks*dpb]
     std::vector<float> Dn;               // [nblocks*dpb]
     std::vector<double> Dc;              // [nblocks*dpb]

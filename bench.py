@@ -21,7 +21,7 @@ is far over capacity it empties demands, and on this workload it stays below
 
 Default workload: the 1500-node synthetic WAN (10,056 directed edges, all
 2,248,500 ordered pairs as gravity demands, k = 16 paths, 36M paths, 215M
-path-edge incidences).  Inputs stay resident; each iteration streams 0.77 GB
+path-edge incidences).  Inputs stay resident; each iteration streams 0.80 GB
 (> the 126 MB L2) so no extra L2 flush is needed.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle

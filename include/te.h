@@ -172,8 +172,20 @@ te_status te_allocation(te_handle* h, float* x_out, int32_t project, int32_t out
  * Lagrangian dual bound g(p) = sum_e p_e C_e + sum_c max_{0<=S<=D_c}
  * [U_alpha(S) - pi_c S], pi_c = min_{r in P_c} sum_{e in r} p_e, at the
  * current prices p_e = beta u_e, minus sum_c U_alpha(S_c(x^)), at the
- * current alpha.  Any output pointer may be NULL. */
+ * current alpha (weak duality of the TE problem, Eqs. 1-4; tight at the
+ * optimum by Slater's condition, Appendix C).  x^ is the iterate after
+ * Algorithm 2 (Section 3.5).  Any output pointer may be NULL. */
 te_status te_gap(te_handle* h, double* gap_out, double* primal_out, double* dual_out);
+
+/* te_gap with the feasibility step chosen by project: TE_PROJECT_ALG2
+ * (the same as te_gap) or TE_PROJECT_SCALE (proportional scaling, see
+ * te_allocation).  Algorithm 2 trims whole paths and can leave a demand at
+ * S_c = 0, where U_alpha is -infinity for alpha >= 1 (the primal is then
+ * -INFINITY and the gap +INFINITY); scaling keeps every demand that has a
+ * rate, so its primal stays finite.  Errors: TE_EINVAL (NULL handle,
+ * another project value), TE_ECUDA. */
+te_status te_gap_projected(te_handle* h, int32_t project, double* gap_out, double* primal_out,
+                           double* dual_out);
 
 /* Current edge prices p_e = beta u_e in the caller's units (FP64,
  * [n_edges]); these are the capacity multipliers dual_cap_e of Eq. 9. */

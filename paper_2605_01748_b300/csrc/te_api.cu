@@ -559,18 +559,25 @@ extern "C" te_status te_allocation(te_handle* h, float* x_out, int32_t project, 
     return h->cuda(ce, "te_allocation");
 }
 
-extern "C" te_status te_gap(te_handle* h, double* gap_out, double* primal_out, double* dual_out) {
-    if (!h) return TE_EINVAL;
+extern "C" te_status te_gap_projected(te_handle* h, int32_t project, double* gap_out, double* primal_out,
+                                      double* dual_out) {
+    if (!h || (project != TE_PROJECT_ALG2 && project != TE_PROJECT_SCALE)) return TE_EINVAL;
     cudaStream_t s = h->stream;
     const size_t ns = (size_t)h->L.nslots * kLanes;
     const float* src = h->x + (size_t)h->hsc.xbuf * ns;
     cudaError_t ce = cudaSuccess;
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
     A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
-    A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
+    if (project == TE_PROJECT_ALG2) {
+        A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
+        h->launches += te::kProjectLaunches;
+    } else {
+        A(te::launch_project_scale(h->L, h->xtmp, h->ps, s));
+        h->launches += te::kProjectScaleLaunches;
+    }
     A(cudaMemsetAsync(h->gacc, 0, sizeof(double) * 4, s));
     A(te::launch_gap_impl(h->L, h->xtmp, h->u, h->hsc.beta, h->hsc.alpha, h->scale, h->Dc, h->gacc, s));
-    h->launches += te::kProjectLaunches + 2;
+    h->launches += 2;
     double acc[4] = {0, 0, 0, 0};
     A(cudaMemcpyAsync(acc, h->gacc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     A(cudaStreamSynchronize(s));
@@ -580,6 +587,10 @@ extern "C" te_status te_gap(te_handle* h, double* gap_out, double* primal_out, d
     if (primal_out) *primal_out = primal;
     if (dual_out) *dual_out = dual;
     return TE_OK;
+}
+
+extern "C" te_status te_gap(te_handle* h, double* gap_out, double* primal_out, double* dual_out) {
+    return te_gap_projected(h, TE_PROJECT_ALG2, gap_out, primal_out, dual_out);
 }
 
 extern "C" te_status te_prices(te_handle* h, double* p_out, int32_t out_is_device) {

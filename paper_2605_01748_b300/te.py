@@ -6,7 +6,7 @@ loads libte.so and fails loudly when the library has not been built
 (``python -m paper_2605_01748_b300.build``); there is no CPU fallback.
 
 The functions mirror the C entry points one to one (``te_create``,
-``te_solve``, ``te_allocation``, ``te_gap``, ``te_prices``,
+``te_solve``, ``te_allocation``, ``te_gap``, ``te_gap_projected``, ``te_prices``,
 ``te_set_warm_start``, ``te_reset``, ``te_trace``, ``te_layout``,
 ``te_destroy``, ``te_last_error``); :class:`TE` bundles a handle with them.
 """
@@ -30,8 +30,8 @@ PROJECT_NONE, PROJECT_ALG2, PROJECT_SCALE = 0, 1, 2
 STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "TE_ETIMEOUT",
                 5: "TE_ENUMERIC", 6: "TE_ENOTCONVERGED", 7: "TE_EUNSUPPORTED"}
 
-EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_gap", "te_prices",
-            "te_set_warm_start", "te_set_demands", "te_set_capacities", "te_reset", "te_trace", "te_layout",
+EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_gap", "te_gap_projected",
+            "te_prices", "te_set_warm_start", "te_set_demands", "te_set_capacities", "te_reset", "te_trace", "te_layout",
             "te_destroy", "te_last_error", "te_gap_noalloc", "te_batch_create", "te_batch_solve",
             "te_batch_allocation", "te_batch_reset", "te_batch_info", "te_batch_destroy", "te_batch_last_error",
             "te_gradient")
@@ -112,6 +112,8 @@ def _load() -> ctypes.CDLL:
     lib.te_allocation.argtypes = [H, P, ctypes.c_int32, ctypes.c_int32]
     lib.te_gap.restype = ctypes.c_int
     lib.te_gap.argtypes = [H, P, P, P]
+    lib.te_gap_projected.restype = ctypes.c_int
+    lib.te_gap_projected.argtypes = [H, ctypes.c_int32, P, P, P]
     lib.te_prices.restype = ctypes.c_int
     lib.te_prices.argtypes = [H, P, ctypes.c_int32]
     lib.te_set_warm_start.restype = ctypes.c_int
@@ -246,6 +248,14 @@ def te_gap(h):
     return g.value, p.value, d.value
 
 
+def te_gap_projected(h, project: int):
+    """(gap, primal, dual) of te_gap with the feasibility step `project`
+    (PROJECT_ALG2 or PROJECT_SCALE)."""
+    g, p, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(_lib.te_gap_projected(h, int(project), ctypes.byref(g), ctypes.byref(p), ctypes.byref(d)), h)
+    return g.value, p.value, d.value
+
+
 def te_prices(h, out) -> None:
     _check(_lib.te_prices(h, _ptr(out), int(_is_device(out))), h)
 
@@ -337,8 +347,12 @@ class TE:
         te_allocation(self.h, out, project)
         return out
 
-    def gap(self):
-        return te_gap(self.h)
+    def gap(self, project: int = PROJECT_ALG2):
+        """(gap, primal, dual); project selects the feasibility step applied
+        before the primal utility (PROJECT_ALG2 as te_gap, or PROJECT_SCALE)."""
+        if project == PROJECT_ALG2:
+            return te_gap(self.h)
+        return te_gap_projected(self.h, project)
 
     def prices(self, out=None) -> np.ndarray:
         if out is None:

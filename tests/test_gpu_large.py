@@ -58,3 +58,18 @@ def test_large_runs_repeat_and_stay_feasible(te, large):
         assert (O.demand_totals(large, xp) <= large.demand * (1 + 1e-5)).all()
         assert (O.edge_loads(large, xp) <= large.capacity * (1 + 1e-5)).all()
     t.close()
+
+
+def test_large_gap_after_scaling_is_finite(te, large):
+    """At alpha = 1 Algorithm 2 empties some demands of this workload (their
+    utility log 0 is -inf, so te_gap reports an infinite gap); after
+    proportional scaling every demand keeps a rate and the gap is finite and
+    non-negative up to rounding (weak duality)."""
+    t = te.TE(large, alpha_target=1.0, alpha_start=1.0, continuation=0)
+    t.solve(400)
+    g, pr, du = t.gap(project=te.PROJECT_SCALE)
+    assert np.isfinite(g) and np.isfinite(pr) and np.isfinite(du)
+    assert g >= -1e-6 * abs(pr)
+    xs = t.allocation(project=te.PROJECT_SCALE).astype(np.float64)
+    assert (O.demand_totals(large, xs) > 0).all()
+    t.close()

@@ -219,6 +219,14 @@ def test_gap_parity(te, tiny):
         assert abs(du - duo) <= 1e-6 * max(1.0, abs(duo))
         assert g >= -1e-6 * abs(pr)
         assert g <= 1e-2 * abs(pr), (g, pr)
+        # the same gap after proportional scaling instead of Algorithm 2
+        gs, prs, dus = t.gap(project=te.PROJECT_SCALE)
+        xs = t.allocation(project=te.PROJECT_SCALE).astype(np.float64)
+        gso, prso, duso = O.gap(tiny, xs, t.prices(), alpha)
+        assert abs(prs - prso) <= 1e-6 * max(1.0, abs(prso))
+        assert abs(dus - duso) <= 1e-6 * max(1.0, abs(duso))
+        assert dus == du  # the dual bound does not depend on the feasibility step
+        assert gs >= -1e-6 * abs(prs)
         t.close()
 
 

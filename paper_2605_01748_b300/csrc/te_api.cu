@@ -95,6 +95,7 @@ struct te_handle {
     float* xtmp = nullptr;    // [nslots*32]
     float* user = nullptr;    // [P]
     double* gacc = nullptr;   // [3]
+    double* gslots = nullptr; // [2*gap_slot_count] per-CTA partials of the gap
     double* pbuf = nullptr;   // [E]
     double* dstage = nullptr; // [K] staging of new demands
     double* cstage = nullptr; // [E] staging of new capacities
@@ -365,17 +366,23 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->xtmp, sizeof(float) * ns));
     A(h->alloc(&h->user, sizeof(float) * (size_t)NP));
     A(h->alloc(&h->gacc, sizeof(double) * 4));
+    {
+        te::Layout lg{};
+        lg.nblocks = nblocks;
+        lg.dpb = DPB;
+        A(h->alloc(&h->gslots, sizeof(double) * 2 * te::gap_slot_count(lg)));
+    }
     A(h->alloc(&h->pbuf, sizeof(double) * E));
     A(h->alloc(&h->dstage, sizeof(double) * K));
     A(h->alloc(&h->cstage, sizeof(double) * E));
     A(h->alloc(&h->flag, sizeof(int)));
     A(h->alloc(&h->lam, sizeof(float) * ND));
     A(h->alloc(&h->ps.S, sizeof(double) * ND));
-    A(h->alloc(&h->ps.loads, sizeof(double) * E));
+    A(h->alloc(&h->ps.loads, sizeof(unsigned long long) * E));
     A(h->alloc(&h->ps.viol, (size_t)E));
     A(h->alloc(&h->ps.vidx, sizeof(int) * E));
     A(h->alloc(&h->ps.nviol, sizeof(int)));
-    A(h->alloc(&h->ps.hist, sizeof(double) * 256 * (size_t)E));
+    A(h->alloc(&h->ps.hist, sizeof(unsigned long long) * 256 * (size_t)E));
     A(h->alloc(&h->ps.prefix, sizeof(unsigned long long) * E));
     A(h->alloc(&h->ps.rem, sizeof(double) * E));
     A(h->alloc(&h->ps.Cp, ns));
@@ -575,9 +582,8 @@ extern "C" te_status te_gap_projected(te_handle* h, int32_t project, double* gap
         A(te::launch_project_scale(h->L, h->xtmp, h->ps, s));
         h->launches += te::kProjectScaleLaunches;
     }
-    A(cudaMemsetAsync(h->gacc, 0, sizeof(double) * 4, s));
-    A(te::launch_gap_impl(h->L, h->xtmp, h->u, h->hsc.beta, h->hsc.alpha, h->scale, h->Dc, h->gacc, s));
-    h->launches += 2;
+    A(te::launch_gap_impl(h->L, h->xtmp, h->u, h->hsc.beta, h->hsc.alpha, h->scale, h->Dc, h->gacc, h->gslots, s));
+    h->launches += te::kGapLaunches;
     double acc[4] = {0, 0, 0, 0};
     A(cudaMemcpyAsync(acc, h->gacc, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
     A(cudaStreamSynchronize(s));

@@ -627,11 +627,11 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     A(b->alloc(&b->xtmp, sizeof(float) * maxNS));
     A(b->alloc(&b->user, sizeof(float) * maxP));
     A(b->alloc(&b->ps.S, sizeof(double) * maxND));
-    A(b->alloc(&b->ps.loads, sizeof(double) * E));
+    A(b->alloc(&b->ps.loads, sizeof(unsigned long long) * E));
     A(b->alloc(&b->ps.viol, (size_t)E));
     A(b->alloc(&b->ps.vidx, sizeof(int) * E));
     A(b->alloc(&b->ps.nviol, sizeof(int)));
-    A(b->alloc(&b->ps.hist, sizeof(double) * 256 * (size_t)E));
+    A(b->alloc(&b->ps.hist, sizeof(unsigned long long) * 256 * (size_t)E));
     A(b->alloc(&b->ps.prefix, sizeof(unsigned long long) * E));
     A(b->alloc(&b->ps.rem, sizeof(double) * E));
     A(b->alloc(&b->ps.Cp, maxNS));

@@ -129,16 +129,16 @@ cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st);
 
 // Feasibility projection (Algorithm 2) of a copy x (sliced layout, in place).
-// The projection's sums (demand totals, edge loads, remainders, histograms)
-// are FP64 so that the violation tests see the loads of the FP32 rates
-// without accumulation error.
+// Demand totals and remainders are FP64; the edge loads and radix-select
+// histograms are exact 64-bit integer sums of the FP32 rates in units of
+// 2^-40 (order-free, so the projection is deterministic).
 struct ProjScratch {
     double* S;           // [nblocks*dpb] demand totals
-    double* loads;       // [E]
+    unsigned long long* loads;  // [E] fixed point, rates rounded up
     unsigned char* viol; // [E] 1 if L_e > C_e
     int* vidx;           // [E] compact index of violated edges or -1
     int* nviol;          // [1]
-    double* hist;        // [E*256] radix-select histograms
+    unsigned long long* hist;   // [E*256] radix-select histograms, fixed point, rates rounded down
     unsigned long long* prefix;  // [E] selected key prefix per violated edge
     double* rem;         // [E] remaining violation per violated edge
     unsigned char* Cp;   // [nslots*32] violated edges per path
@@ -157,11 +157,15 @@ cudaError_t launch_to_user(const Layout& L, const float* x, float* out, float sc
 cudaError_t launch_from_user(const Layout& L, const float* in, float* x, float inv_scale, cudaStream_t st);
 
 // Duality gap terms of a feasible sliced x (normalised) at prices
-// p = beta*u: acc[0] += sum_c U(S_c), acc[1] += sum_c max_S [U(S) - pi_c S],
-// acc[2] += sum_e p_e C_e, all in caller units (acc zeroed by the caller).
+// p = beta*u: acc[0] = sum_c U(S_c), acc[1] = sum_c max_S [U(S) - pi_c S],
+// acc[2] = sum_e p_e C_e, all in caller units.
 // Dc: caller-unit demand of each demand slot (0 on padding).
+// The sums are deterministic: per-CTA partials in slots (gap_slot_count(L)
+// pairs of doubles, no initial value needed) added in a fixed order.
+size_t gap_slot_count(const Layout& L);
 cudaError_t launch_gap_impl(const Layout& L, const float* x, const float* u, double beta, double alpha,
-                            double scale, const double* Dc, double* acc, cudaStream_t st);
+                            double scale, const double* Dc, double* acc, double* slots, cudaStream_t st);
+constexpr int kGapLaunches = 3;
 
 // Reverse-mode step of one fixed-schedule iteration (te_adjoint.cu): FP64
 // adjoints of the rates (per path lane of the sliced layout), of the edge

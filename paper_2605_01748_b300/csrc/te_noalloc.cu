@@ -19,6 +19,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "te.h"
@@ -30,10 +33,18 @@ constexpr int kGapScratchSlots = 16384;  // demand CTAs + edge CTAs per call
 
 static __device__ __align__(256) double g_gap_scratch[2 * kGapScratchSlots];
 
-// Host-side device addresses of g_gap_scratch, one per device, resolved once.
+// Host-side device addresses of g_gap_scratch, one per device, each tagged
+// with the unique id of the CUDA context it was resolved in.  After a
+// cudaDeviceReset (or any re-creation of the primary context) the module is
+// loaded again, possibly at another address; the id then differs and the
+// address is looked up again.
 constexpr int kMaxDevices = 64;
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    double* ptr;
+};
 std::mutex g_mu;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+ScratchEntry g_scratch[kMaxDevices] = {};
 
 __device__ double na_utility(double S, double alpha) {
     if (alpha == 1.0) return log(S);
@@ -115,21 +126,52 @@ __global__ void k_gap_finish(int n, const double* scratch, double* out) {
     }
 }
 
-// Device address of g_gap_scratch on the current device; resolved on the
-// first call per device.
+// Unique id of the current context (0 if none is current or the driver
+// entry points are unavailable).  The driver functions are reached through
+// the runtime's entry-point query, so the library does not link libcuda.
+unsigned long long current_ctx_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f);
+    });
+    if (!get_current || !get_id) return 0ull;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0ull;
+    unsigned long long id = 0ull;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0ull;
+    return id;
+}
+
+// Device address of g_gap_scratch on the current device, valid in the
+// current context.  Resolved by cudaGetSymbolAddress (with this device
+// current) on the first call per device, and again whenever the current
+// context is not the one the cached address belongs to.
 te_status scratch_for_current_device(double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TE_ECUDA;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* ptr = nullptr;
-        if (cudaGetSymbolAddress(&ptr, g_gap_scratch) != cudaSuccess || !ptr) {
-            cudaGetLastError();
-            return TE_ECUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<double*>(ptr);
+    ScratchEntry& ent = g_scratch[dev];
+    const unsigned long long id = current_ctx_id();
+    if (ent.ptr && id != 0ull && ent.ctx_id == id) {
+        *out = ent.ptr;
+        return TE_OK;
     }
-    *out = g_scratch_ptr[dev];
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_gap_scratch) != cudaSuccess || !ptr) return TE_ECUDA;
+    // the lookup made the device's primary context current if none was
+    ent.ctx_id = current_ctx_id();
+    ent.ptr = static_cast<double*>(ptr);
+    *out = ent.ptr;
     return TE_OK;
 }
 
@@ -146,6 +188,9 @@ extern "C" te_status te_gap_noalloc(int32_t n_edges, int32_t n_demands, int64_t 
     const long long ndc = ((long long)n_demands + kGapThreads - 1) / kGapThreads;
     const long long nec = ((long long)n_edges + kGapThreads - 1) / kGapThreads;
     if (ndc + nec > kGapScratchSlots) return TE_EUNSUPPORTED;  // more than ~4.19M demands plus edges
+    // an error left pending by an earlier, unrelated call is not ours to
+    // clear: report it without queuing work and leave it pending
+    if (cudaPeekAtLastError() != cudaSuccess) return TE_ECUDA;
     double* scratch = nullptr;
     te_status st = scratch_for_current_device(&scratch);
     if (st != TE_OK) return st;
@@ -153,6 +198,14 @@ extern "C" te_status te_gap_noalloc(int32_t n_edges, int32_t n_demands, int64_t 
     k_gap_partials<<<(unsigned)(ndc + nec), kGapThreads, 0, s>>>(n_demands, n_edges, demand_path_off,
                                                                   path_edge_off, path_edges, demands, capacities,
                                                                   x, prices, alpha, (int)ndc, scratch);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();  // this launch's own error
+        return TE_ECUDA;
+    }
     k_gap_finish<<<1, kGapThreads, 0, s>>>((int)(ndc + nec), scratch, out);
-    return cudaGetLastError() == cudaSuccess ? TE_OK : TE_ECUDA;
+    if (cudaPeekAtLastError() != cudaSuccess) {
+        cudaGetLastError();
+        return TE_ECUDA;
+    }
+    return TE_OK;
 }

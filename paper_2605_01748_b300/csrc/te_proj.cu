@@ -19,6 +19,14 @@
 //      key order reaches V_e; paths above it are trimmed in full and the
 //      threshold path by the remainder.
 // Scores are compared as alpha*log(S_c) + log(C_p) in FP32.
+//
+// Edge loads and the radix-select histograms are sums over many paths; they
+// are accumulated as 64-bit integers in units of 2^-40 (normalised
+// rates), so the sums do not depend on the order of the atomics and two
+// projections of the same iterate return the same bits.  Rounding is
+// conservative: a rate enters the loads rounded up (a violation is never
+// missed, never under-estimated) and the histograms rounded down (the trims
+// cover at least the violation).
 #include <math.h>
 #include <stdint.h>
 
@@ -28,6 +36,19 @@ namespace te {
 namespace {
 
 constexpr int kThreads = 256;
+// 2^-40 resolution; a load of up to 2^23 normalised units fits in 63 bits
+// (te_create bounds the demand through an edge far below that)
+constexpr double kFixScale = 1099511627776.0;  // 2^40
+
+__device__ __forceinline__ unsigned long long fix_up(float v) {
+    return (unsigned long long)ceil((double)v * kFixScale);
+}
+__device__ __forceinline__ unsigned long long fix_down(float v) {
+    return (unsigned long long)floor((double)v * kFixScale);
+}
+// integer sum back to normalised units, rounded up / down
+__device__ __forceinline__ double unfix_up(unsigned long long q) { return __ull2double_ru(q) * (1.0 / kFixScale); }
+__device__ __forceinline__ double unfix_down(unsigned long long q) { return __ull2double_rd(q) * (1.0 / kFixScale); }
 
 inline unsigned grid_for(long long n, int threads) {
     long long b = (n + threads - 1) / threads;
@@ -62,9 +83,10 @@ __global__ void k_clamp_sum(Layout L, float* x, double* S) {
     S[i] = acc;
 }
 
-// L_e = sum of rates over the paths through e (loads must be zeroed).
+// L_e = sum of rates over the paths through e, each rounded up to the
+// fixed-point unit (loads must be zeroed).
 template <typename IdT>
-__global__ void k_loads(Layout L, const float* x, double* loads) {
+__global__ void k_loads(Layout L, const float* x, unsigned long long* loads) {
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -74,19 +96,22 @@ __global__ void k_loads(Layout L, const float* x, double* loads) {
         const size_t sl = (size_t)(s0 + j);
         const float v = x[sl * kLanes + lane];
         if (v == 0.f) continue;
+        const unsigned long long q = fix_up(v);
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
-            if ((int)id != L.E) atomicAdd(&loads[id], (double)v);
+            if ((int)id != L.E) atomicAdd(&loads[id], q);
         }
     }
 }
 
 // V_e > 0 flags, compact indices of violated edges and their violation.
-__global__ void k_viol(Layout L, const double* loads, unsigned char* viol, int* vidx, int* nviol, double* rem,
-                       unsigned long long* prefix) {
+// The compact index of an edge depends on the order of the atomics, but every
+// result below is computed per edge and does not depend on it.
+__global__ void k_viol(Layout L, const unsigned long long* loads, unsigned char* viol, int* vidx, int* nviol,
+                       double* rem, unsigned long long* prefix) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= L.E) return;
-    const double V = loads[e] - (double)L.cap_n[e];
+    const double V = unfix_up(loads[e]) - (double)L.cap_n[e];
     if (V > 0.0) {
         viol[e] = 1;
         const int v = atomicAdd(nviol, 1);
@@ -167,7 +192,7 @@ __device__ __forceinline__ unsigned long long path_key(double S, int Cp, float a
 template <typename IdT>
 __global__ void k_select_hist(Layout L, const float* x, const double* S, const unsigned char* Cp,
                               const int* vidx, const unsigned long long* prefix, const unsigned char* done,
-                              double* hist, float alpha, int pass) {
+                              unsigned long long* hist, float alpha, int pass) {
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -182,33 +207,36 @@ __global__ void k_select_hist(Layout L, const float* x, const double* S, const u
         const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha,
                                                 L.slot_path[sl * kLanes + lane]);
         const int digit = (int)((key >> shift) & 0xffull);
+        const unsigned long long q = fix_down(v);
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
             if ((int)id == L.E) continue;
             const int vi = vidx[id];
             if (vi < 0 || done[vi]) continue;
             if (pass > 0 && ((key ^ prefix[vi]) >> (shift + 8)) != 0ull) continue;
-            atomicAdd(&hist[(size_t)vi * 256 + digit], (double)v);
+            atomicAdd(&hist[(size_t)vi * 256 + digit], q);
         }
     }
 }
 
 // Per violated edge: choose the digit at which the running sum (from the top
-// digit down) reaches the remaining violation.
-__global__ void k_select_pick(const int* nviol, double* hist, unsigned long long* prefix, double* rem,
+// digit down) reaches the remaining violation.  The sums are integers (rates
+// rounded down), compared with the violation rounded up.
+__global__ void k_select_pick(const int* nviol, unsigned long long* hist, unsigned long long* prefix, double* rem,
                               unsigned char* done, int pass) {
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= *nviol || done[v]) return;
     const int shift = 56 - 8 * pass;
-    double* h = hist + (size_t)v * 256;
-    double cum = 0.0;
+    unsigned long long* h = hist + (size_t)v * 256;
+    unsigned long long cum = 0ull;
     const double need = rem[v];
+    const unsigned long long need_q = (unsigned long long)ceil(need * kFixScale);
     int pick = -1;
     for (int d = 255; d >= 0; --d) {
-        const double c = h[d];
-        h[d] = 0.0;  // ready for the next pass
+        const unsigned long long c = h[d];
+        h[d] = 0ull;  // ready for the next pass
         if (pick < 0) {
-            if (cum + c >= need && c > 0.0) pick = d;
+            if (cum + c >= need_q && c > 0ull) pick = d;
             else cum += c;
         }
     }
@@ -218,7 +246,7 @@ __global__ void k_select_pick(const int* nviol, double* hist, unsigned long long
         return;
     }
     prefix[v] |= (unsigned long long)pick << shift;
-    rem[v] = need - cum;
+    rem[v] = need - unfix_down(cum);
 }
 
 // Apply: every path loses the largest trim planned for it by its violated
@@ -307,12 +335,13 @@ __global__ void k_demand_scale(Layout L, float* x, const double* S) {
         }
 }
 
-// f_e = min(1, C_e / L_e).
-__global__ void k_edge_factor(Layout L, const double* loads, double* f) {
+// f_e = min(1, C_e / L_e), L_e rounded up.
+__global__ void k_edge_factor(Layout L, const unsigned long long* loads, double* f) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= L.E) return;
     const double C = (double)L.cap_n[e];
-    f[e] = loads[e] > C ? __ddiv_rz(C, loads[e]) : 1.0;
+    const double Le = unfix_up(loads[e]);
+    f[e] = Le > C ? __ddiv_rz(C, Le) : 1.0;
 }
 
 // x_p <- x_p * min_{e in p} f_e.  One thread per lane of a block.
@@ -344,7 +373,7 @@ cudaError_t project_scale_t(const Layout& L, float* x, const ProjScratch& s, cud
     cudaError_t err;
     k_clamp_sum<<<gd, kThreads, 0, st>>>(L, x, s.S);
     k_demand_scale<<<gd, kThreads, 0, st>>>(L, x, s.S);
-    if ((err = cudaMemsetAsync(s.loads, 0, sizeof(double) * (size_t)L.E, st)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(s.loads, 0, sizeof(unsigned long long) * (size_t)L.E, st)) != cudaSuccess) return err;
     k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
     k_edge_factor<<<ge, kThreads, 0, st>>>(L, s.loads, s.rem);
     k_path_scale<IdT><<<gl, kThreads, 0, st>>>(L, x, s.rem);
@@ -360,7 +389,8 @@ cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch&
     const unsigned gd = grid_for((long long)L.nblocks * L.dpb, kThreads);
     for (int round = 0; round < 2; ++round) {
         k_clamp_sum<<<gd, kThreads, 0, st>>>(L, x, s.S);
-        if ((err = cudaMemsetAsync(s.loads, 0, sizeof(double) * (size_t)L.E, st)) != cudaSuccess) return err;
+        if ((err = cudaMemsetAsync(s.loads, 0, sizeof(unsigned long long) * (size_t)L.E, st)) != cudaSuccess)
+            return err;
         if ((err = cudaMemsetAsync(s.nviol, 0, sizeof(int), st)) != cudaSuccess) return err;
         k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
         k_viol<<<ge, kThreads, 0, st>>>(L, s.loads, s.viol, s.vidx, s.nviol, s.rem, s.prefix);
@@ -370,7 +400,8 @@ cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch&
     // capacity step: radix select of each violated edge's threshold path
     unsigned char* done = s.viol;  // reuse: per violated-edge flags (E bytes >= nviol)
     if ((err = cudaMemsetAsync(done, 0, (size_t)L.E, st)) != cudaSuccess) return err;
-    if ((err = cudaMemsetAsync(s.hist, 0, sizeof(double) * 256 * (size_t)L.E, st)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(s.hist, 0, sizeof(unsigned long long) * 256 * (size_t)L.E, st)) != cudaSuccess)
+        return err;
     for (int pass = 0; pass < 8; ++pass) {
         k_select_hist<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, done, s.hist, alpha, pass);
         k_select_pick<<<ge, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);

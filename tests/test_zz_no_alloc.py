@@ -76,3 +76,70 @@ def test_gap_noalloc_rejects_oversized_input():
     st = te.lib().te_gap_noalloc(1, 5_000_000, 5_000_000, 5_000_000, te._ptr(z64), te._ptr(z64), te._ptr(z32),
                                  te._ptr(d), te._ptr(d), te._ptr(x), te._ptr(d), 1.0, te._ptr(out), 0)
     assert st == te.TE_EUNSUPPORTED
+
+
+_RESET_CHILD = r"""
+import ctypes, json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2605_01748_b300 import instances, te
+
+rt = ctypes.CDLL("libcudart.so.13")  # the runtime that libte.so links
+rt.cudaMalloc.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t]
+rt.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+rt.cudaFree.argtypes = [ctypes.c_void_p]
+inst = instances.make_tiny()
+t = te.TE(inst, alpha_target=1.0, alpha_start=1.0, gamma=1e-4)
+t.solve(3000)
+ref = list(t.gap())
+xp = t.allocation(project=te.PROJECT_ALG2)
+p = t.prices()
+alpha = t.solve(0)["alpha"]
+t.close()
+host = [np.ascontiguousarray(a) for a in (inst.demand_path_off.astype(np.int64),
+        inst.path_edge_off.astype(np.int64), inst.path_edges.astype(np.int32), inst.demand.astype(np.float64),
+        inst.capacity.astype(np.float64), xp.astype(np.float32), p.astype(np.float64),
+        np.full(3, np.nan))]
+
+def run():
+    bufs = []
+    for a in host:
+        ptr = ctypes.c_void_p()
+        assert rt.cudaMalloc(ctypes.byref(ptr), a.nbytes) == 0
+        assert rt.cudaMemcpy(ptr, a.ctypes.data, a.nbytes, 1) == 0
+        bufs.append(ptr)
+    st = te.lib().te_gap_noalloc(inst.n_edges, inst.n_demands, inst.n_paths, int(host[2].shape[0]), *bufs[:7],
+                                 float(alpha), bufs[7], None)
+    assert st == 0, st
+    assert rt.cudaDeviceSynchronize() == 0
+    res = np.zeros(3)
+    assert rt.cudaMemcpy(res.ctypes.data, bufs[7], 24, 2) == 0
+    for b in bufs:
+        rt.cudaFree(b)
+    return res.tolist()
+
+first = run()
+assert rt.cudaDeviceReset() == 0  # ends this process's context only
+second = run()
+print(json.dumps({"ref": ref, "first": first, "second": second}))
+"""
+
+
+def test_gap_noalloc_after_device_reset():
+    """After cudaDeviceReset the library's module is loaded again in a new
+    context; te_gap_noalloc must look up its static array's address again
+    instead of reusing the old one.  Runs in a child process that uses only
+    the CUDA runtime (no torch), so resetting the device strands nothing."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", _RESET_CHILD, root], capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    g_ref, pr_ref, du_ref = d["ref"]
+    for g, pr, du in (d["first"], d["second"]):
+        assert _close(pr, pr_ref) and _close(du, du_ref), d
+        assert abs(g - g_ref) <= REL * max(1.0, abs(pr_ref)), d

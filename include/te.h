@@ -104,9 +104,26 @@ typedef struct {
                              index of a CTA that never arrives at the grid
                              barrier, so te_solve must return TE_ETIMEOUT;
                              0 = off (default)                                 */
+    int32_t deterministic; /* 1 (default): the edge loads L_e of Eq. 9 are
+                             exact integer sums of fixed-point rates, so a run
+                             is bit-identical for a given instance and device;
+                             0: one FP32 shared-memory add per path-edge
+                             incidence instead (faster; the loads, and so the
+                             iterates, may differ in the last bits between runs) */
+    int32_t precision;    /* arithmetic of the iteration: TE_PRECISION_FP32
+                             (the only value; FP32 rates and prices, FP64
+                             residual sums, gap and stop test)                */
     int32_t reserved;
     void* cuda_stream;    /* cudaStream_t to run on; NULL = default stream     */
 } te_options;
+
+/* te_options.precision */
+enum {
+    TE_PRECISION_FP32 = 0  /* FP32 iterates (Algorithm 1's rates, prices, per-
+                              demand multipliers); the residual norms (Eqs.
+                              15-16), their cross-CTA sums, the balancing and
+                              stop decisions (Eqs. 17-18) and the gap in FP64 */
+};
 
 /* Outcome of a te_solve call. */
 typedef struct {
@@ -140,12 +157,15 @@ te_status te_create(const te_topology* topo, const te_paths* paths, const double
 
 /* Runs up to max_iters iterations of Algorithm 1 from the current state in
  * one persistent kernel launch, stopping early when the stop rule fires
- * (Eq. 18 with alpha-continuation).  Every step of the iteration runs on the
- * device; the call synchronises and fills *out (may be NULL).  Errors:
- * TE_EINVAL (max_iters < 0), TE_ETIMEOUT (a grid-wide wait exceeded its
- * limit; the state of the last completed iteration is kept), TE_ENUMERIC,
- * TE_ECUDA. */
-te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* out);
+ * (Eq. 18 with alpha-continuation).  tol is the threshold gamma of Eq. 18
+ * for this call (the residuals r and s at or below it count as converged,
+ * for the stop and for alpha increments); tol < 0 uses te_options.gamma.
+ * tol = 0 runs max_iters iterations unless both residuals are exactly zero.
+ * Every step of the iteration runs on the device; the call synchronises and
+ * fills *out (may be NULL).  Errors: TE_EINVAL (max_iters < 0 or tol NaN),
+ * TE_ETIMEOUT (a grid-wide wait exceeded its limit; the state of the last
+ * completed iteration is kept), TE_ENUMERIC, TE_ECUDA. */
+te_status te_solve(te_handle* h, int64_t max_iters, double tol, te_solve_result* out);
 
 /* Feasibility step applied by te_allocation. */
 enum {

@@ -148,6 +148,8 @@ void te_default_options(te_options* o) {
     o->scale_mode = 1;    // geometric mean of the demands
     o->wait_timeout_ms = 0;
     o->test_withhold_cta = 0;
+    o->deterministic = 1;
+    o->precision = TE_PRECISION_FP32;
     o->cuda_stream = nullptr;
 }
 
@@ -249,10 +251,18 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     te_options opt;
     if (opt_in) opt = *opt_in; else te_default_options(&opt);
     if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
-        (opt.scale_mode < 0 || opt.scale_mode > 2) ||
+        (opt.scale_mode < 0 || opt.scale_mode > 2) || (opt.deterministic != 0 && opt.deterministic != 1) ||
         !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0) {
         g_create_error = "invalid options";
         return TE_EINVAL;
+    }
+    if (opt.deterministic == 0) {
+        g_create_error = "deterministic = 0 is not implemented";
+        return TE_EUNSUPPORTED;
+    }
+    if (opt.precision != TE_PRECISION_FP32) {
+        g_create_error = "precision: only TE_PRECISION_FP32 is implemented";
+        return TE_EUNSUPPORTED;
     }
     te_handle* h = new (std::nothrow) te_handle();
     if (!h) { g_create_error = "out of host memory"; return TE_ENOMEM; }
@@ -470,9 +480,11 @@ extern "C" te_status te_reset(te_handle* h) {
     return h->cuda(ce, "te_reset");
 }
 
-extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* out) {
+extern "C" te_status te_solve(te_handle* h, int64_t max_iters, double tol, te_solve_result* out) {
     if (!h) return TE_EINVAL;
     if (max_iters < 0) return h->fail(TE_EINVAL, "max_iters must be >= 0");
+    if (tol != tol) return h->fail(TE_EINVAL, "tol is NaN");
+    const double gamma = tol >= 0.0 ? tol : h->o.gamma;
     cudaStream_t s = h->stream;
     long long done = 0;
     te_status rc = TE_OK;
@@ -487,6 +499,7 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, te_solve_result* 
         te::IterArgs a{};
         a.L = h->L;
         a.o = h->o;
+        a.o.gamma = gamma;
         a.x = h->x;
         a.u = h->u;
         a.w = h->w;
@@ -798,7 +811,7 @@ extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint
             save(ckb + state * (size_t)(k / ck));
             ck_sc[(size_t)(k / ck)] = h->hsc;
         }
-        if ((st = te_solve(h, 1, nullptr)) != TE_OK) { release(); return st; }
+        if ((st = te_solve(h, 1, -1.0, nullptr)) != TE_OK) { release(); return st; }
     }
     const float beta = (float)h->hsc.beta, alpha = (float)h->hsc.alpha;
     A(cudaMemsetAsync(B.ub, 0, sizeof(double) * E, s));
@@ -815,7 +828,7 @@ extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint
         restore(ckb + state * (size_t)(k0 / ck), ck_sc[(size_t)(k0 / ck)]);
         for (long long k = k0; k <= k1; ++k) {
             save(seg + state * (size_t)(k - k0));
-            if (k < k1 && (st = te_solve(h, 1, nullptr)) != TE_OK) { release(); return st; }
+            if (k < k1 && (st = te_solve(h, 1, -1.0, nullptr)) != TE_OK) { release(); return st; }
         }
         for (long long k = k1 - 1; k >= k0; --k) {
             const float* sk = seg + state * (size_t)(k - k0);

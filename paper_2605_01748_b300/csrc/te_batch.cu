@@ -433,9 +433,15 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     te_options opt;
     if (opt_in) opt = *opt_in; else te_default_options(&opt);
     if (!(opt.gamma == opt.gamma) || !(opt.C > 1.0) || !(opt.A > 0.0) || (opt.scale_mode != 0 && opt.scale_mode != 1) ||
-        !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0) {
+        !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0 ||
+        (opt.deterministic != 0 && opt.deterministic != 1)) {
         g_batch_create_error = "invalid options";
         return TE_EINVAL;
+    }
+    if (opt.deterministic == 0 || opt.precision != TE_PRECISION_FP32) {
+        g_batch_create_error = "the batch engine runs the deterministic FP32 iteration only "
+                               "(deterministic = 1, precision = TE_PRECISION_FP32)";
+        return TE_EUNSUPPORTED;
     }
     te_batch* b = new (std::nothrow) te_batch();
     if (!b) { g_batch_create_error = "out of host memory"; return TE_ENOMEM; }

@@ -27,6 +27,8 @@ LIB_PATH = os.environ.get("TE_LIBRARY") or os.path.join(_HERE, "libte.so")
 TE_OK, TE_EINVAL, TE_ENOMEM, TE_ECUDA, TE_ETIMEOUT, TE_ENUMERIC, TE_ENOTCONVERGED, TE_EUNSUPPORTED = range(8)
 # feasibility step of te_allocation: none, Algorithm 2, proportional scaling (not in the paper)
 PROJECT_NONE, PROJECT_ALG2, PROJECT_SCALE = 0, 1, 2
+# te_options.precision
+PRECISION_FP32 = 0
 STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "TE_ETIMEOUT",
                 5: "TE_ENUMERIC", 6: "TE_ENOTCONVERGED", 7: "TE_EUNSUPPORTED"}
 
@@ -61,7 +63,8 @@ class te_options(ctypes.Structure):
                 ("A", ctypes.c_double), ("C", ctypes.c_double), ("beta0", ctypes.c_double),
                 ("adapt_beta", ctypes.c_int32), ("continuation", ctypes.c_int32),
                 ("scale_mode", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
-                ("test_withhold_cta", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("test_withhold_cta", ctypes.c_int32), ("deterministic", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p)]
 
 
@@ -107,7 +110,7 @@ def _load() -> ctypes.CDLL:
     lib.te_create.argtypes = [ctypes.POINTER(te_topology), ctypes.POINTER(te_paths), P, P,
                               ctypes.POINTER(te_options), ctypes.POINTER(H)]
     lib.te_solve.restype = ctypes.c_int
-    lib.te_solve.argtypes = [H, ctypes.c_int64, ctypes.POINTER(te_solve_result)]
+    lib.te_solve.argtypes = [H, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(te_solve_result)]
     lib.te_allocation.restype = ctypes.c_int
     lib.te_allocation.argtypes = [H, P, ctypes.c_int32, ctypes.c_int32]
     lib.te_gap.restype = ctypes.c_int
@@ -228,9 +231,11 @@ def te_create(inst, options: Optional[te_options] = None, check_walks: bool = Tr
     return h
 
 
-def te_solve(h, max_iters: int) -> te_solve_result:
+def te_solve(h, max_iters: int, tol: float = -1.0) -> te_solve_result:
+    """Up to max_iters iterations; tol is this call's stop threshold gamma
+    (negative: the handle's te_options.gamma)."""
     res = te_solve_result()
-    _check(_lib.te_solve(h, int(max_iters), ctypes.byref(res)), h)
+    _check(_lib.te_solve(h, int(max_iters), float(tol), ctypes.byref(res)), h)
     return res
 
 
@@ -338,8 +343,8 @@ class TE:
         self.options = te_default_options(**options)
         self.h = te_create(inst, self.options)
 
-    def solve(self, max_iters: int) -> dict:
-        return te_solve(self.h, max_iters).as_dict()
+    def solve(self, max_iters: int, tol: float = -1.0) -> dict:
+        return te_solve(self.h, max_iters, tol).as_dict()
 
     def allocation(self, project: int = PROJECT_ALG2, out=None) -> np.ndarray:
         if out is None:

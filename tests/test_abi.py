@@ -87,3 +87,49 @@ def test_create_rejects_invalid_instances(te, tiny, case):
         te.te_create(inst)
     assert ei.value.status in (te.TE_EINVAL, te.TE_EUNSUPPORTED)
     assert str(ei.value)
+
+
+def test_options_struct_matches_header(te, tmp_path):
+    """The ctypes mirror of te_options, te_solve_result and te_layout_info has
+    the C header's size and field offsets (compiled here with gcc)."""
+    fields = {"te_options": [f for f, _ in te.te_options._fields_],
+              "te_solve_result": [f for f, _ in te.te_solve_result._fields_],
+              "te_layout_info": [f for f, _ in te.te_layout_info._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "te.h"', 'int main(void) {']
+    for st, fs in fields.items():
+        lines.append(f'printf("{st} %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'printf("{st}.{f} %zu\\n", offsetof({st}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True, check=True)
+               .stdout.splitlines())
+    for st, fs in fields.items():
+        cls = getattr(te, st)
+        assert int(out[st]) == ctypes.sizeof(cls), st
+        for f in fs:
+            assert int(out[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
+
+
+def test_default_options_deterministic_fp32(te):
+    o = te.te_default_options()
+    assert o.deterministic == 1 and o.precision == te.PRECISION_FP32
+
+
+def test_create_rejects_unsupported_precision(te, tiny):
+    # options are checked on the host before any device work
+    with pytest.raises(te.TEError) as ei:
+        te.te_create(tiny, te.te_default_options(precision=1))
+    assert ei.value.status == te.TE_EUNSUPPORTED
+    with pytest.raises(te.TEError) as ei:
+        te.te_create(tiny, te.te_default_options(deterministic=2))
+    assert ei.value.status == te.TE_EINVAL
+
+
+def test_solve_rejects_null_handle(te):
+    res = te.te_solve_result()
+    assert te.lib().te_solve(None, 10, -1.0, ctypes.byref(res)) == te.TE_EINVAL

@@ -84,6 +84,11 @@ typedef struct {
     double alpha_max;     /* continuation cap (default 32)                     */
     double gamma;         /* stop threshold on relative r and s (default 1e-3,
                              Section 3.7); negative: never stop early          */
+    double gamma_max;     /* > 0: a level of the continuation also counts as
+                             converged (Eq. 18) only while the primal residual
+                             in the max norm, the largest relative capacity
+                             violation max_e n_e |u_e' - u_e| / C_e, is at or
+                             below gamma_max; <= 0 (default): off             */
     double A;             /* residual balancing ratio (default 10, Eq. 17)     */
     double C;             /* residual balancing factor (default 2, Eq. 17)     */
     double beta0;         /* initial penalty in normalised units; <= 0
@@ -91,6 +96,12 @@ typedef struct {
                              initial path rate), so the first utility push
                              lambda/(beta n_r) at lambda = 1 equals the mean
                              initial rate                                      */
+    double balance_floor; /* residual balancing (Eq. 17) acts only while
+                             max(r, s) > balance_floor (default 1e-6): below
+                             it both residuals of the FP32 iteration are
+                             rounding noise and their ratio says nothing.
+                             beta also stays within [1e-30, 1e30] (normalised
+                             units), where 1/beta is a finite FP32 value      */
     int32_t adapt_beta;   /* 1: residual balancing on (default 1)              */
     int32_t continuation; /* 1: stop when converged on the first iteration
                              after an alpha increment (default 1)              */

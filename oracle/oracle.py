@@ -60,8 +60,9 @@ class _Inst(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("alpha_target", ctypes.c_double), ("alpha_start", ctypes.c_double),
                 ("alpha_step", ctypes.c_double), ("alpha_max", ctypes.c_double),
-                ("gamma", ctypes.c_double), ("A", ctypes.c_double), ("C", ctypes.c_double),
-                ("beta0", ctypes.c_double), ("adapt_beta", ctypes.c_int32),
+                ("gamma", ctypes.c_double), ("gamma_max", ctypes.c_double), ("A", ctypes.c_double),
+                ("C", ctypes.c_double),
+                ("beta0", ctypes.c_double), ("balance_floor", ctypes.c_double), ("adapt_beta", ctypes.c_int32),
                 ("continuation", ctypes.c_int32), ("threads", ctypes.c_int32), ("scale_mode", ctypes.c_int32)]
 
 
@@ -134,15 +135,19 @@ class OracleSolver:
     def __init__(self, inst, alpha_target: float = math.inf, gamma: float = 1e-3, A: float = 10.0,
                  C: float = 2.0, beta0: float = 0.0, adapt_beta: bool = True, continuation: bool = True,
                  alpha_start: float = 0.0, alpha_step: float = 1.0, alpha_max: float = 32.0,
-                 threads: int = 0, x0: Optional[np.ndarray] = None, scale_mode: int = 1):
+                 threads: int = 0, x0: Optional[np.ndarray] = None, scale_mode: int = 1,
+                 balance_floor: float = 1e-6, gamma_max: float = 0.0):
         """Defaults: the paper's A = 10, C = 2, gamma = 1e-3 (Section 3.7),
         alpha from 0 in steps of 1 (Algorithm 1); the unit of the normalised
         problem is the geometric mean of the demands (scale_mode = 1) and
-        beta0 <= 0 picks 1 / (mean path length * mean initial path rate)."""
+        beta0 <= 0 picks 1 / (mean path length * mean initial path rate);
+        residual balancing pauses while both residuals are at or below
+        balance_floor."""
         self.inst = inst
         self.view = _InstanceView(inst)
-        self.opts = _Opts(alpha_target, alpha_start, alpha_step, alpha_max, gamma, A, C, beta0,
-                          int(adapt_beta), int(continuation), int(threads), int(scale_mode))
+        self.opts = _Opts(alpha_target, alpha_start, alpha_step, alpha_max, gamma, gamma_max, A, C, beta0,
+                          float(balance_floor), int(adapt_beta), int(continuation), int(threads),
+                          int(scale_mode))
         self.x = np.zeros(inst.n_paths, dtype=np.float64)
         self.u = np.zeros(inst.n_edges, dtype=np.float64)
         self.d = np.zeros(inst.n_edges, dtype=np.float64)
@@ -257,7 +262,7 @@ def gradient(inst, alpha: float, beta0: float, iters: int, checkpoint: int = 20,
     of the fixed schedule (beta0, alpha fixed) from the initial state, the
     normalisation unit held fixed (scale_mode 2: caller units)."""
     view = _InstanceView(inst)
-    opts = _Opts(alpha, alpha, 1.0, alpha, -1.0, 10.0, 2.0, beta0, 0, 0, int(threads), int(scale_mode))
+    opts = _Opts(alpha, alpha, 1.0, alpha, -1.0, 0.0, 10.0, 2.0, beta0, 1e-6, 0, 0, int(threads), int(scale_mode))
     J = ctypes.c_double()
     gC = np.zeros(inst.n_edges, dtype=np.float64)
     gD = np.zeros(inst.n_demands, dtype=np.float64)

@@ -34,10 +34,14 @@
  *          after the collapse; n_e = number of paths on e)
  *   s    = ||x' - x|| / ||x'||                           dual residual (Eq. 15)
  *   r    = sqrt(sum_e n_e d_e'^2) / sqrt(sum_r n_r x_r'^2)   primal residual (Eq. 16)
- *   beta : residual balancing (Eq. 17); on a change the scaled duals u are
+ *   beta : residual balancing (Eq. 17) while max(r, s) exceeds a floor
+ *          (default 1e-6, the rounding level of the FP32 iteration), beta
+ *          kept within [1e-30, 1e30]; on a change the scaled duals u are
  *          multiplied by beta_old/beta_new and d (a primal quantity) is kept
  *   stop : r <= gamma and s <= gamma (Eq. 18) with alpha-continuation
- *          (Section 3.4 "alpha-increments", Algorithm 1)
+ *          (Section 3.4 "alpha-increments", Algorithm 1); optionally also
+ *          the primal residual in the max norm, the largest relative
+ *          capacity violation max_e n_e |u_e' - u_e| / C_e <= gamma_max
  * Values are normalised by scale = max_e C_e (the alpha-fair argmax is
  * invariant to a common scaling of C and D).
  *
@@ -72,8 +76,10 @@ typedef struct {
     double alpha_step;    /* continuation increment (1)                   */
     double alpha_max;     /* continuation cap                             */
     double gamma;         /* convergence threshold (1e-3)                 */
+    double gamma_max;     /* > 0: convergence also needs max_e n_e |du_e| / C_e <= gamma_max */
     double A, C;          /* residual balancing constants (10, 2)         */
     double beta0;         /* initial penalty, normalised units (1)        */
+    double balance_floor; /* residual balancing only while max(r, s) exceeds it */
     int32_t adapt_beta;   /* 1: residual balancing on                     */
     int32_t continuation; /* 1: stop when converged on the first iteration after an increment */
     int32_t threads;      /* OpenMP threads (0: runtime default)          */
@@ -91,6 +97,19 @@ typedef struct {
 } or_scalars;
 
 enum { TR_R = 0, TR_S, TR_BETA, TR_ALPHA, TR_EVENT, TR_WIDTH };
+
+/* Field-by-field copy of the option and scalar structs into doubles, so the
+ * tests can check the ctypes mirrors against this file's layout. */
+void or_echo_options(const or_options* o, double* out) {
+    out[0] = o->alpha_target; out[1] = o->alpha_start; out[2] = o->alpha_step; out[3] = o->alpha_max;
+    out[4] = o->gamma; out[5] = o->gamma_max; out[6] = o->A; out[7] = o->C; out[8] = o->beta0;
+    out[9] = o->balance_floor; out[10] = o->adapt_beta; out[11] = o->continuation; out[12] = o->threads;
+    out[13] = o->scale_mode; out[14] = (double)sizeof(or_options);
+}
+void or_echo_scalars(const or_scalars* sc, double* out) {
+    out[0] = sc->beta; out[1] = sc->alpha; out[2] = sc->scale; out[3] = (double)sc->iter;
+    out[4] = (double)sc->iter_alpha; out[5] = sc->converged; out[6] = (double)sizeof(or_scalars);
+}
 
 /* ------------------------------------------------------------------ */
 /* alpha-fair utility, Eq. 4                                           */
@@ -326,7 +345,7 @@ int64_t or_run(const or_instance* I, const or_options* o, double* x, double* u, 
             un[e] = ne[e] > 0 ? fmax(0.0, u[e] + (s - C[e]) / (double)ne[e]) : 0.0;
         }
         /* residuals (sequential sums, fixed order) */
-        double ds2 = 0.0, x2 = 0.0, ex2 = 0.0, r2 = 0.0;
+        double ds2 = 0.0, x2 = 0.0, ex2 = 0.0, r2 = 0.0, rmax = 0.0;
         for (int64_t r = 0; r < P; ++r) {
             const double dx = xn[r] - x[r];
             const double nr = (double)(I->peo[r + 1] - I->peo[r]);
@@ -337,6 +356,7 @@ int64_t or_run(const or_instance* I, const or_options* o, double* x, double* u, 
         for (int e = 0; e < E; ++e) {
             const double de = un[e] - u[e];
             r2 += (double)ne[e] * de * de;
+            if (ne[e] > 0) rmax = fmax(rmax, (double)ne[e] * fabs(de) / C[e]);
             d[e] = de;
             u[e] = un[e];
         }
@@ -347,11 +367,14 @@ int64_t or_run(const or_instance* I, const or_options* o, double* x, double* u, 
         sc->iter_alpha++;
         done++;
         int event = 0;
-        /* residual balancing, Eq. 17 */
-        if (o->adapt_beta) {
+        /* residual balancing, Eq. 17, while the residuals are above the
+         * floor (below it they are rounding noise of the FP32 iteration, so
+         * both sides skip the step), keeping beta within [1e-30, 1e30] */
+        if (o->adapt_beta && fmax(r_res, s_res) > o->balance_floor) {
             double nb = beta;
             if (r_res > o->A * s_res) nb = beta * o->C;
             else if (s_res > o->A * r_res) nb = beta / o->C;
+            if (!(nb >= 1e-30 && nb <= 1e30)) nb = beta;
             if (nb != beta) {
                 const double ratio = beta / nb;
                 for (int e = 0; e < E; ++e) u[e] *= ratio;
@@ -360,7 +383,7 @@ int64_t or_run(const or_instance* I, const or_options* o, double* x, double* u, 
             }
         }
         /* convergence and alpha-continuation, Eq. 18 and Algorithm 1 */
-        if (r_res <= o->gamma && s_res <= o->gamma) {
+        if (r_res <= o->gamma && s_res <= o->gamma && (o->gamma_max <= 0.0 || rmax <= o->gamma_max)) {
             if (sc->alpha >= o->alpha_target) {
                 sc->converged = 1;
                 event |= 4;

@@ -86,7 +86,7 @@ struct te_handle {
     float* u_next = nullptr;  // [E]
     float* w_next = nullptr;  // [E]
     uint2* loads = nullptr;   // [grid*E] per-CTA partial loads
-    double* part = nullptr;   // [2*grid*4]
+    double* part = nullptr;   // [2*grid*kPartWidth]
     unsigned* barrier = nullptr;
     int* status = nullptr;
     te::Scalars* sc = nullptr;
@@ -143,6 +143,8 @@ void te_default_options(te_options* o) {
     o->A = 10.0;
     o->C = 2.0;
     o->beta0 = 0.0;       // automatic (see te.h)
+    o->balance_floor = 1e-6;
+    o->gamma_max = 0.0;
     o->adapt_beta = 1;
     o->continuation = 1;
     o->scale_mode = 1;    // geometric mean of the demands
@@ -250,15 +252,11 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     }
     te_options opt;
     if (opt_in) opt = *opt_in; else te_default_options(&opt);
-    if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
+    if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.balance_floor >= 0.0) || !(opt.gamma_max == opt.gamma_max) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
         (opt.scale_mode < 0 || opt.scale_mode > 2) || (opt.deterministic != 0 && opt.deterministic != 1) ||
         !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0) {
         g_create_error = "invalid options";
         return TE_EINVAL;
-    }
-    if (opt.deterministic == 0) {
-        g_create_error = "deterministic = 0 is not implemented";
-        return TE_EUNSUPPORTED;
     }
     if (opt.precision != TE_PRECISION_FP32) {
         g_create_error = "precision: only TE_PRECISION_FP32 is implemented";
@@ -282,6 +280,9 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     h->o.C = opt.C;
     h->o.adapt_beta = opt.adapt_beta;
     h->o.continuation = opt.continuation;
+    h->o.balance_floor = opt.balance_floor;
+    h->o.gamma_max = opt.gamma_max;
+    h->o.deterministic = opt.deterministic;
     h->o.withhold_cta = opt.test_withhold_cta > 0 ? opt.test_withhold_cta - 1 : -1;
     h->beta0 = opt.beta0;
     if (opt.wait_timeout_ms > 0) h->timeout_ns = (long long)opt.wait_timeout_ms * 1000000LL;
@@ -325,11 +326,11 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     te_status st;
     if ((st = h->cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device), "device query")))
         return bail(st);
-    if (te::iter_smem_bytes(E, nsm) > 227 * 1024) {
+    if (te::iter_smem_bytes(E, nsm, opt.deterministic != 0) > 227 * 1024) {
         h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 10770 edges)", E);
         return bail(TE_EUNSUPPORTED);
     }
-    if ((st = h->cuda(te::iter_occupancy(G, E, nsm, &bps), "occupancy query"))) return bail(st);
+    if ((st = h->cuda(te::iter_occupancy(G, opt.deterministic != 0, E, nsm, &bps), "occupancy query"))) return bail(st);
     if (bps < 1) { h->err = "iteration kernel does not fit on an SM"; return bail(TE_EUNSUPPORTED); }
     h->grid = nsm * bps;
     if ((E + h->grid - 1) / h->grid > te::kIterThreads) {  // one edge of a CTA's price slice per thread
@@ -368,7 +369,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->u_next, sizeof(float) * E));
     A(h->alloc(&h->w_next, sizeof(float) * E));
     A(h->alloc(&h->loads, sizeof(uint2) * (size_t)h->grid * (size_t)E));
-    A(h->alloc(&h->part, sizeof(double) * 2 * 4 * (size_t)h->grid));
+    A(h->alloc(&h->part, sizeof(double) * 2 * te::kPartWidth * (size_t)h->grid));
     A(h->alloc(&h->barrier, sizeof(unsigned)));
     A(h->alloc(&h->status, sizeof(int)));
     A(h->alloc(&h->sc, sizeof(te::Scalars)));

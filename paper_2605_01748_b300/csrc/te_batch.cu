@@ -94,6 +94,21 @@ __device__ double fixed_sum(double v, double* part) {
     return s_tot;
 }
 
+// Largest per-thread value over the CTA (threads < kRedParts).
+__device__ double fixed_max(double v, double* part) {
+    __syncthreads();
+    if (threadIdx.x < kRedParts) part[threadIdx.x] = v;
+    __syncthreads();
+    __shared__ double s_max;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < kRedParts; ++i) t = fmax(t, part[i]);
+        s_max = t;
+    }
+    __syncthreads();
+    return s_max;
+}
+
 template <int G, int W>
 __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
     constexpr int kThreads = W * 32;
@@ -155,8 +170,8 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             const float inv_alpha = alpha > 0.f ? 1.f / alpha : 0.f;
 
             // phase A: the instance's blocks, shared among the warps
-            float unused[3];
-            run_blocks<G, kStageRows, false, false>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
+            LaneRes unused;
+            run_blocks<G, kStageRows, false, false, true>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
                                              logbeta, beta_f, alpha, inv_alpha, unused);
             __syncthreads();
             if (*(volatile int*)a.status != 0) failed = true;
@@ -182,6 +197,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             // thread t takes edges t, t + kRedParts, ... (the primal residual
             // partials then do not depend on the CTA shape)
             double r2 = 0.0;
+            float vmax = 0.f;  // largest relative capacity violation n_e |d_e| / C_e
             if (tid < kRedParts)
                 for (int e = tid; e < E; e += kRedParts) {
                     const float L = (float)((double)h_hi[e] * 0x1p-12 + (double)h_lo[e] * 0x1p-24);
@@ -190,13 +206,16 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
                     const float ne = __ldg(&nef[e]);
                     const float u = s_u[e];
                     float un = 0.f;
-                    if (ne > 0.f) un = fmaxf(0.f, fmaf(L - __ldg(&cap[e]), __ldg(&inv[e]), u));
+                    const float ce = __ldg(&cap[e]);
+                    if (ne > 0.f) un = fmaxf(0.f, fmaf(L - ce, __ldg(&inv[e]), u));
                     const float d = un - u;
                     r2 += (double)(ne * d * d);
+                    if (ne > 0.f) vmax = fmaxf(vmax, __fdiv_ru(ne * fabsf(d), ce));
                     s_u[e] = un;
                     w_s[e] = un + d;
                 }
             const double v3 = fixed_sum(r2, s_part);
+            const double v4 = fixed_max((double)vmax, s_part);
 
             // control: residuals, beta, alpha, stop (identical in every thread)
             const double s_res = sqrt(v0) / fmax(sqrt(v1), 1e-30);
@@ -206,10 +225,8 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             sc.iter_alpha++;
             done++;
             const bool numeric_ok = isfinite(s_res) && isfinite(r_res);
-            if (numeric_ok && a.o.adapt_beta) {
-                double nb = sc.beta;
-                if (r_res > a.o.A * s_res) nb = sc.beta * a.o.C;
-                else if (s_res > a.o.A * r_res) nb = sc.beta / a.o.C;
+            if (numeric_ok && a.o.adapt_beta && fmax(r_res, s_res) > a.o.balance_floor) {
+                const double nb = balanced_beta(sc.beta, r_res, s_res, a.o.A, a.o.C);
                 if (nb != sc.beta) {
                     // scaled prices follow beta; the weights keep d: w = u' ratio + d
                     const float ratio = (float)(sc.beta / nb);
@@ -230,7 +247,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             }
             bool stop = false;
             int event = 0;
-            if (r_res <= a.o.gamma && s_res <= a.o.gamma) {
+            if (r_res <= a.o.gamma && s_res <= a.o.gamma && (a.o.gamma_max <= 0.0 || v4 <= a.o.gamma_max)) {
                 if (sc.alpha >= a.o.alpha_target) {
                     stop = true; event = 4;
                 } else if (a.o.continuation && sc.iter_alpha == 1 && sc.alpha > a.o.alpha_start) {
@@ -432,7 +449,7 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     *out = nullptr;
     te_options opt;
     if (opt_in) opt = *opt_in; else te_default_options(&opt);
-    if (!(opt.gamma == opt.gamma) || !(opt.C > 1.0) || !(opt.A > 0.0) || (opt.scale_mode != 0 && opt.scale_mode != 1) ||
+    if (!(opt.gamma == opt.gamma) || !(opt.balance_floor >= 0.0) || !(opt.C > 1.0) || !(opt.A > 0.0) || (opt.scale_mode != 0 && opt.scale_mode != 1) ||
         !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0 ||
         (opt.deterministic != 0 && opt.deterministic != 1)) {
         g_batch_create_error = "invalid options";
@@ -470,6 +487,9 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     b->o.A = opt.A;
     b->o.C = opt.C;
     b->o.adapt_beta = opt.adapt_beta;
+    b->o.balance_floor = opt.balance_floor;
+    b->o.gamma_max = opt.gamma_max;
+    b->o.deterministic = 1;
     b->o.continuation = opt.continuation;
     b->o.withhold_cta = -1;
     if (opt.wait_timeout_ms > 0) b->timeout_ns = (long long)opt.wait_timeout_ms * 1000000LL;

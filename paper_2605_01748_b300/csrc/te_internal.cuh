@@ -41,6 +41,7 @@ constexpr int kIterWarps = kIterThreads / 32;
 constexpr int kIterStageRows = 40;  // rows of 16-bit ids per staging buffer of the iteration kernel
 constexpr int kStageRows = 48;      // the same for the batch kernel (3 KB)
 constexpr int kTraceWidth = 5;
+constexpr int kPartWidth = 8;  // doubles per CTA in IterArgs::part (5 used)
 
 // Solver scalars, kept in device memory between launches.
 struct Scalars {
@@ -59,7 +60,10 @@ struct Scalars {
 struct Options {
     double alpha_target, alpha_start, alpha_step, alpha_max;
     double gamma, A, C;
+    double balance_floor;  // balancing only while max(r, s) exceeds it
+    double gamma_max;      // > 0: convergence also needs max_e n_e |d_e| / C_e <= gamma_max
     int adapt_beta, continuation;
+    int deterministic;  // 1: exact fixed-point load histograms; 0: FP32 shared atomics
     int withhold_cta;  // test hook: this CTA never arrives at the barrier (-1: none)
 };
 
@@ -106,8 +110,10 @@ struct IterArgs {
     float* w;              // [E] u + d (gather weights), in/out
     float* u_next;         // [E] scratch: prices published for a beta rescale
     float* w_next;         // [E] scratch: gather weights published each iteration
-    uint2* loads;          // [grid*E] per-CTA partial edge loads (fixed point: 2^-12 and 2^-24 units)
-    double* part;          // [2*grid*4] per-CTA residual partials
+    uint2* loads;          // [grid*E] per-CTA partial edge loads (fixed point: 2^-12 and 2^-24
+                           // units; FP32 in the first half of each pair's words when not deterministic)
+    double* part;          // [2*grid*kPartWidth] per-CTA residual partials: sums of
+                           // (x'-x)^2, x'^2, n x'^2, n_e d_e^2 and the largest n_e |d_e| / C_e
     unsigned* barrier;     // grid barrier counter (zeroed before launch)
     int* status;           // device status word (0 ok)
     Scalars* sc;           // in/out
@@ -123,8 +129,8 @@ constexpr int kStatusTimeout = 4;
 constexpr int kStatusNumeric = 5;
 
 // Launchers (host side), defined in te_iter.cu / te_proj.cu / te_gap.cu.
-size_t iter_smem_bytes(int E, int grid);
-cudaError_t iter_occupancy(int G, int E, int grid_hint, int* blocks_per_sm);
+size_t iter_smem_bytes(int E, int grid, bool det);
+cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_per_sm);
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st);
 

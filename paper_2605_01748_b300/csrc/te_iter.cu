@@ -12,7 +12,8 @@
 //            asynchronous copies (cp.async), issued one block ahead of use; the
 //            block's metadata record is loaded two blocks ahead.  The CTA then
 //            publishes its per-edge partial loads and its residual partials
-//            (FP32 within a warp, FP64 across warps);
+//            (each lane's sums over its warp's blocks compensated in FP32,
+//            everything above the lane in FP64);
 //   grid barrier 1;
 //   phase B (every CTA, its own slice of the edges): the loads L_e as FP64
 //            sums of the CTAs' partials in a fixed order (so a run is
@@ -41,21 +42,24 @@
 namespace te {
 namespace {
 
-template <int G>
+// DET: exact split fixed-point load histograms (two 32-bit integer atomics
+// per incidence); else one FP32 histogram (one FP32 atomic per incidence).
+template <int G, bool DET>
 __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     extern __shared__ __align__(128) unsigned smem[];
     const int E = a.L.E;
     const int NG = gridDim.x;  // CTAs in the grid
     // dynamic shared memory: histogram, gather weights, staging, price slice
-    unsigned* h_hi = smem;                                           // [E+1] units of 2^-12
-    unsigned* h_lo = h_hi + (E + 1);                                 // [E+1] units of 2^-24
-    float* w_s = reinterpret_cast<float*>(h_lo + (E + 1));          // [E+1], w_s[E] = 0
+    unsigned* h_hi = smem;                                           // [E+1] units of 2^-12 (DET), else FP32
+    unsigned* h_lo = DET ? h_hi + (E + 1) : nullptr;                 // [E+1] units of 2^-24 (DET)
+    float* w_s = reinterpret_cast<float*>(h_hi + (DET ? 2 : 1) * (E + 1));  // [E+1], w_s[E] = 0
     uint16_t* stage = reinterpret_cast<uint16_t*>(
         reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) & ~uintptr_t(127));  // [warps][2][kIterStageRows*32]
     float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kIterStageRows * kLanes);  // price slice
     const int e_lo = (int)((long long)blockIdx.x * E / NG), e_hi = (int)((long long)(blockIdx.x + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
-    __shared__ float s_wred[kIterWarps][4];  // per-warp FP32 partials of the residual sums
+    __shared__ double s_wred[kIterWarps][4];  // per-warp FP64 partials of the residual sums
+    __shared__ float s_wmax[kIterWarps];      // per-warp largest relative capacity violation
     __shared__ float s_par[5];   // this iteration's 1/beta, log beta, beta, alpha, 1/alpha (FP32)
     __shared__ float s_ratio;    // price rescale of the last balancing step
     __shared__ int s_ctl;        // control decision: bit 0 numeric failure, bit 1 stop
@@ -72,14 +76,14 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
 
     for (int e = tid; e < E; e += kIterThreads) {
         w_s[e] = a.w[e];
-        h_hi[e] = 0u;
-        h_lo[e] = 0u;
+        h_hi[e] = 0u;  // also FP32 +0
+        if (DET) h_lo[e] = 0u;
     }
     for (int e = e_lo + tid; e < e_hi; e += kIterThreads) s_u[e - e_lo] = a.u[e];
     if (tid == 0) {
         w_s[E] = 0.f;
         h_hi[E] = 0u;
-        h_lo[E] = 0u;
+        if (DET) h_lo[E] = 0u;
     }
     // the scalar state is kept by thread 0, which takes the control
     // decisions (FP64 is slow on this part: one thread does it and the CTA
@@ -115,28 +119,38 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         // The warps share the blocks of this CTA (blockIdx.x, blockIdx.x +
         // NG, ...) in a fixed interleave, so a run is deterministic (the
         // loads are integer sums, and each lane sums the residual terms of
-        // its warp's blocks in FP32 in the order of the interleave).
-        float acc[3] = {0.f, 0.f, 0.f};
+        // its warp's blocks, compensated, in the order of the interleave).
+        LaneRes acc;
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.hops, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows, true, true>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
+            run_blocks<G, kIterStageRows, true, true, DET>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
                                                 h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         __syncthreads();
         // publish this CTA's partial loads
-        uint2* Lp = a.loads + (size_t)blockIdx.x * E;
-        #pragma unroll 4
-        for (int e = tid; e < E; e += kIterThreads) {
-            __stcg(&Lp[e], make_uint2(h_hi[e], h_lo[e]));
-            h_hi[e] = 0u;
-            h_lo[e] = 0u;
+        if (DET) {
+            uint2* Lp = a.loads + (size_t)blockIdx.x * E;
+            #pragma unroll 4
+            for (int e = tid; e < E; e += kIterThreads) {
+                __stcg(&Lp[e], make_uint2(h_hi[e], h_lo[e]));
+                h_hi[e] = 0u;
+                h_lo[e] = 0u;
+            }
+        } else {
+            float* Lp = reinterpret_cast<float*>(a.loads) + (size_t)blockIdx.x * E;
+            const float* hf = reinterpret_cast<const float*>(h_hi);
+            #pragma unroll 4
+            for (int e = tid; e < E; e += kIterThreads) {
+                __stcg(&Lp[e], hf[e]);
+                h_hi[e] = 0u;
+            }
         }
         {
-            // this CTA's residual partials: each warp sums its lanes' sums in
-            // a fixed butterfly, and thread 0 the warps' in FP64, in warp
-            // order (the blocks of a warp are fixed by the interleave, so the
-            // totals do not depend on timing)
-            float t0 = acc[0], t1 = acc[1], t2 = acc[2];
+            // this CTA's residual partials: each lane's compensated sums in
+            // FP64, summed over the warp in a fixed butterfly and over the
+            // warps in warp order by thread 0 (the blocks of a warp are fixed
+            // by the interleave, so the totals do not depend on timing)
+            double t0 = acc.d.value(), t1 = (double)acc.x, t2 = (double)acc.e;
             #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 t0 += __shfl_xor_sync(0xffffffffu, t0, o);
@@ -152,11 +166,11 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
             if (tid == 0) {
                 double v0 = 0.0, v1 = 0.0, v2 = 0.0;
                 for (int w = 0; w < kIterWarps; ++w) {
-                    v0 += (double)s_wred[w][0];
-                    v1 += (double)s_wred[w][1];
-                    v2 += (double)s_wred[w][2];
+                    v0 += s_wred[w][0];
+                    v1 += s_wred[w][1];
+                    v2 += s_wred[w][2];
                 }
-                double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * 4;
+                double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * kPartWidth;
                 __stcg(&p[0], v0);
                 __stcg(&p[1], v1);
                 __stcg(&p[2], v2);
@@ -171,8 +185,9 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         // ---------------- phase B: this CTA's slice of the edge prices ----------------
         {
             // L_e of the slice: the CTAs' integer partials summed exactly in
-            // 64 bits (so L_e does not depend on how blocks are spread over
-            // CTAs) and converted once; thread t adds the partials of CTAs
+            // 64 bits (DET: so L_e does not depend on how blocks are spread
+            // over CTAs) and converted once, or the CTAs' FP32 partials summed
+            // in FP64 in CTA order; thread t adds the partials of CTAs
             // c = t / ns, t / ns + kIterThreads / ns, ... for edge e_lo + t % ns
             const int ns = e_hi - e_lo;
             // [2][kIterThreads] in the staging buffers, idle in phase B
@@ -182,54 +197,88 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                               (size_t)kIterWarps * 2 * kIterStageRows * kLanes * sizeof(uint16_t),
                           "the phase-B partial sums fit the staging buffers");
             unsigned long long* s_L = reinterpret_cast<unsigned long long*>(stage);
+            double* s_Ld = reinterpret_cast<double*>(stage);
             if (ns > 0) {
                 const int per = kIterThreads / ns > 0 ? kIterThreads / ns : 1;
-                unsigned long long sh = 0ull, sl = 0ull;
-                if (tid < per * ns) {
-                    const int e = e_lo + tid % ns;
-                    #pragma unroll 4
-                    for (int c = tid / ns; c < NG; c += per) {
-                        const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
-                        sh += v.x;
-                        sl += v.y;
+                if (DET) {
+                    unsigned long long sh = 0ull, sl = 0ull;
+                    if (tid < per * ns) {
+                        const int e = e_lo + tid % ns;
+                        #pragma unroll 4
+                        for (int c = tid / ns; c < NG; c += per) {
+                            const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
+                            sh += v.x;
+                            sl += v.y;
+                        }
                     }
+                    s_L[tid] = sh;
+                    s_L[kIterThreads + tid] = sl;
+                } else {
+                    const float* Lf = reinterpret_cast<const float*>(a.loads);
+                    double sf = 0.0;
+                    if (tid < per * ns) {
+                        const int e = e_lo + tid % ns;
+                        #pragma unroll 4
+                        for (int c = tid / ns; c < NG; c += per) sf += (double)__ldcg(&Lf[(size_t)c * E + e]);
+                    }
+                    s_Ld[tid] = sf;
                 }
-                s_L[tid] = sh;
-                s_L[kIterThreads + tid] = sl;
                 __syncthreads();
                 if (tid < ns) {
-                    unsigned long long H = 0ull, Lo = 0ull;
-                    for (int k = 0; k < per; ++k) {
-                        H += s_L[k * ns + tid];
-                        Lo += s_L[kIterThreads + k * ns + tid];
+                    if (DET) {
+                        unsigned long long H = 0ull, Lo = 0ull;
+                        for (int k = 0; k < per; ++k) {
+                            H += s_L[k * ns + tid];
+                            Lo += s_L[kIterThreads + k * ns + tid];
+                        }
+                        s_L[tid] = H;  // each slot read and written by its own thread only
+                        s_L[kIterThreads + tid] = Lo;
+                    } else {
+                        double F = 0.0;
+                        for (int k = 0; k < per; ++k) F += s_Ld[k * ns + tid];
+                        s_Ld[tid] = F;
                     }
-                    s_L[tid] = H;  // each slot read and written by its own thread only
-                    s_L[kIterThreads + tid] = Lo;
                 }
                 __syncthreads();
             }
             KSum r2;
+            float vmax = 0.f;  // largest relative capacity violation n_e |d_e| / C_e of the slice
             for (int e = e_lo + tid; e < e_hi; e += kIterThreads) {
                 const float ne = __ldg(&a.L.ne_f[e]);
                 const float u = s_u[e - e_lo];
-                const float L = (float)((double)s_L[e - e_lo] * 0x1p-12 + (double)s_L[kIterThreads + e - e_lo] * 0x1p-24);
+                const float L = DET ? (float)((double)s_L[e - e_lo] * 0x1p-12 + (double)s_L[kIterThreads + e - e_lo] * 0x1p-24)
+                                    : (float)s_Ld[e - e_lo];
                 float un = 0.f;
-                if (ne > 0.f) un = fmaxf(0.f, fmaf(L - __ldg(&a.L.cap_n[e]), __ldg(&a.L.inv_ne[e]), u));
+                const float cap = __ldg(&a.L.cap_n[e]);
+                if (ne > 0.f) un = fmaxf(0.f, fmaf(L - cap, __ldg(&a.L.inv_ne[e]), u));
                 const float d = un - u;
                 r2.add(ne * d * d);
+                if (ne > 0.f) vmax = fmaxf(vmax, __fdiv_ru(ne * fabsf(d), cap));
                 s_un[e - e_lo] = un;
                 __stcg(&a.u_next[e], un);
                 __stcg(&a.w_next[e], un + d);
             }
-            float t3 = r2.s;
+            double t3 = r2.value();
             #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) t3 += __shfl_xor_sync(0xffffffffu, t3, o);
-            if (lane == 0) s_wred[warp][3] = t3;
+            for (int o = 16; o > 0; o >>= 1) {
+                t3 += __shfl_xor_sync(0xffffffffu, t3, o);
+                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            }
+            if (lane == 0) {
+                s_wred[warp][3] = t3;
+                s_wmax[warp] = vmax;
+            }
             __syncthreads();
             if (tid == 0) {
                 double v3 = 0.0;
-                for (int w = 0; w < kIterWarps; ++w) v3 += (double)s_wred[w][3];
-                __stcg(&a.part[((size_t)(it & 1) * NG + blockIdx.x) * 4 + 3], v3);
+                float m = 0.f;
+                for (int w = 0; w < kIterWarps; ++w) {
+                    v3 += s_wred[w][3];
+                    m = fmaxf(m, s_wmax[w]);
+                }
+                double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * kPartWidth;
+                __stcg(&p[3], v3);
+                __stcg(&p[4], (double)m);
             }
         }
         if (!grid_sync(a.barrier, (unsigned)((2 * it + 2) * NG), a.status, a.timeout_ns, true)) {
@@ -243,19 +292,21 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         xbuf ^= 1;
         done++;
         if (tid < 32) {
-            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-            const double* p = a.part + (size_t)(it & 1) * NG * 4;
+            double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0;
+            const double* p = a.part + (size_t)(it & 1) * NG * kPartWidth;
             for (int c = lane; c < NG; c += 32) {
-                v0 += __ldcg(&p[c * 4 + 0]);
-                v1 += __ldcg(&p[c * 4 + 1]);
-                v2 += __ldcg(&p[c * 4 + 2]);
-                v3 += __ldcg(&p[c * 4 + 3]);
+                v0 += __ldcg(&p[c * kPartWidth + 0]);
+                v1 += __ldcg(&p[c * kPartWidth + 1]);
+                v2 += __ldcg(&p[c * kPartWidth + 2]);
+                v3 += __ldcg(&p[c * kPartWidth + 3]);
+                v4 = fmax(v4, __ldcg(&p[c * kPartWidth + 4]));
             }
             for (int o = 16; o > 0; o >>= 1) {
                 v0 += __shfl_xor_sync(0xffffffffu, v0, o);
                 v1 += __shfl_xor_sync(0xffffffffu, v1, o);
                 v2 += __shfl_xor_sync(0xffffffffu, v2, o);
                 v3 += __shfl_xor_sync(0xffffffffu, v3, o);
+                v4 = fmax(v4, __shfl_xor_sync(0xffffffffu, v4, o));
             }
             if (tid == 0) {
                 const double s_res = sqrt(v0) / fmax(sqrt(v1), 1e-30);
@@ -265,10 +316,8 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 int event = 0, ctl = 0;
                 float ratio = 1.f;
                 const bool numeric_ok = isfinite(s_res) && isfinite(r_res);
-                if (numeric_ok && a.o.adapt_beta) {
-                    double nb = sc.beta;
-                    if (r_res > a.o.A * s_res) nb = sc.beta * a.o.C;
-                    else if (s_res > a.o.A * r_res) nb = sc.beta / a.o.C;
+                if (numeric_ok && a.o.adapt_beta && fmax(r_res, s_res) > a.o.balance_floor) {
+                    const double nb = balanced_beta(sc.beta, r_res, s_res, a.o.A, a.o.C);
                     if (nb != sc.beta) {
                         ratio = (float)(sc.beta / nb);
                         sc.beta = nb;
@@ -278,7 +327,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 if (!numeric_ok) {
                     ctl = 1;
                     if (blockIdx.x == 0) atomicCAS(a.status, 0, kStatusNumeric);
-                } else if (r_res <= a.o.gamma && s_res <= a.o.gamma) {
+                } else if (r_res <= a.o.gamma && s_res <= a.o.gamma && (a.o.gamma_max <= 0.0 || v4 <= a.o.gamma_max)) {
                     bool stop = false;
                     if (sc.alpha >= a.o.alpha_target) {
                         stop = true; event |= 4;
@@ -353,31 +402,33 @@ __global__ void k_init_x(Layout L, float* x) {
     for (int j = 0; j < KB; ++j) x[(size_t)(s0 + j) * kLanes + lane] = j * L.G + hh < np ? v : 0.f;
 }
 
-template <int G>
+template <int G, bool DET>
 cudaError_t launch_iter_t(const IterArgs& a, int grid, cudaStream_t st) {
-    const size_t smem = iter_smem_bytes(a.L.E, grid);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = iter_smem_bytes(a.L.E, grid, DET);
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     IterArgs args = a;
     void* params[] = {&args};
-    return cudaLaunchCooperativeKernel((const void*)k_iter<G>, dim3(grid), dim3(kIterThreads), params, smem, st);
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G, DET>, dim3(grid), dim3(kIterThreads), params, smem,
+                                       st);
 }
 
-template <int G>
+template <int G, bool DET>
 cudaError_t occupancy_t(int E, int grid_hint, int* blocks) {
-    const size_t smem = iter_smem_bytes(E, grid_hint);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = iter_smem_bytes(E, grid_hint, DET);
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G>, kIterThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G, DET>, kIterThreads, smem);
 }
 
 }  // namespace
 
-// Dynamic shared memory of the iteration kernel: histogram (8 B per edge),
-// gather weights (4 B per edge), staging buffers, and the CTA's price slice
-// (current and next) for a grid of at least `grid` CTAs.
-size_t iter_smem_bytes(int E, int grid) {
-    size_t b = 2 * (size_t)(E + 1) * sizeof(unsigned) + (size_t)(E + 1) * sizeof(float);
+// Dynamic shared memory of the iteration kernel: histogram (8 B per edge
+// deterministic, 4 B otherwise), gather weights (4 B per edge), staging
+// buffers, and the CTA's price slice (current and next) for a grid of at
+// least `grid` CTAs.
+size_t iter_smem_bytes(int E, int grid, bool det) {
+    size_t b = (det ? 2 : 1) * (size_t)(E + 1) * sizeof(unsigned) + (size_t)(E + 1) * sizeof(float);
     b = (b + 31 * sizeof(float) + 127) & ~size_t(127);
     b += (size_t)kIterWarps * 2 * kIterStageRows * kLanes * sizeof(uint16_t);
     const int slice = (E + grid - 1) / (grid > 0 ? grid : 1) + 1;
@@ -385,21 +436,37 @@ size_t iter_smem_bytes(int E, int grid) {
     return b;
 }
 
-cudaError_t iter_occupancy(int G, int E, int grid_hint, int* blocks_per_sm) {
+cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_per_sm) {
+    if (det) {
+        switch (G) {
+            case 1: return occupancy_t<1, true>(E, grid_hint, blocks_per_sm);
+            case 2: return occupancy_t<2, true>(E, grid_hint, blocks_per_sm);
+            case 4: return occupancy_t<4, true>(E, grid_hint, blocks_per_sm);
+            default: return occupancy_t<8, true>(E, grid_hint, blocks_per_sm);
+        }
+    }
     switch (G) {
-        case 1: return occupancy_t<1>(E, grid_hint, blocks_per_sm);
-        case 2: return occupancy_t<2>(E, grid_hint, blocks_per_sm);
-        case 4: return occupancy_t<4>(E, grid_hint, blocks_per_sm);
-        default: return occupancy_t<8>(E, grid_hint, blocks_per_sm);
+        case 1: return occupancy_t<1, false>(E, grid_hint, blocks_per_sm);
+        case 2: return occupancy_t<2, false>(E, grid_hint, blocks_per_sm);
+        case 4: return occupancy_t<4, false>(E, grid_hint, blocks_per_sm);
+        default: return occupancy_t<8, false>(E, grid_hint, blocks_per_sm);
     }
 }
 
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
+    if (a.o.deterministic) {
+        switch (a.L.G) {
+            case 1: return launch_iter_t<1, true>(a, grid, st);
+            case 2: return launch_iter_t<2, true>(a, grid, st);
+            case 4: return launch_iter_t<4, true>(a, grid, st);
+            default: return launch_iter_t<8, true>(a, grid, st);
+        }
+    }
     switch (a.L.G) {
-        case 1: return launch_iter_t<1>(a, grid, st);
-        case 2: return launch_iter_t<2>(a, grid, st);
-        case 4: return launch_iter_t<4>(a, grid, st);
-        default: return launch_iter_t<8>(a, grid, st);
+        case 1: return launch_iter_t<1, false>(a, grid, st);
+        case 2: return launch_iter_t<2, false>(a, grid, st);
+        case 4: return launch_iter_t<4, false>(a, grid, st);
+        default: return launch_iter_t<8, false>(a, grid, st);
     }
 }
 

@@ -53,8 +53,22 @@ __device__ bool grid_sync(unsigned* counter, unsigned target, int* status, long 
     return s_ok != 0;
 }
 
+// Residual balancing (Eq. 17): beta times C when r > A s, divided by C when
+// s > A r; a step that would leave [kBetaMin, kBetaMax] is not taken (1/beta
+// and log beta stay finite FP32 values).
+constexpr double kBetaMin = 1e-30, kBetaMax = 1e30;
+__device__ __forceinline__ double balanced_beta(double beta, double r, double s, double A, double C) {
+    double nb = beta;
+    if (r > A * s) nb = beta * C;
+    else if (s > A * r) nb = beta / C;
+    return (nb >= kBetaMin && nb <= kBetaMax) ? nb : beta;
+}
+
 // Kahan-compensated FP32 accumulation (per-thread partial sums of the
-// residual norms; the cross-thread reduction is FP64).
+// residual norms; the cross-thread reduction is FP64).  c holds minus the
+// low-order part lost so far, so the sum is s - c; for non-negative terms
+// the error of the compensated sum is at most about 2 eps times the sum
+// (eps = 2^-24), independent of the number of terms.
 struct KSum {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float v) {
@@ -63,6 +77,17 @@ struct KSum {
         c = (t - s) - y;
         s = t;
     }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// A lane's running sums of the residual terms of its warp's blocks (Eqs.
+// 15-16): sum (x' - x)^2 compensated (it decides convergence: its terms are
+// small differences that shrink by orders of magnitude over a solve), and
+// the norms sum x'^2 and sum n_r x'^2 (positive terms of similar size, which
+// only scale the residuals) in plain FP32.
+struct LaneRes {
+    KSum d;
+    float x = 0.f, e = 0.f;
 };
 
 // Root of A + H nu = (beta nu)^(-1/alpha) in t = log nu on (tlo, thi); the
@@ -278,16 +303,20 @@ __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int l
     return in;
 }
 
-// ACC: the block's residual terms are added into this lane's running sums
-// acc[3] (the caller reduces them once per phase), else summed over the warp
-// and stored per block.  HOPS: the hop counts come with the block's inputs,
-// else the gather counts the non-padding ids.
-template <int G, bool STAGED, bool ACC, bool HOPS>
+// ACC: the block's residual terms are added into this lane's compensated
+// running sums acc (the caller reduces them once per phase, in FP64), else
+// summed over the warp and stored per block.  HOPS: the hop counts come with the block's inputs,
+// else the gather counts the non-padding ids.  DET: each rate enters the
+// load histogram as an exact split fixed-point pair (h_hi, h_lo: two 32-bit
+// integer atomics per incidence, order-free); else h_hi is an FP32
+// histogram and each rate is added by one FP32 shared atomic per incidence
+// (the sum then depends on the order of the atomics in its last bits).
+template <int G, bool STAGED, bool ACC, bool HOPS, bool DET>
 __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane, const uint16_t* bids, int s0,
                                               unsigned counts, int KB, const BlockIn& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
                                               unsigned* h_lo, float inv_beta, float logbeta,
-                                              float beta_f, float alpha, float inv_alpha, float (&acc)[3]) {
+                                              float beta_f, float alpha, float inv_alpha, LaneRes& acc) {
     constexpr int KL = kMaxPathsPerLane;
     const uint16_t sentinel = a.sentinel;
     const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -336,7 +365,8 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
         nu = solve_nu<KL, G>(m, an, D, inv_beta, logbeta, alpha, inv_alpha, lam0 * inv_beta, gm);
         if ((lane & (G - 1)) == 0) __stcg(&a.lam[di], nu * beta_f);
     }
-    float bd = ACC ? acc[0] : 0.f, bx = ACC ? acc[1] : 0.f, be = ACC ? acc[2] : 0.f;
+    // this block's residual terms (at most 4 paths per lane, plain FP32)
+    float bd = 0.f, bx = 0.f, be = 0.f;
     float* xq = xout + (size_t)s0 * kLanes + lane;
     rs = 0;
     #pragma unroll
@@ -348,7 +378,12 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
             const float dx = xn - xo[j];
             bd = fmaf(dx, dx, bd);
             bx = fmaf(xn, xn, bx);
-            if (xn != 0.f) {
+            if (xn != 0.f && !DET) {
+                be = fmaf(xn * xn, (float)((nbits >> (8 * j)) & 0xffu), be);
+                float* h_f = reinterpret_cast<float*>(h_hi);
+                #pragma unroll 8
+                for (unsigned r = 0; r < cnt; ++r) atomicAdd(&h_f[id_at(rs + r)], xn);
+            } else if (xn != 0.f) {
                 // the path's hop count n (n <= 255 hops)
                 be = fmaf(xn * xn, (float)((nbits >> (8 * j)) & 0xffu), be);
                 // split fixed point: integer part of xn * 2^12 and the
@@ -371,9 +406,10 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
         }
     }
     if (ACC) {
-        acc[0] = bd;
-        acc[1] = bx;
-        acc[2] = be;
+        // added into the lane's compensated running sums
+        acc.d.add(bd);
+        acc.x += bx;
+        acc.e += be;
     } else {
         // the block's residual terms, summed over the warp in a fixed order
         // and stored per block, so that their totals do not depend on which
@@ -420,14 +456,14 @@ struct WarpStage {
 // cycles per block against 6.8 % less time per iteration with cp.async.
 //
 // ACC (see process_block): the residual terms of the warp's blocks are summed
-// per lane into acc[3], in the fixed order of the interleave.  HOPS: see
-// process_block.
-template <int G, int ROWS, bool ACC, bool HOPS>
+// per lane into acc (compensated), in the fixed order of the interleave.  HOPS
+// and DET: see process_block.
+template <int G, int ROWS, bool ACC, bool HOPS, bool DET>
 __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __restrict__ blkmeta,
                            const uint16_t* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
                            unsigned* h_hi, unsigned* h_lo, float inv_beta, float logbeta, float beta_f,
-                           float alpha, float inv_alpha, float (&acc)[3]) {
+                           float alpha, float inv_alpha, LaneRes& acc) {
     const int lane = threadIdx.x & 31;
     const int none = start + count * stride;  // any index >= none means "no block"
     const int nw = (int)(blockDim.x >> 5);
@@ -495,11 +531,11 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
             // lane; the __syncwarp makes each lane's copies visible to all
             cp_async_wait_prev();
             __syncwarp();
-            process_block<G, true, ACC, HOPS>(bc, b0, lane, ws.buf[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
+            process_block<G, true, ACC, HOPS, DET>(bc, b0, lane, ws.buf[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                         inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         } else {
             const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
-            process_block<G, false, ACC, HOPS>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
+            process_block<G, false, ACC, HOPS, DET>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
                                          w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         b0 = b1;

@@ -52,7 +52,8 @@ def _pair(te, inst, iters, **kw):
     t = te.TE(inst, **kw)
     res = t.solve(iters)
     okw = {k: v for k, v in kw.items() if k in ("alpha_target", "alpha_start", "alpha_step", "alpha_max",
-                                               "gamma", "A", "C", "beta0", "adapt_beta", "continuation")}
+                                               "gamma", "gamma_max", "A", "C", "beta0", "adapt_beta",
+                                               "continuation", "balance_floor")}
     s = O.OracleSolver(inst, **okw)
     s.run(iters)
     return t, res, s

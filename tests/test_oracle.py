@@ -276,3 +276,36 @@ def test_printed_rate_suggestion_does_not_see_capacity(tiny):
         return np.maximum((cost.mean() - cost) / beta, 0.0)
 
     assert np.allclose(printed(1.0, 0.3), printed(100.0, 7.0), rtol=0, atol=1e-12)
+
+
+def test_oracle_structs_match_ctypes_mirrors():
+    """The ctypes mirrors of the oracle's option and scalar structs have the
+    C layout: every field set from Python comes back unchanged."""
+    import ctypes
+    lib = O._L()
+    lib.or_echo_options.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.or_echo_scalars.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    vals = [1.5, 2.5, 3.5, 4.5, 5.5, 6.5, 7.5, 8.5, 9.5, 10.5, 11, 12, 13, 14]
+    o = O._Opts(*vals)
+    out = np.zeros(15)
+    lib.or_echo_options(ctypes.byref(o), out.ctypes.data)
+    assert out[:14].tolist() == vals and out[14] == ctypes.sizeof(O._Opts)
+    sc = O._Scalars(1.25, 2.25, 3.25, 7, 8, 1, 0)
+    out = np.zeros(7)
+    lib.or_echo_scalars(ctypes.byref(sc), out.ctypes.data)
+    assert out[:6].tolist() == [1.25, 2.25, 3.25, 7, 8, 1] and out[6] == ctypes.sizeof(O._Scalars)
+
+
+def test_max_norm_primal_residual_bounds_overload_at_stop(tiny):
+    """With gamma_max set, a level counts as converged only when the largest
+    n_e |u_e' - u_e| / C_e is within gamma_max.  An edge loaded above its
+    capacity keeps a positive price, so its n_e (u_e' - u_e) is exactly
+    L_e - C_e: at the stop every relative overload, recomputed here from the
+    final rates, is within gamma_max (and the plain stop rule alone does not
+    guarantee that)."""
+    for gmax in (1e-2, 1e-3):
+        s = O.OracleSolver(tiny, alpha_max=8.0, gamma_max=gmax)
+        s.run(200000)
+        assert s.converged
+        over = (O.edge_loads(tiny, s.allocation()) - tiny.capacity) / tiny.capacity
+        assert over.max() <= gmax * (1 + 1e-9), (gmax, over.max())

@@ -53,7 +53,21 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="large", choices=["tiny", "medium", "large"])
-    ap.add_argument("--ref-iters", type=int, default=30000)
+    ap.add_argument("--ref-iters", type=int, default=40000)
+    ap.add_argument("--ref-alpha-max", type=float, default=32.0,
+                    help="alpha cap of the OPT reference run")
+    ap.add_argument("--ref-gamma", type=float, default=1e-3, help="gamma of the OPT reference run")
+    ap.add_argument("--ref-gamma-max", type=float, default=0.0,
+                    help="max-norm primal residual bar of the OPT reference run (0: off)")
+    ap.add_argument("--ref-beta-max", type=float, default=4096.0,
+                    help="bound on beta of the OPT reference run, times beta0")
+    ap.add_argument("--ref-k", type=int, default=9050,
+                    help="reference arm on the large workload: iterations the oracle is extrapolated to "
+                         "(the CUDA arm's measured count to 1%%)")
+    ap.add_argument("--no-k1-check", action="store_true",
+                    help="skip the reference rule's accuracy check on the k = 1 variant")
+    ap.add_argument("--no-medium-oracle", action="store_true",
+                    help="skip the measured oracle solve of the 200-node workload")
     ap.add_argument("--probe-every", type=int, default=250)
     ap.add_argument("--refine-every", type=int, default=25)
     ap.add_argument("--target", type=float, default=0.99)
@@ -206,23 +220,86 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per iteration from the committed ncu summary, or None when the
-    kernel sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "k_iter_large.md")
-    if not os.path.exists(path):
-        return None
-    h = kernel_hash()
-    src_hash, per_iter = None, None
-    for ln in open(path):
-        if ln.startswith("kernel_source_sha256_16:"):
-            src_hash = ln.split(":", 1)[1].strip()
-        if ln.startswith("dram_bytes_per_iteration:"):
-            try:
-                per_iter = float(ln.split(":", 1)[1].strip())
-            except ValueError:
-                per_iter = None
-    return per_iter if src_hash == h else None
+# DRAM traffic of the iteration kernel from one ncu capture (written by hand
+# from the capture's dram__bytes_read.sum + dram__bytes_write.sum): a JSON
+# object with the workload, the bytes per iteration and the hash of the
+# kernel sources it was taken on.  The traffic is reported only while the
+# sources are unchanged and the workload is the captured one.
+NCU_TRAFFIC_JSON = os.path.join(ROOT, "profiles", "k_iter_large_traffic.json")
+
+
+def ncu_traffic(workload: str):
+    """(DRAM bytes per iteration, source) of the captured workload, or
+    (None, reason)."""
+    if not os.path.exists(NCU_TRAFFIC_JSON):
+        return None, "no capture recorded"
+    rec = json.load(open(NCU_TRAFFIC_JSON))
+    if rec.get("workload") != workload:
+        return None, f"the capture is of the {rec.get('workload')} workload"
+    if rec.get("kernel_source_sha256_16") != kernel_hash():
+        return None, "the kernel changed since the capture"
+    return float(rec["dram_bytes_per_iteration"]), os.path.relpath(NCU_TRAFFIC_JSON, ROOT)
+
+
+def survey_bytes(inst, grid: int) -> int:
+    """Algorithmic bytes of one iteration by the per-unit figures of the
+    method's traffic with int32 edge ids: 4 B per incidence (the path-edge
+    ids), 12 B per path (its rate read and written, its offset), 8 B per
+    demand (demand and multiplier) and 8 B per edge per CTA (the partial
+    loads)."""
+    return int(4 * inst.nnz + 12 * inst.n_paths + 8 * inst.n_demands + 8 * grid * inst.n_edges)
+
+
+def ref_options(a) -> dict:
+    """Options of the OPT reference run (a stricter rule than the default):
+    beta bounded by --ref-beta-max times beta0, so that the balancing cannot
+    freeze the iterate after the alpha increments."""
+    return dict(alpha_max=a.ref_alpha_max, gamma=a.ref_gamma, gamma_max=a.ref_gamma_max, beta_max=a.ref_beta_max)
+
+
+def first_path_variant(inst):
+    """The k = 1 variant: every demand keeps only its first path."""
+    import numpy as np
+    from paper_2605_01748_b300 import instances
+    keep = np.zeros(inst.n_paths, dtype=bool)
+    keep[inst.demand_path_off[:-1]] = True
+    v = instances.drop_paths(inst, keep, name=inst.name + "-k1")
+    v.meta["k"] = 1
+    return v
+
+
+def exact_maxmin_k1(inst1):
+    """Host reference leg: the exact max-min rates of single-path demands by
+    progressive filling (the FP64 oracle's), and the host time it took."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    exact = O.maxmin_single_path(inst1)
+    return exact, time.perf_counter() - t0
+
+
+def run_rule_on(te, inst, dev, stream, opts, opt_eval, iters, every=0):
+    """Runs the solver with `opts` on `inst` for up to `iters` iterations
+    (stopping where its rule fires) and returns (result, optimality of the
+    proportionally scaled allocation, first iteration count probed at
+    `every` whose optimality reached 0.99 or None)."""
+    import torch
+    x = torch.empty(inst.n_paths, dtype=torch.float32, device=dev)
+    t = te.TE(inst, cuda_stream=stream.cuda_stream, **opts)
+    first = None
+    if every > 0:
+        while True:
+            r = t.solve(every)
+            te.te_allocation(t.h, x, te.PROJECT_SCALE)
+            if first is None and opt_eval(x) >= 0.99:
+                first = r["total_iters"]
+            if r["converged"] or r["total_iters"] >= iters:
+                break
+    else:
+        r = t.solve(iters)
+    te.te_allocation(t.h, x, te.PROJECT_SCALE)
+    q = opt_eval(x)
+    t.close()
+    return r, q, first
 
 
 def run_ours(a, ws, rank, local, dist):
@@ -246,38 +323,63 @@ def run_ours(a, ws, rank, local, dist):
     opt = Optimality(inst, dev)
 
     SCALE, ALG2 = te.PROJECT_SCALE, te.PROJECT_ALG2
-
-    # reference: the solver run to its own stop rule (converged on the first
-    # iteration after an alpha increment, Section 3.4), or to --ref-iters
-    ref_res = t.solve(a.iters if a.iters > 0 else a.ref_iters)
-    te.te_allocation(t.h, xdev, SCALE)
-    opt.set_reference(xdev)
-    te.te_allocation(t.h, xdev, ALG2)
-    alg2_at_ref = opt(xdev)
+    ref_desc, ref_k1 = None, None
+    if a.iters <= 0:
+        # OPT: the stricter reference rule run from the cold start, made
+        # feasible by proportional scaling
+        ropts = ref_options(a)
+        tr = te.TE(inst, cuda_stream=stream.cuda_stream, **ropts)
+        ref_res = tr.solve(a.ref_iters)
+        te.te_allocation(tr.h, xdev, SCALE)
+        opt.set_reference(xdev)
+        te.te_allocation(tr.h, xdev, ALG2)
+        alg2_at_ref = opt(xdev)
+        tr.close()
+        ref_desc = (f"the solver under the reference rule {ropts} from the cold start, {ref_res['total_iters']} "
+                    f"iterations (alpha {ref_res['alpha']:g}; "
+                    f"{'stopped by its rule' if ref_res['converged'] else 'iteration cap'}), proportionally "
+                    f"scaled; theta = 1e-6 max C_e")
+        if rank == 0 and not a.no_k1_check:
+            # accuracy of that rule against an exact optimum: the k = 1
+            # variant of this workload, whose exact max-min is progressive filling
+            inst1 = first_path_variant(inst)
+            exact, ex_s = exact_maxmin_k1(inst1)
+            ev1 = Optimality(inst1, dev)
+            ev1.opt = torch.from_numpy(np.maximum(exact, ev1.theta)).to(dev)
+            r1, q1, _ = run_rule_on(te, inst1, dev, stream, ropts, ev1, a.ref_iters)
+            rd, qd, _ = run_rule_on(te, inst1, dev, stream, {}, ev1, a.ref_iters)
+            ref_k1 = {"workload": workload_desc(inst1),
+                      "reference_rule": {"optimality": round(q1, 5), "iters": r1["total_iters"],
+                                         "alpha": r1["alpha"]},
+                      "default_rule": {"optimality": round(qd, 5), "iters": rd["total_iters"], "alpha": rd["alpha"]},
+                      "exact": f"progressive filling on the host ({ex_s:.1f} s)"}
 
     def probe_at(n):
-        """Runs to total iteration n; returns (alpha, optimality scaled, optimality Algorithm 2)."""
+        """Runs to total iteration n; returns (result, optimality scaled, optimality Algorithm 2)."""
         r = t.solve(n - t.solve(0)["total_iters"])
         te.te_allocation(t.h, xdev, SCALE)
         q = opt(xdev)
         te.te_allocation(t.h, xdev, ALG2)
         return r, q, opt(xdev)
 
-    # probe: first K whose scaled allocation is within 1%, coarse then fine
+    # probe: first K whose scaled allocation is within 1% of OPT, coarse then fine
     K, trace = (a.iters if a.iters > 0 else None), []
     alg2_best = (0.0, 0)
+    stop_iters = None
     if K is None:
         t.reset()
-        n_ref = ref_res["total_iters"]
         n, lo = 0, 0
-        while n < n_ref:
-            n = min(n + a.probe_every, n_ref)
-            r, q, q2 = probe_at(n)
+        while n < a.ref_iters:
+            r, q, q2 = probe_at(n + a.probe_every)
+            n = r["total_iters"]
             trace.append((n, r["alpha"], round(q, 5), round(q2, 5)))
             if q2 > alg2_best[0]:
                 alg2_best = (q2, n)
             if q >= a.target:
                 K = n
+                break
+            if r["converged"]:
+                stop_iters = n
                 break
             lo = n
         if K is not None and K - lo > a.refine_every:
@@ -292,11 +394,10 @@ def run_ours(a, ws, rank, local, dist):
                     K = n
                     break
         if K is None:
-            K = max(1, n_ref)
+            K = stop_iters or a.ref_iters
     q_at_K = trace[-1][2] if trace else None
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(a.warmup + a.steps)]
     launches0 = None
-    opt_check = None
     for i in range(a.warmup + a.steps):
         if i == a.warmup:
             if dist:
@@ -324,7 +425,7 @@ def run_ours(a, ws, rank, local, dist):
     step_ms = [e[0].elapsed_time(e[3]) for e in timed]
     solve_ms = [e[1].elapsed_time(e[2]) for e in timed]
     total_ms = sum(step_ms)
-    opt_check = opt(xdev)
+    opt_check = opt(xdev) if opt.opt is not None else None
 
     # end to end through the public API with host buffers: demands in from
     # pinned host memory, allocation out to pinned host memory
@@ -347,9 +448,10 @@ def run_ours(a, ws, rank, local, dist):
     ms_step, e2e_mean = max_over_ranks([ms_step, statistics.mean(e2e_ms)], dist, dev)
 
     solve_mean = statistics.mean(solve_ms)
-    achieved = lay["bytes_per_iter"] * K / (solve_mean * 1e-3) / 1e9
-    # the recorded ncu traffic is that of the 1500-node capture
-    traffic_iter = ncu_traffic() if a.workload == "large" else None
+    alg_bytes = survey_bytes(inst, lay["grid"])
+    achieved = alg_bytes * K / (solve_mean * 1e-3) / 1e9
+    moved = lay["bytes_per_iter"] * K / (solve_mean * 1e-3) / 1e9
+    traffic_iter, traffic_src = ncu_traffic(a.workload)
     l2_resident = lay["bytes_per_iter"] < 126e6
     out = {
         "metric": METRIC,
@@ -368,17 +470,17 @@ def run_ours(a, ws, rank, local, dist):
             "workload": workload_desc(inst),
             "objective": "max-min via alpha-continuation (alpha from 0, +1 per convergence, gamma 1e-3)",
             "iters_to_1pct": K,
+            "k_source": "--iters" if a.iters > 0 else "probe of this run",
             "optimality_at_K": q_at_K,
-            "optimality_timed_output": round(opt_check, 5),
+            "optimality_timed_output": None if opt_check is None else round(opt_check, 5),
             "feasibility_step": "proportional scaling (te_allocation PROJECT_SCALE; not in the paper)",
-            "opt_reference": f"same solver from the cold start, {ref_res['total_iters']} iterations "
-                             f"(alpha {ref_res['alpha']:g}; "
-                             f"{'stopped by its stop rule' if ref_res['converged'] else 'iteration cap, stop rule not yet fired'}), "
-                             f"proportionally scaled; theta = 1e-6 max C_e",
-            "algorithm2": {"best_optimality_probed": round(alg2_best[0], 5), "at_iters": alg2_best[1],
-                           "optimality_at_reference": round(alg2_at_ref, 5),
-                           "note": "the paper's projection on the same iterates; whole-path trims empty "
-                                   "the demands on edges far over capacity"},
+            "opt_reference": ref_desc,
+            "opt_reference_accuracy_k1": ref_k1,
+            "algorithm2": None if ref_desc is None else {
+                "best_optimality_probed": round(alg2_best[0], 5), "at_iters": alg2_best[1],
+                "optimality_at_reference": round(alg2_at_ref, 5),
+                "note": "the paper's projection on the same iterates; whole-path trims empty "
+                        "the demands on edges far over capacity"},
             "probe_trace_tail": trace[-4:],
             "l2": (f"L2-resident: {lay['bytes_per_iter'] / 1e6:.1f} MB per iteration (< 126 MB L2), no flush; "
                    f"a step is one launch of K iterations over the same data") if l2_resident else
@@ -397,8 +499,14 @@ def run_ours(a, ws, rank, local, dist):
             "unit": "GB/s",
             "frac": round(achieved / hbm_peak, 4),
             "traffic": None if traffic_iter is None else int(traffic_iter * K),
+            "traffic_source": traffic_src,
             "kernel": "k_iter (persistent; one launch = K iterations)",
-            "bytes_per_iter": lay["bytes_per_iter"],
+            "algorithmic_bytes_per_iter": alg_bytes,
+            "algorithmic_bytes_rule": "4 B per incidence (int32 id) + 12 B per path + 8 B per demand "
+                                      "+ 8 B per edge per CTA",
+            "layout_bytes_per_iter": lay["bytes_per_iter"],
+            "layout_achieved": round(moved, 1),
+            "layout_frac": round(moved / hbm_peak, 4),
             "peak_source": peak_src,
             **({"note": "L2-resident workload: bound by latency and the grid barriers, not HBM"}
                if l2_resident else {}),
@@ -409,57 +517,81 @@ def run_ours(a, ws, rank, local, dist):
         "clocks": clocks.summary(),
         "wall_s_timed": round(wall, 3),
     }
-    # FP64 oracle beside it: the same workload on the host cores, a bounded
-    # sample of iterations, and the GPU's error against it after those iterations
+    # FP64 oracle beside it (host cores): a bounded sample of iterations of
+    # the same workload, extrapolated to K, the GPU's error against it after
+    # those iterations, and one full oracle solve of the 200-node workload
+    # timed for real beside the same solve on the GPU
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
-        from oracle import oracle as O
-        n = a.oracle_sample_iters
-        cores = os.cpu_count() or 1
-        s = O.OracleSolver(inst, threads=cores)
-        t0 = time.perf_counter()
-        s.run(n)
-        dt = time.perf_counter() - t0
-        per_iter = dt / n
-        t1 = time.perf_counter()
-        O.project_scale(inst, s.allocation())
-        dp = time.perf_counter() - t1
-        t.reset()
-        t.solve(n)
-        xg = t.allocation(project=False).astype(np.float64)
-        xo = s.allocation()
-        err = float(np.max(np.abs(xg - xo)) / max(np.max(np.abs(xo)), 1e-300))
-        # and one iteration on a single thread (the oracle's parallel scaling)
-        s1 = O.OracleSolver(inst, threads=1)
-        t2 = time.perf_counter()
-        s1.run(1)
-        d1 = time.perf_counter() - t2
-        del s1
-        out["cpu_baseline"] = {"value": round((per_iter * K + dp) * 1e3, 1), "unit": "ms", "cores": cores,
-                               "kind": "oracle",
-                               "sample": f"{n} FP64 oracle iterations of the same workload in one call "
-                                         f"({dt:.2f} s, incl. its edge->path transpose), scaled to K={K} "
-                                         f"iterations, plus one proportional scaling ({dp:.2f} s)",
-                               "s_per_iter": round(per_iter, 4),
-                               "s_per_iter_1_thread": round(d1, 4)}
-        out["error_vs_oracle"] = {"max_rel_err_after_sample_iters": err, "iters": n}
+        out.update(cpu_legs(a, inst, t, K, te, dev, stream))
     if rank == 0:
         print(json.dumps(out), flush=True)
     t.close()
 
 
-def recorded_k(workload: str):
-    """The iteration count to 1% that the last committed benchmark run of
-    `workload` measured (profiles/bench_<workload>.md, line 'iters_to_1pct:')."""
-    path = os.path.join(ROOT, "profiles", f"bench_{workload}.md")
-    if not os.path.exists(path):
-        return None
-    for ln in open(path):
-        if ln.startswith("iters_to_1pct:"):
-            try:
-                return int(ln.split(":", 1)[1].strip())
-            except ValueError:
-                return None
-    return None
+def cpu_legs(a, inst, t, K, te, dev, stream):
+    """The oracle's baseline numbers and the GPU's error against it."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2605_01748_b300 import instances
+    n = a.oracle_sample_iters
+    cores = os.cpu_count() or 1
+    s = O.OracleSolver(inst, threads=cores)
+    t0 = time.perf_counter()
+    s.run(n)
+    dt = time.perf_counter() - t0
+    per_iter = dt / n
+    t1 = time.perf_counter()
+    O.project_scale(inst, s.allocation())
+    dp = time.perf_counter() - t1
+    t.reset()
+    t.solve(n)
+    xg = t.allocation(project=False).astype(np.float64)
+    xo = s.allocation()
+    err = float(np.max(np.abs(xg - xo)) / max(np.max(np.abs(xo)), 1e-300))
+    s1 = O.OracleSolver(inst, threads=1)
+    t2 = time.perf_counter()
+    s1.run(1)
+    d1 = time.perf_counter() - t2
+    del s1, s
+    base = {"value": round((per_iter * K + dp) * 1e3, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+            "extrapolated": True,
+            "sample": f"{n} FP64 oracle iterations of the same workload in one call ({dt:.2f} s, incl. its "
+                      f"edge->path transpose), extrapolated to K={K} iterations, plus one proportional scaling "
+                      f"({dp:.2f} s)",
+            "s_per_iter": round(per_iter, 4), "s_per_iter_1_thread": round(d1, 4)}
+    errs = {"max_rel_err_after_sample_iters": err, "iters": n}
+    if a.workload != "medium" and not a.no_medium_oracle:
+        # measured, not extrapolated: the 200-node workload solved to the stop
+        # rule by the oracle on all host cores and by the GPU
+        med = instances.make("medium", threads=cores)
+        so = O.OracleSolver(med, threads=cores)
+        t3 = time.perf_counter()
+        so.run(a.ref_iters)
+        xo_s = O.project_scale(med, so.allocation())
+        d_or = time.perf_counter() - t3
+        import torch
+        tg = te.TE(med, cuda_stream=stream.cuda_stream)
+        x = torch.empty(med.n_paths, dtype=torch.float32, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tg.solve(10)
+        tg.reset()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rg = tg.solve(a.ref_iters)
+        te.te_allocation(tg.h, x, te.PROJECT_SCALE)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        xg_s = x.cpu().numpy().astype(np.float64)
+        tg.close()
+        Sg, So = O.demand_totals(med, xg_s), O.demand_totals(med, xo_s)
+        base["measured_medium"] = {
+            "workload": workload_desc(med), "oracle_ms": round(d_or * 1e3, 1), "oracle_iters": so.iters,
+            "gpu_ms": round(e0.elapsed_time(e1), 3), "gpu_iters": rg["total_iters"], "cores": cores,
+            "step": "cold start to the stop rule (default options) plus proportional scaling, not extrapolated"}
+        errs["medium_full_solve"] = {
+            "same_stop_iteration": bool(so.iters == rg["total_iters"]),
+            "max_rel_err_demand_totals": float(np.max(np.abs(Sg - So)) / max(So.max(), 1e-300))}
+    return {"cpu_baseline": base, "error_vs_oracle": errs}
 
 
 def oracle_k(inst, O, target: float, every: int, cap: int, threads: int):
@@ -652,49 +784,75 @@ def run_batch(a, ws=1, rank=0, dist=None):
 
 
 def run_exact_k1(a):
-    """Optimality (Section 4.1) of the solver's max-min against the exact
-    max-min of single-path demands: the first path of every demand of the
-    200- and 1500-node workloads, progressive filling on the host (FP64
-    oracle), the solver with default options probed every 250 iterations
-    until its stop rule fires."""
+    """Against an exact optimum: the single-path (k = 1) variants of the 200-
+    and 1500-node workloads, whose exact max-min rates come from progressive
+    filling (host reference leg).  For each: the solver under the default
+    options and under the reference rule, probed every --probe-every
+    iterations until its rule fires; the first iteration count whose
+    proportionally scaled allocation is within 1% of the exact optimum (then
+    refined), and that many iterations timed like the headline step (reset,
+    solve, feasibility step).  One JSON line per variant."""
     import numpy as np
     import torch
-    from oracle import oracle as O
     from paper_2605_01748_b300 import instances, te
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     for name in ("medium", "large"):
-        full = instances.make(name, threads=os.cpu_count() or 0)
-        keep = np.zeros(full.n_paths, dtype=bool)
-        keep[full.demand_path_off[:-1]] = True
-        inst = instances.drop_paths(full, keep, name=name + "-k1")
-        inst.meta["k"] = 1
-        t0 = time.time()
-        exact = O.maxmin_single_path(inst)
-        wf_s = time.time() - t0
+        inst = first_path_variant(instances.make(name, threads=os.cpu_count() or 0))
+        exact, wf_s = exact_maxmin_k1(inst)
         ev = Optimality(inst, dev)
         ev.opt = torch.from_numpy(np.maximum(exact, ev.theta)).to(dev)
         x = torch.empty(inst.n_paths, dtype=torch.float32, device=dev)
-        t = te.TE(inst, cuda_stream=stream.cuda_stream)
-        rows, first = [], None
-        while True:
-            r = t.solve(250)
-            te.te_allocation(t.h, x, te.PROJECT_SCALE)
-            q = ev(x)
-            te.te_allocation(t.h, x, te.PROJECT_ALG2)
-            q2 = ev(x)
-            rows.append((r["total_iters"], r["alpha"], round(q, 5), round(q2, 5)))
-            if first is None and q >= a.target:
-                first = r["total_iters"]
-            if r["converged"] or r["total_iters"] >= a.ref_iters:
-                break
-        t.close()
-        print(json.dumps({"mode": "exact-k1", "workload": workload_desc(inst), "exact_host_s": round(wf_s, 1),
-                          "iters_to_target": first, "stop": rows[-1], "trace_tail": rows[-5:],
-                          "columns": "iterations, alpha, optimality (proportional scaling), optimality (Algorithm 2)"}),
-              flush=True)
+        line = {"mode": "exact-k1", "workload": workload_desc(inst), "exact_host_s": round(wf_s, 1),
+                "metric": "ms to within 1% of the exact max-min (optimality >= 0.99)", "unit": "ms"}
+        for label, opts in (("default", {}), ("reference_rule", ref_options(a))):
+            t = te.TE(inst, cuda_stream=stream.cuda_stream, **opts)
+            rows, first, lo, best = [], None, 0, 0.0
+            while True:
+                r = t.solve(a.probe_every)
+                te.te_allocation(t.h, x, te.PROJECT_SCALE)
+                q = ev(x)
+                best = max(best, q)
+                rows.append((r["total_iters"], r["alpha"], round(q, 5)))
+                if first is None and q >= a.target:
+                    first = r["total_iters"]
+                    break
+                if r["converged"] or r["total_iters"] >= a.ref_iters:
+                    break
+                lo = r["total_iters"]
+            res = {"stop_or_hit": rows[-1], "best_optimality": round(best, 5), "trace_tail": rows[-4:]}
+            if first is not None:
+                t.reset()
+                t.solve(lo)
+                n = lo
+                while n < first:
+                    n += a.refine_every
+                    t.solve(a.refine_every)
+                    te.te_allocation(t.h, x, te.PROJECT_SCALE)
+                    if ev(x) >= a.target:
+                        first = n
+                        break
+                ms = []
+                for i in range(a.warmup + a.steps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    t.reset()
+                    t.solve(first)
+                    te.te_allocation(t.h, x, te.PROJECT_SCALE)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    if i >= a.warmup:
+                        ms.append(e0.elapsed_time(e1))
+                res.update({"iters_to_1pct": first, "value": round(statistics.mean(ms), 4),
+                            "optimality_timed_output": round(ev(x), 5)})
+            else:
+                res.update({"iters_to_1pct": None, "value": None})
+            line[label] = res
+            t.close()
+        line["reference_rule_options"] = ref_options(a)
+        print(json.dumps(line), flush=True)
 
 
 def run_reference(a, ws, rank):
@@ -703,8 +861,9 @@ def run_reference(a, ws, rank):
     workload, scales it to K iterations and adds one proportional scaling of
     the result.  K: on tiny and medium the oracle's own count to 1%; on large
     (about 20,000 FP64 iterations of 1 s each would be needed to find it) the
-    count the CUDA arm measured, read from its committed benchmark summary;
-    both arms run the same iteration, equal within 1e-4 at equal counts."""
+    count given by --ref-k (the CUDA arm's measured count); both arms run the
+    same iteration, equal within 1e-4 at equal counts.  The value is an
+    extrapolation from the timed sample and says so."""
     from oracle import oracle as O
     from paper_2605_01748_b300 import instances
 
@@ -718,9 +877,8 @@ def run_reference(a, ws, rank):
         K = oracle_k(inst, O, a.target, a.refine_every, a.ref_iters, cores)
         k_src = "the oracle's own probe (stop-rule reference, proportional scaling)"
     else:
-        K, k_src = recorded_k(a.workload), "CUDA arm's measured K (profiles/bench_%s.md)" % a.workload
-    if K is None:
-        K, k_src = 10000, "default 10000 (no recorded count)"
+        K, k_src = a.ref_k, ("--ref-k: the iteration count to 1% that the CUDA arm measures on this workload "
+                             "(finding it with the oracle would take about 20,000 FP64 iterations of ~1 s)")
     n = a.oracle_sample_iters
     times, proj = [], []
     for i in range(a.warmup + a.steps):
@@ -739,8 +897,9 @@ def run_reference(a, ws, rank):
            "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(v, 1), "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload_desc(inst), "iters_to_1pct": K, "k_source": k_src,
+                      "extrapolated": True,
                       "feasibility_step": "proportional scaling (oracle project_scale)"},
-           "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": cores, "kind": "oracle",
+           "cpu_baseline": {"value": round(v, 1), "unit": "ms", "cores": cores, "kind": "oracle", "extrapolated": True,
                             "sample": f"per step: {n} FP64 oracle iterations of the full workload from the cold "
                                       f"start, scaled to K={K}, plus one proportional scaling "
                                       f"({statistics.mean(proj):.0f} ms)"},

@@ -96,6 +96,11 @@ typedef struct {
                              initial path rate), so the first utility push
                              lambda/(beta n_r) at lambda = 1 equals the mean
                              initial rate                                      */
+    double beta_max;      /* > 0: residual balancing never raises beta above
+                             beta_max * beta0 (the balancing of Eq. 17 with
+                             the paper's residuals can raise beta without
+                             bound after alpha increments, which freezes the
+                             iterate); 0 (default): no bound                  */
     double balance_floor; /* residual balancing (Eq. 17) acts only while
                              max(r, s) > balance_floor (default 1e-6): below
                              it both residuals of the FP32 iteration are
@@ -311,7 +316,8 @@ typedef struct {
  * [topo->n_edges]; the caller keeps its buffers) to the device and sets every
  * instance to the initial state of Algorithm 1.  Inputs must satisfy the rules
  * of te_create (edge ids are range-checked here, path walks are not).  The
- * options apply to every instance; a NULL cuda_stream makes the batch create
+ * options apply to every instance (deterministic = 1, beta_max = 0 and
+ * TE_PRECISION_FP32 only; others return TE_EUNSUPPORTED); a NULL cuda_stream makes the batch create
  * and own a stream (graph capture needs one).  Errors as te_create. */
 te_status te_batch_create(const te_topology* topo, int32_t n, const te_paths* const* paths,
                           const double* const* demands, const double* const* capacities,

@@ -62,13 +62,14 @@ class _Opts(ctypes.Structure):
                 ("alpha_step", ctypes.c_double), ("alpha_max", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("gamma_max", ctypes.c_double), ("A", ctypes.c_double),
                 ("C", ctypes.c_double),
-                ("beta0", ctypes.c_double), ("balance_floor", ctypes.c_double), ("adapt_beta", ctypes.c_int32),
+                ("beta0", ctypes.c_double), ("beta_max", ctypes.c_double), ("balance_floor", ctypes.c_double),
+                ("adapt_beta", ctypes.c_int32),
                 ("continuation", ctypes.c_int32), ("threads", ctypes.c_int32), ("scale_mode", ctypes.c_int32)]
 
 
 class _Scalars(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("alpha", ctypes.c_double), ("scale", ctypes.c_double),
-                ("iter", ctypes.c_int64), ("iter_alpha", ctypes.c_int64),
+                ("beta0", ctypes.c_double), ("iter", ctypes.c_int64), ("iter_alpha", ctypes.c_int64),
                 ("converged", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
@@ -136,7 +137,7 @@ class OracleSolver:
                  C: float = 2.0, beta0: float = 0.0, adapt_beta: bool = True, continuation: bool = True,
                  alpha_start: float = 0.0, alpha_step: float = 1.0, alpha_max: float = 32.0,
                  threads: int = 0, x0: Optional[np.ndarray] = None, scale_mode: int = 1,
-                 balance_floor: float = 1e-6, gamma_max: float = 0.0):
+                 balance_floor: float = 1e-6, gamma_max: float = 0.0, beta_max: float = 0.0):
         """Defaults: the paper's A = 10, C = 2, gamma = 1e-3 (Section 3.7),
         alpha from 0 in steps of 1 (Algorithm 1); the unit of the normalised
         problem is the geometric mean of the demands (scale_mode = 1) and
@@ -146,7 +147,7 @@ class OracleSolver:
         self.inst = inst
         self.view = _InstanceView(inst)
         self.opts = _Opts(alpha_target, alpha_start, alpha_step, alpha_max, gamma, gamma_max, A, C, beta0,
-                          float(balance_floor), int(adapt_beta), int(continuation), int(threads),
+                          float(beta_max), float(balance_floor), int(adapt_beta), int(continuation), int(threads),
                           int(scale_mode))
         self.x = np.zeros(inst.n_paths, dtype=np.float64)
         self.u = np.zeros(inst.n_edges, dtype=np.float64)
@@ -262,7 +263,7 @@ def gradient(inst, alpha: float, beta0: float, iters: int, checkpoint: int = 20,
     of the fixed schedule (beta0, alpha fixed) from the initial state, the
     normalisation unit held fixed (scale_mode 2: caller units)."""
     view = _InstanceView(inst)
-    opts = _Opts(alpha, alpha, 1.0, alpha, -1.0, 0.0, 10.0, 2.0, beta0, 1e-6, 0, 0, int(threads), int(scale_mode))
+    opts = _Opts(alpha, alpha, 1.0, alpha, -1.0, 0.0, 10.0, 2.0, beta0, 0.0, 1e-6, 0, 0, int(threads), int(scale_mode))
     J = ctypes.c_double()
     gC = np.zeros(inst.n_edges, dtype=np.float64)
     gD = np.zeros(inst.n_demands, dtype=np.float64)

@@ -79,6 +79,7 @@ typedef struct {
     double gamma_max;     /* > 0: convergence also needs max_e n_e |du_e| / C_e <= gamma_max */
     double A, C;          /* residual balancing constants (10, 2)         */
     double beta0;         /* initial penalty, normalised units (1)        */
+    double beta_max;      /* > 0: balancing never raises beta above beta_max * beta0 */
     double balance_floor; /* residual balancing only while max(r, s) exceeds it */
     int32_t adapt_beta;   /* 1: residual balancing on                     */
     int32_t continuation; /* 1: stop when converged on the first iteration after an increment */
@@ -90,6 +91,7 @@ typedef struct {
 /* Scalars of the solver state (arrays are passed separately). */
 typedef struct {
     double beta, alpha, scale;
+    double beta0;        /* initial penalty                               */
     int64_t iter;        /* iterations run so far                        */
     int64_t iter_alpha;  /* iterations since alpha last changed          */
     int32_t converged;   /* 1 once the stop rule fired                   */
@@ -103,12 +105,12 @@ enum { TR_R = 0, TR_S, TR_BETA, TR_ALPHA, TR_EVENT, TR_WIDTH };
 void or_echo_options(const or_options* o, double* out) {
     out[0] = o->alpha_target; out[1] = o->alpha_start; out[2] = o->alpha_step; out[3] = o->alpha_max;
     out[4] = o->gamma; out[5] = o->gamma_max; out[6] = o->A; out[7] = o->C; out[8] = o->beta0;
-    out[9] = o->balance_floor; out[10] = o->adapt_beta; out[11] = o->continuation; out[12] = o->threads;
-    out[13] = o->scale_mode; out[14] = (double)sizeof(or_options);
+    out[9] = o->beta_max; out[10] = o->balance_floor; out[11] = o->adapt_beta; out[12] = o->continuation;
+    out[13] = o->threads; out[14] = o->scale_mode; out[15] = (double)sizeof(or_options);
 }
 void or_echo_scalars(const or_scalars* sc, double* out) {
-    out[0] = sc->beta; out[1] = sc->alpha; out[2] = sc->scale; out[3] = (double)sc->iter;
-    out[4] = (double)sc->iter_alpha; out[5] = sc->converged; out[6] = (double)sizeof(or_scalars);
+    out[0] = sc->beta; out[1] = sc->alpha; out[2] = sc->scale; out[3] = sc->beta0; out[4] = (double)sc->iter;
+    out[5] = (double)sc->iter_alpha; out[6] = sc->converged; out[7] = (double)sizeof(or_scalars);
 }
 
 /* ------------------------------------------------------------------ */
@@ -271,6 +273,7 @@ int or_init(const or_instance* I, const or_options* o, const double* x0, double*
         const double nbar = (double)I->nnz / (double)I->n_paths;
         sc->beta = 1.0 / (nbar * xbar);
     }
+    sc->beta0 = sc->beta;
     sc->alpha = isfinite(o->alpha_target) && o->alpha_start > o->alpha_target ? o->alpha_target : o->alpha_start;
     sc->scale = scale;
     sc->iter = 0;
@@ -375,6 +378,7 @@ int64_t or_run(const or_instance* I, const or_options* o, double* x, double* u, 
             if (r_res > o->A * s_res) nb = beta * o->C;
             else if (s_res > o->A * r_res) nb = beta / o->C;
             if (!(nb >= 1e-30 && nb <= 1e30)) nb = beta;
+            if (o->beta_max > 0.0 && nb > o->beta_max * sc->beta0) nb = beta;
             if (nb != beta) {
                 const double ratio = beta / nb;
                 for (int e = 0; e < E; ++e) u[e] *= ratio;

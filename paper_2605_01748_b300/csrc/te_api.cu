@@ -145,6 +145,7 @@ void te_default_options(te_options* o) {
     o->beta0 = 0.0;       // automatic (see te.h)
     o->balance_floor = 1e-6;
     o->gamma_max = 0.0;
+    o->beta_max = 0.0;
     o->adapt_beta = 1;
     o->continuation = 1;
     o->scale_mode = 1;    // geometric mean of the demands
@@ -252,7 +253,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     }
     te_options opt;
     if (opt_in) opt = *opt_in; else te_default_options(&opt);
-    if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.balance_floor >= 0.0) || !(opt.gamma_max == opt.gamma_max) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
+    if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.balance_floor >= 0.0) || !(opt.gamma_max == opt.gamma_max) || !(opt.beta_max >= 0.0) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
         (opt.scale_mode < 0 || opt.scale_mode > 2) || (opt.deterministic != 0 && opt.deterministic != 1) ||
         !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0) {
         g_create_error = "invalid options";
@@ -282,6 +283,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     h->o.continuation = opt.continuation;
     h->o.balance_floor = opt.balance_floor;
     h->o.gamma_max = opt.gamma_max;
+    h->o.beta_cap = 1e30;
     h->o.deterministic = opt.deterministic;
     h->o.withhold_cta = opt.test_withhold_cta > 0 ? opt.test_withhold_cta - 1 : -1;
     h->beta0 = opt.beta0;
@@ -455,6 +457,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
                         3LL * (long long)sizeof(float) * (long long)ND +
                         (long long)sizeof(te::BlockMeta) * (long long)nblocks +
                         (long long)sizeof(unsigned) * (long long)hl.hops.size();
+    if (opt.beta_max > 0.0) h->o.beta_cap = opt.beta_max * h->beta0;
     te_status rs = te_reset(h);
     if (rs != TE_OK) return bail(rs);
     *out = h;

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
             done++;
             const bool numeric_ok = isfinite(s_res) && isfinite(r_res);
             if (numeric_ok && a.o.adapt_beta && fmax(r_res, s_res) > a.o.balance_floor) {
-                const double nb = balanced_beta(sc.beta, r_res, s_res, a.o.A, a.o.C);
+                const double nb = balanced_beta(sc.beta, r_res, s_res, a.o.A, a.o.C, a.o.beta_cap);
                 if (nb != sc.beta) {
                     // scaled prices follow beta; the weights keep d: w = u' ratio + d
                     const float ratio = (float)(sc.beta / nb);
@@ -489,6 +489,11 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     b->o.adapt_beta = opt.adapt_beta;
     b->o.balance_floor = opt.balance_floor;
     b->o.gamma_max = opt.gamma_max;
+    b->o.beta_cap = 1e30;
+    if (opt.beta_max > 0.0) {
+        b->err = "beta_max is not supported by the batch engine (per-instance beta0)";
+        return bail(TE_EUNSUPPORTED);
+    }
     b->o.deterministic = 1;
     b->o.continuation = opt.continuation;
     b->o.withhold_cta = -1;

@@ -62,6 +62,7 @@ struct Options {
     double gamma, A, C;
     double balance_floor;  // balancing only while max(r, s) exceeds it
     double gamma_max;      // > 0: convergence also needs max_e n_e |d_e| / C_e <= gamma_max
+    double beta_cap;       // upper bound of beta (beta_max * beta0, or 1e30)
     int adapt_beta, continuation;
     int deterministic;  // 1: exact fixed-point load histograms; 0: FP32 shared atomics
     int withhold_cta;  // test hook: this CTA never arrives at the barrier (-1: none)

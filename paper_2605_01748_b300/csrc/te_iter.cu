@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 float ratio = 1.f;
                 const bool numeric_ok = isfinite(s_res) && isfinite(r_res);
                 if (numeric_ok && a.o.adapt_beta && fmax(r_res, s_res) > a.o.balance_floor) {
-                    const double nb = balanced_beta(sc.beta, r_res, s_res, a.o.A, a.o.C);
+                    const double nb = balanced_beta(sc.beta, r_res, s_res, a.o.A, a.o.C, a.o.beta_cap);
                     if (nb != sc.beta) {
                         ratio = (float)(sc.beta / nb);
                         sc.beta = nb;

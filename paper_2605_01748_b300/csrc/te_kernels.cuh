@@ -54,14 +54,15 @@ __device__ bool grid_sync(unsigned* counter, unsigned target, int* status, long 
 }
 
 // Residual balancing (Eq. 17): beta times C when r > A s, divided by C when
-// s > A r; a step that would leave [kBetaMin, kBetaMax] is not taken (1/beta
-// and log beta stay finite FP32 values).
+// s > A r; a step that would leave [kBetaMin, min(kBetaMax, cap)] is not
+// taken (1/beta and log beta stay finite FP32 values; cap is the caller's
+// bound beta_max * beta0, or kBetaMax).
 constexpr double kBetaMin = 1e-30, kBetaMax = 1e30;
-__device__ __forceinline__ double balanced_beta(double beta, double r, double s, double A, double C) {
+__device__ __forceinline__ double balanced_beta(double beta, double r, double s, double A, double C, double cap) {
     double nb = beta;
     if (r > A * s) nb = beta * C;
     else if (s > A * r) nb = beta / C;
-    return (nb >= kBetaMin && nb <= kBetaMax) ? nb : beta;
+    return (nb >= kBetaMin && nb <= fmin(kBetaMax, cap)) ? nb : beta;
 }
 
 // Kahan-compensated FP32 accumulation (per-thread partial sums of the

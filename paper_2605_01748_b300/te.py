@@ -61,7 +61,7 @@ class te_options(ctypes.Structure):
     _fields_ = [("alpha_target", ctypes.c_double), ("alpha_start", ctypes.c_double),
                 ("alpha_step", ctypes.c_double), ("alpha_max", ctypes.c_double), ("gamma", ctypes.c_double), ("gamma_max", ctypes.c_double),
                 ("A", ctypes.c_double), ("C", ctypes.c_double), ("beta0", ctypes.c_double),
-                ("balance_floor", ctypes.c_double),
+                ("beta_max", ctypes.c_double), ("balance_floor", ctypes.c_double),
                 ("adapt_beta", ctypes.c_int32), ("continuation", ctypes.c_int32),
                 ("scale_mode", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
                 ("test_withhold_cta", ctypes.c_int32), ("deterministic", ctypes.c_int32),

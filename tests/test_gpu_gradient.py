@@ -95,3 +95,28 @@ def test_gradient_rejects_adaptive_schedule(te, tiny):
     with pytest.raises(te.TEError):
         t.gradient(10)
     t.close()
+
+
+def test_gradient_matches_central_differences_config5(te, medium):
+    """The differentiated configuration: alpha = 1 on the 200-node workload,
+    K = 200 unrolled iterations, checkpoints every 20; te_gradient against
+    FP64 central differences of the oracle's objective at relative step 1e-3
+    on 50 seeded coordinates of capacities and demands (tests/golden/
+    fd_medium_alpha1_K200.json, from tests/golden/make_fd_medium.py).  Same
+    bounds as the oracle's own reverse pass against these differences: every
+    coordinate within 2e-3 of the largest derivative (a step can cross a
+    kink of the piecewise-smooth map), the median to truncation error."""
+    import json
+    import os
+    d = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                    "fd_medium_alpha1_K200.json")))
+    t = _fixed(te, medium, d["alpha"], d["beta0"])
+    J, gC, gD = t.gradient(d["K"], 20)
+    t.close()
+    assert abs(J - d["J"]) <= 1e-6 * abs(d["J"])
+    fd = np.array([c["fd"] for c in d["coords"]])
+    g = np.array([gC[c["index"]] if c["kind"] == "C" else gD[c["index"]] for c in d["coords"]])
+    scale = np.max(np.abs(fd))
+    assert np.max(np.abs(g - fd)) <= 2e-3 * scale
+    rel = np.abs(g - fd) / np.maximum(np.abs(fd), 1e-3 * scale)
+    assert np.median(rel) <= 1e-4

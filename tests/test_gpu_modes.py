@@ -104,3 +104,23 @@ def test_nan_tolerance_rejected(te, tiny):
         t.solve(10, math.nan)
     assert ei.value.status == te.TE_EINVAL
     t.close()
+
+
+@pytest.mark.parametrize("name", ["tiny", "medium"])
+def test_beta_bound_matches_oracle(te, tiny, medium, name):
+    """With beta_max the balancing never raises beta above beta_max * beta0;
+    the GPU and the oracle take the same beta and alpha decisions."""
+    inst = tiny if name == "tiny" else medium
+    iters = 1500 if name == "tiny" else 400
+    t = te.TE(inst, beta_max=8.0)
+    t.solve(iters)
+    s = O.OracleSolver(inst, beta_max=8.0)
+    s.run(iters)
+    tg, to = t.trace(iters), s.trace
+    n = min(tg.shape[0], to.shape[0])
+    beta0 = s.sc.beta0  # the initial penalty (the same on both sides up to summation order)
+    assert np.all(tg[:, 2] <= 8.0 * beta0 * (1 + 1e-9)) and np.all(to[:, 2] <= 8.0 * beta0 * (1 + 1e-12))
+    diff = np.where((np.abs(tg[:n, 2] / to[:n, 2] - 1.0) > 1e-9) | (tg[:n, 3] != to[:n, 3]))[0]
+    first = int(diff[0]) if diff.size else n
+    assert first >= min(n, 100), first
+    t.close()

@@ -53,7 +53,7 @@ def _pair(te, inst, iters, **kw):
     res = t.solve(iters)
     okw = {k: v for k, v in kw.items() if k in ("alpha_target", "alpha_start", "alpha_step", "alpha_max",
                                                "gamma", "gamma_max", "A", "C", "beta0", "adapt_beta",
-                                               "continuation", "balance_floor")}
+                                               "continuation", "balance_floor", "beta_max")}
     s = O.OracleSolver(inst, **okw)
     s.run(iters)
     return t, res, s

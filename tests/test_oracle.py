@@ -285,15 +285,15 @@ def test_oracle_structs_match_ctypes_mirrors():
     lib = O._L()
     lib.or_echo_options.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
     lib.or_echo_scalars.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
-    vals = [1.5, 2.5, 3.5, 4.5, 5.5, 6.5, 7.5, 8.5, 9.5, 10.5, 11, 12, 13, 14]
+    vals = [1.5, 2.5, 3.5, 4.5, 5.5, 6.5, 7.5, 8.5, 9.5, 10.5, 11.5, 12, 13, 14, 15]
     o = O._Opts(*vals)
-    out = np.zeros(15)
+    out = np.zeros(16)
     lib.or_echo_options(ctypes.byref(o), out.ctypes.data)
-    assert out[:14].tolist() == vals and out[14] == ctypes.sizeof(O._Opts)
-    sc = O._Scalars(1.25, 2.25, 3.25, 7, 8, 1, 0)
-    out = np.zeros(7)
+    assert out[:15].tolist() == vals and out[15] == ctypes.sizeof(O._Opts)
+    sc = O._Scalars(1.25, 2.25, 3.25, 4.25, 7, 8, 1, 0)
+    out = np.zeros(8)
     lib.or_echo_scalars(ctypes.byref(sc), out.ctypes.data)
-    assert out[:6].tolist() == [1.25, 2.25, 3.25, 7, 8, 1] and out[6] == ctypes.sizeof(O._Scalars)
+    assert out[:7].tolist() == [1.25, 2.25, 3.25, 4.25, 7, 8, 1] and out[7] == ctypes.sizeof(O._Scalars)
 
 
 def test_max_norm_primal_residual_bounds_overload_at_stop(tiny):

@@ -63,3 +63,33 @@ def test_zero_iterations_closed_form(tiny, alpha):
     assert abs(J - float(np.sum(O.utility(tiny.demand, alpha)))) <= 1e-12 * abs(J)
     assert np.abs(gC).max() == 0.0
     assert np.allclose(gD, tiny.demand ** (-alpha), rtol=1e-14, atol=0)
+
+
+def _fd_golden():
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fd_medium_alpha1_K200.json")
+    return json.load(open(path))
+
+
+def test_oracle_adjoint_matches_central_differences_medium():
+    """The differentiated configuration (200-node workload, alpha = 1, K = 200,
+    checkpoints every 20): the oracle's reverse pass against FP64 central
+    differences at relative step 1e-3 on 50 seeded coordinates
+    (tests/golden/fd_medium_alpha1_K200.json, written by
+    tests/golden/make_fd_medium.py from the oracle's forward runs).  The map
+    after K iterations is piecewise smooth (active paths, binding caps and
+    positive prices switch), so a step of 1e-3 can cross a kink: every
+    coordinate agrees within 2e-3 of the largest derivative, and the typical
+    one (the median) to the differences' truncation error."""
+    from paper_2605_01748_b300 import instances
+    d = _fd_golden()
+    inst = instances.make_medium(seed=0)
+    J, gC, gD = O.gradient(inst, d["alpha"], d["beta0"], d["K"], checkpoint=20)
+    assert abs(J - d["J"]) <= 1e-9 * abs(d["J"])
+    fd = np.array([c["fd"] for c in d["coords"]])
+    g = np.array([gC[c["index"]] if c["kind"] == "C" else gD[c["index"]] for c in d["coords"]])
+    scale = np.max(np.abs(fd))
+    assert np.max(np.abs(g - fd)) <= 2e-3 * scale
+    rel = np.abs(g - fd) / np.maximum(np.abs(fd), 1e-3 * scale)
+    assert np.median(rel) <= 1e-5

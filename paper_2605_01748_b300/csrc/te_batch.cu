@@ -125,8 +125,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5;
     WarpStage ws;
-    ws.buf[0] = stage + (size_t)(warp * 2) * kStageRows * kLanes;
-    ws.buf[1] = stage + (size_t)(warp * 2 + 1) * kStageRows * kLanes;
+    ws.base = stage + (size_t)(warp * 2) * kStageRows * kLanes;
     bool failed = false;
     __syncthreads();
 

@@ -71,8 +71,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     const int nbc = blockIdx.x < (unsigned)b_hi ? (b_hi - (int)blockIdx.x + NG - 1) / NG : 0;
     const uint16_t* ids = static_cast<const uint16_t*>(a.L.ids);
     WarpStage ws;
-    ws.buf[0] = stage + (size_t)(warp * 2) * kIterStageRows * kLanes;
-    ws.buf[1] = stage + (size_t)(warp * 2 + 1) * kIterStageRows * kLanes;
+    ws.base = stage + (size_t)(warp * 2) * kIterStageRows * kLanes;
 
     for (int e = tid; e < E; e += kIterThreads) {
         w_s[e] = a.w[e];

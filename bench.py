@@ -71,7 +71,7 @@ def parse():
                     help="max-norm primal residual bar of the OPT reference run (0: off)")
     ap.add_argument("--ref-beta-max", type=float, default=4096.0,
                     help="bound on beta of the OPT reference run, times beta0")
-    ap.add_argument("--ref-k", type=int, default=9050,
+    ap.add_argument("--ref-k", type=int, default=7975,
                     help="reference arm on the large workload: iterations the oracle is extrapolated to "
                          "(the CUDA arm's measured count to 1%%)")
     ap.add_argument("--no-k1-check", action="store_true",

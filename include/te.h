@@ -299,8 +299,10 @@ te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint_every, dou
 /* Many TE instances that share the topology's edge numbering but have their
  * own path sets (e.g. paths through failed links removed), demands and
  * capacities, solved together: each instance runs Algorithm 1 (with the same
- * options) on its own, one instance per CTA, all in one launch captured in a
- * CUDA graph.  Not in the paper, which solves one instance at a time; the
+ * options) on its own, all in one launch.  With at least twice as many SMs as
+ * instances, te_solve's iteration kernel runs them with SMs / n CTAs each;
+ * otherwise a batch kernel runs one instance per CTA, captured in a CUDA
+ * graph.  Not in the paper, which solves one instance at a time; the
  * per-instance iteration is the same as te_solve's. */
 typedef struct te_batch te_batch;
 
@@ -310,6 +312,10 @@ typedef struct {
     int64_t device_bytes, kernel_launches;
     int32_t warps_per_cta, ctas_per_sm;  /* CTA shape chosen by the first te_batch_solve (0 before) */
     int32_t lanes_per_demand;
+    int32_t ctas_per_instance;  /* > 0: the instances run in one launch of te_solve's iteration
+                                   kernel with this many CTAs each (chosen at te_batch_create
+                                   when there are at most half as many instances as SMs);
+                                   0: the batch kernel, one instance per CTA */
 } te_batch_info_t;
 
 /* Copies n instances (paths[i], demands[i] [paths[i]->n_demands], capacities[i]

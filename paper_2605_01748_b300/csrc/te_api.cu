@@ -335,10 +335,6 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     if ((st = h->cuda(te::iter_occupancy(G, opt.deterministic != 0, E, nsm, &bps), "occupancy query"))) return bail(st);
     if (bps < 1) { h->err = "iteration kernel does not fit on an SM"; return bail(TE_EUNSUPPORTED); }
     h->grid = nsm * bps;
-    if ((E + h->grid - 1) / h->grid > te::kIterThreads) {  // one edge of a CTA's price slice per thread
-        h->err = "too many edges per CTA price slice";
-        return bail(TE_EUNSUPPORTED);
-    }
 
     // ---------------- device memory ----------------
     void* d_ids;

@@ -348,6 +348,17 @@ struct te_batch {
     long long bytes_per_iter = 0, device_bytes = 0, launches = 0;
     long long timeout_ns = 2000000000LL;
     int shape_w = 0, shape_ctas = 0;    // chosen CTA shape (0: not yet tuned)
+    // fewer instances than half the SMs: the iteration kernel of te_solve runs
+    // them all in one cooperative launch, `group` CTAs per instance (0: the
+    // batch kernel, one instance per CTA)
+    int group = 0;
+    unsigned* hops = nullptr;           // [blocks*32] per layout, for the iteration kernel
+    float *u_next = nullptr, *w_next = nullptr;  // [n][E]
+    uint2* gloads = nullptr;            // [n][group][E] per-CTA partial loads
+    double* gpart = nullptr;            // [n][2][group][kPartWidth]
+    unsigned* gbar = nullptr;           // [n] barrier counters
+    te::IterArgs* d_args = nullptr;     // [n]
+    std::vector<te::IterArgs> h_args;
     std::vector<float> shape_ms;
     std::map<long long, cudaGraphExec_t> graphs;
     std::vector<void*> owned;
@@ -665,6 +676,27 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     A(b->alloc(&b->ps.prefix, sizeof(unsigned long long) * E));
     A(b->alloc(&b->ps.rem, sizeof(double) * E));
     A(b->alloc(&b->ps.Cp, maxNS));
+    A(b->alloc(&b->hops, sizeof(unsigned) * (size_t)metas * kLanes));
+    // one cooperative launch of the iteration kernel with `group` CTAs per
+    // instance when there are fewer instances than half the SMs (one
+    // instance per CTA would leave SMs idle)
+    if (2 * n <= nsm) {
+        const int g = nsm / n;
+        int occ = 0;
+        if (te::iter_smem_bytes(E, g, true) <= 227 * 1024 &&
+            te::iter_occupancy(G, true, E, g, &occ) == cudaSuccess && occ >= 1)
+            b->group = g;
+        cudaGetLastError();
+    }
+    if (b->group > 0) {
+        const size_t g = (size_t)b->group;
+        A(b->alloc(&b->u_next, sizeof(float) * (size_t)n * E));
+        A(b->alloc(&b->w_next, sizeof(float) * (size_t)n * E));
+        A(b->alloc(&b->gloads, sizeof(uint2) * (size_t)n * g * E));
+        A(b->alloc(&b->gpart, sizeof(double) * (size_t)n * 2 * g * te::kPartWidth));
+        A(b->alloc(&b->gbar, sizeof(unsigned) * (size_t)n));
+        A(b->alloc(&b->d_args, sizeof(te::IterArgs) * (size_t)n));
+    }
     if (ce != cudaSuccess) {
         b->err = std::string("device allocation failed: ") + cudaGetErrorString(ce);
         cudaGetLastError();
@@ -681,6 +713,8 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
                           cudaMemcpyHostToDevice, s));
         A(cudaMemcpyAsync(b->rowoff + lro[j], H.rowoff.data(), sizeof(unsigned) * H.rowoff.size(), cudaMemcpyHostToDevice, s));
         A(cudaMemcpyAsync(b->slotbase + lso[j], H.slotbase.data(), sizeof(int) * H.slotbase.size(), cudaMemcpyHostToDevice, s));
+        A(cudaMemcpyAsync(b->hops + (size_t)lmeta0[j] * kLanes, H.hops.data(), sizeof(unsigned) * H.hops.size(),
+                          cudaMemcpyHostToDevice, s));
         A(cudaMemcpyAsync(b->np + (size_t)lmeta0[j] * b->dpb, H.np.data(), nd, cudaMemcpyHostToDevice, s));
         A(cudaMemcpyAsync(b->demand_of + (size_t)lmeta0[j] * b->dpb, H.demand_of.data(), sizeof(int) * nd,
                           cudaMemcpyHostToDevice, s));
@@ -731,7 +765,7 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
         V.rowoff = b->rowoff + lro[j];
         V.slotbase = b->slotbase + lso[j];
         V.blkmeta = b->blkmeta + lmeta0[j];
-        V.hops = nullptr;  // the batch kernel counts hops in its gather
+        V.hops = b->hops + (size_t)lmeta0[j] * kLanes;  // for the iteration kernel (the batch kernel counts hops)
         V.Dn = b->Dn + I.dslot0;
         V.np = b->np + (size_t)lmeta0[j] * b->dpb;
         V.demand_of = b->demand_of + (size_t)lmeta0[j] * b->dpb;
@@ -795,6 +829,42 @@ cudaError_t batch_launch(te_batch* b, long long iters, int W, int ctas) {
     return te::launch_batch(b->G, W, batch_args(b, iters), ctas, b->nsm, s);
 }
 
+// The instances in one cooperative launch of the iteration kernel, `group`
+// CTAs each, for up to iters iterations each.
+cudaError_t grouped_launch(te_batch* b, long long iters) {
+    cudaStream_t s = b->stream;
+    const int n = b->n, E = b->E, g = b->group;
+    b->h_args.resize(n);
+    for (int i = 0; i < n; ++i) {
+        te::IterArgs a{};
+        a.L = b->views[i];
+        a.o = b->o;
+        a.x = b->x + (size_t)b->inst[i].slot0 * kLanes;
+        a.xstride = b->total_slots * kLanes;
+        a.u = b->u + (size_t)i * E;
+        a.w = b->w + (size_t)i * E;
+        a.u_next = b->u_next + (size_t)i * E;
+        a.w_next = b->w_next + (size_t)i * E;
+        a.loads = b->gloads + (size_t)i * g * E;
+        a.part = b->gpart + (size_t)i * 2 * g * te::kPartWidth;
+        a.barrier = b->gbar + i;
+        a.status = b->status;
+        a.sc = b->sc + i;
+        a.trace = nullptr;
+        a.trace_cap = 0;
+        a.lam = b->lam + b->inst[i].dslot0;
+        a.max_iters = iters;
+        a.timeout_ns = b->timeout_ns;
+        b->h_args[i] = a;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_args, b->h_args.data(), sizeof(te::IterArgs) * n, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->gbar, 0, sizeof(unsigned) * n, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    b->launches += 1;
+    return te::launch_iter_grouped(b->d_args, n, g, b->G, E, s);
+}
+
 }  // namespace
 
 extern "C" te_status te_batch_solve(te_batch* b, int64_t max_iters, te_solve_result* results) {
@@ -804,6 +874,11 @@ extern "C" te_status te_batch_solve(te_batch* b, int64_t max_iters, te_solve_res
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
     const std::vector<te::Scalars> before = b->hsc;
     long long left = max_iters;
+    if (b->group > 0) {
+        // the host copy of h_args stays alive until the stream synchronises below
+        if (left > 0) A(grouped_launch(b, left));
+        left = 0;
+    }
     // first call: time each CTA shape on the batch's own first iterations
     if (b->shape_w == 0 && left > 0) {
         float best = 0.f;
@@ -918,8 +993,9 @@ extern "C" te_status te_batch_info(const te_batch* b, te_batch_info_t* info) {
     info->bytes_per_iter = b->bytes_per_iter;
     info->device_bytes = b->device_bytes;
     info->kernel_launches = b->launches;
-    info->warps_per_cta = b->shape_w;
-    info->ctas_per_sm = b->shape_ctas;
+    info->warps_per_cta = b->group > 0 ? te::kIterWarps : b->shape_w;
+    info->ctas_per_sm = b->group > 0 ? 1 : b->shape_ctas;
     info->lanes_per_demand = b->G;
+    info->ctas_per_instance = b->group;
     return TE_OK;
 }

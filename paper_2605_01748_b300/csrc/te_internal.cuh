@@ -123,6 +123,7 @@ struct IterArgs {
     float* lam;            // [nblocks*dpb] previous multiplier lambda = beta*nu of each demand
     long long max_iters;
     long long timeout_ns;  // bound on every wait (the grid barriers)
+    long long xstride;     // floats between the two rate buffers (0: nslots*32)
 };
 
 // Device status codes (mirror te_status).
@@ -133,6 +134,10 @@ constexpr int kStatusNumeric = 5;
 size_t iter_smem_bytes(int E, int grid, bool det);
 cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_per_sm);
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st);
+// Several independent instances in one cooperative launch of the iteration
+// kernel (deterministic loads): instance i runs on CTAs i*group ..
+// i*group+group-1 with the arguments args_dev[i] (device array of n).
+cudaError_t launch_iter_grouped(const IterArgs* args_dev, int n, int group, int G, int E, cudaStream_t st);
 cudaError_t launch_init_x(const Layout& L, float* x, cudaStream_t st);
 
 // Feasibility projection (Algorithm 2) of a copy x (sliced layout, in place).

@@ -44,11 +44,23 @@ namespace {
 
 // DET: exact split fixed-point load histograms (two 32-bit integer atomics
 // per incidence); else one FP32 histogram (one FP32 atomic per incidence).
-template <int G, bool DET>
-__global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
+// GROUPED: the grid runs several independent instances, `group` CTAs each:
+// CTA c takes instance c / group, whose arguments it reads from group_args
+// (each instance has its own barrier counter, scalars and scratch); else the
+// whole grid runs the one instance of a_param.
+template <int G, bool DET, bool GROUPED>
+__global__ void __launch_bounds__(kIterThreads, 1)
+    k_iter(IterArgs a_param, const IterArgs* __restrict__ group_args, int group) {
     extern __shared__ __align__(128) unsigned smem[];
+    __shared__ IterArgs s_args;
+    if (GROUPED) {
+        if (threadIdx.x == 0) s_args = group_args[blockIdx.x / group];
+        __syncthreads();
+    }
+    const IterArgs& a = GROUPED ? s_args : a_param;
     const int E = a.L.E;
-    const int NG = gridDim.x;  // CTAs in the grid
+    const int NG = GROUPED ? group : (int)gridDim.x;  // CTAs of this instance
+    const int cta = GROUPED ? (int)(blockIdx.x % group) : (int)blockIdx.x;  // this CTA's rank among them
     // dynamic shared memory: histogram, gather weights, staging, price slice
     unsigned* h_hi = smem;                                           // [E+1] units of 2^-12 (DET), else FP32
     unsigned* h_lo = DET ? h_hi + (E + 1) : nullptr;                 // [E+1] units of 2^-24 (DET)
@@ -56,7 +68,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     uint16_t* stage = reinterpret_cast<uint16_t*>(
         reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) & ~uintptr_t(127));  // [warps][2][kIterStageRows*32]
     float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kIterStageRows * kLanes);  // price slice
-    const int e_lo = (int)((long long)blockIdx.x * E / NG), e_hi = (int)((long long)(blockIdx.x + 1) * E / NG);
+    const int e_lo = (int)((long long)cta * E / NG), e_hi = (int)((long long)(cta + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
     __shared__ double s_wred[kIterWarps][4];  // per-warp FP64 partials of the residual sums
     __shared__ float s_wmax[kIterWarps];      // per-warp largest relative capacity violation
@@ -65,10 +77,10 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     __shared__ int s_ctl;        // control decision: bit 0 numeric failure, bit 1 stop
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // blocks of this CTA: blockIdx.x, blockIdx.x + NG, ... (round robin, so
+    // blocks of this CTA: cta, cta + NG, ... (round robin, so
     // that every CTA gets a sample of all kinds of blocks)
     const int b_hi = a.L.nblocks;  // block indices >= b_hi mean "none"
-    const int nbc = blockIdx.x < (unsigned)b_hi ? (b_hi - (int)blockIdx.x + NG - 1) / NG : 0;
+    const int nbc = cta < b_hi ? (b_hi - cta + NG - 1) / NG : 0;
     const uint16_t* ids = static_cast<const uint16_t*>(a.L.ids);
     WarpStage ws;
     ws.base = stage + (size_t)(warp * 2) * kIterStageRows * kLanes;
@@ -102,7 +114,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     if (tid == 0) publish_params();
     __syncthreads();
 
-    const size_t xstride = (size_t)a.L.nslots * kLanes;
+    const size_t xstride = a.xstride > 0 ? (size_t)a.xstride : (size_t)a.L.nslots * kLanes;
     long long done = 0;
 
     for (long long it = 0; it < a.max_iters; ++it) {
@@ -115,20 +127,20 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
         const float inv_alpha = s_par[4];
 
         // ---------------- phase A: per-demand rate updates ----------------
-        // The warps share the blocks of this CTA (blockIdx.x, blockIdx.x +
+        // The warps share the blocks of this CTA (cta, cta +
         // NG, ...) in a fixed interleave, so a run is deterministic (the
         // loads are integer sums, and each lane sums the residual terms of
         // its warp's blocks, compensated, in the order of the interleave).
         LaneRes acc;
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.hops, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows, true, true, DET>((int)blockIdx.x, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
+            run_blocks<G, kIterStageRows, true, true, DET>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
                                                 h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         __syncthreads();
         // publish this CTA's partial loads
         if (DET) {
-            uint2* Lp = a.loads + (size_t)blockIdx.x * E;
+            uint2* Lp = a.loads + (size_t)cta * E;
             #pragma unroll 4
             for (int e = tid; e < E; e += kIterThreads) {
                 __stcg(&Lp[e], make_uint2(h_hi[e], h_lo[e]));
@@ -136,7 +148,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 h_lo[e] = 0u;
             }
         } else {
-            float* Lp = reinterpret_cast<float*>(a.loads) + (size_t)blockIdx.x * E;
+            float* Lp = reinterpret_cast<float*>(a.loads) + (size_t)cta * E;
             const float* hf = reinterpret_cast<const float*>(h_hi);
             #pragma unroll 4
             for (int e = tid; e < E; e += kIterThreads) {
@@ -169,26 +181,26 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                     v1 += s_wred[w][1];
                     v2 += s_wred[w][2];
                 }
-                double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * kPartWidth;
+                double* p = a.part + ((size_t)(it & 1) * NG + cta) * kPartWidth;
                 __stcg(&p[0], v0);
                 __stcg(&p[1], v1);
                 __stcg(&p[2], v2);
             }
         }
         if (!grid_sync(a.barrier, (unsigned)((2 * it + 1) * NG), a.status, a.timeout_ns,
-                       (int)blockIdx.x != a.o.withhold_cta)) {
+                       cta != a.o.withhold_cta)) {
             failed = true;
             break;
         }
 
         // ---------------- phase B: this CTA's slice of the edge prices ----------------
         {
-            // L_e of the slice: the CTAs' integer partials summed exactly in
-            // 64 bits (DET: so L_e does not depend on how blocks are spread
-            // over CTAs) and converted once, or the CTAs' FP32 partials summed
-            // in FP64 in CTA order; thread t adds the partials of CTAs
-            // c = t / ns, t / ns + kIterThreads / ns, ... for edge e_lo + t % ns
-            const int ns = e_hi - e_lo;
+            // L_e of the slice, in chunks of at most kIterThreads edges: the
+            // CTAs' integer partials summed exactly in 64 bits (DET: so L_e
+            // does not depend on how blocks are spread over CTAs) and
+            // converted once, or the CTAs' FP32 partials summed in FP64 in CTA
+            // order; thread t adds the partials of CTAs c = t / ns,
+            // t / ns + kIterThreads / ns, ... for edge c0 + t % ns of the chunk
             // [2][kIterThreads] in the staging buffers, idle in phase B
             // (every copy of phase A has landed; the next are issued after
             // the control section's barrier)
@@ -197,12 +209,15 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                           "the phase-B partial sums fit the staging buffers");
             unsigned long long* s_L = reinterpret_cast<unsigned long long*>(stage);
             double* s_Ld = reinterpret_cast<double*>(stage);
-            if (ns > 0) {
-                const int per = kIterThreads / ns > 0 ? kIterThreads / ns : 1;
+            KSum r2;
+            float vmax = 0.f;  // largest relative capacity violation n_e |d_e| / C_e of the slice
+            for (int c0 = e_lo; c0 < e_hi; c0 += kIterThreads) {
+                const int ns = min(kIterThreads, e_hi - c0);
+                const int per = kIterThreads / ns;
                 if (DET) {
                     unsigned long long sh = 0ull, sl = 0ull;
                     if (tid < per * ns) {
-                        const int e = e_lo + tid % ns;
+                        const int e = c0 + tid % ns;
                         #pragma unroll 4
                         for (int c = tid / ns; c < NG; c += per) {
                             const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
@@ -216,7 +231,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                     const float* Lf = reinterpret_cast<const float*>(a.loads);
                     double sf = 0.0;
                     if (tid < per * ns) {
-                        const int e = e_lo + tid % ns;
+                        const int e = c0 + tid % ns;
                         #pragma unroll 4
                         for (int c = tid / ns; c < NG; c += per) sf += (double)__ldcg(&Lf[(size_t)c * E + e]);
                     }
@@ -239,23 +254,23 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                     }
                 }
                 __syncthreads();
-            }
-            KSum r2;
-            float vmax = 0.f;  // largest relative capacity violation n_e |d_e| / C_e of the slice
-            for (int e = e_lo + tid; e < e_hi; e += kIterThreads) {
-                const float ne = __ldg(&a.L.ne_f[e]);
-                const float u = s_u[e - e_lo];
-                const float L = DET ? (float)((double)s_L[e - e_lo] * 0x1p-12 + (double)s_L[kIterThreads + e - e_lo] * 0x1p-24)
-                                    : (float)s_Ld[e - e_lo];
-                float un = 0.f;
-                const float cap = __ldg(&a.L.cap_n[e]);
-                if (ne > 0.f) un = fmaxf(0.f, fmaf(L - cap, __ldg(&a.L.inv_ne[e]), u));
-                const float d = un - u;
-                r2.add(ne * d * d);
-                if (ne > 0.f) vmax = fmaxf(vmax, __fdiv_ru(ne * fabsf(d), cap));
-                s_un[e - e_lo] = un;
-                __stcg(&a.u_next[e], un);
-                __stcg(&a.w_next[e], un + d);
+                if (tid < ns) {
+                    const int e = c0 + tid;
+                    const float ne = __ldg(&a.L.ne_f[e]);
+                    const float u = s_u[e - e_lo];
+                    const float L = DET ? (float)((double)s_L[tid] * 0x1p-12 + (double)s_L[kIterThreads + tid] * 0x1p-24)
+                                        : (float)s_Ld[tid];
+                    float un = 0.f;
+                    const float cap = __ldg(&a.L.cap_n[e]);
+                    if (ne > 0.f) un = fmaxf(0.f, fmaf(L - cap, __ldg(&a.L.inv_ne[e]), u));
+                    const float d = un - u;
+                    r2.add(ne * d * d);
+                    if (ne > 0.f) vmax = fmaxf(vmax, __fdiv_ru(ne * fabsf(d), cap));
+                    s_un[e - e_lo] = un;
+                    __stcg(&a.u_next[e], un);
+                    __stcg(&a.w_next[e], un + d);
+                }
+                __syncthreads();  // the next chunk reuses s_L
             }
             double t3 = r2.value();
             #pragma unroll
@@ -275,7 +290,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                     v3 += s_wred[w][3];
                     m = fmaxf(m, s_wmax[w]);
                 }
-                double* p = a.part + ((size_t)(it & 1) * NG + blockIdx.x) * kPartWidth;
+                double* p = a.part + ((size_t)(it & 1) * NG + cta) * kPartWidth;
                 __stcg(&p[3], v3);
                 __stcg(&p[4], (double)m);
             }
@@ -325,7 +340,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 }
                 if (!numeric_ok) {
                     ctl = 1;
-                    if (blockIdx.x == 0) atomicCAS(a.status, 0, kStatusNumeric);
+                    if (cta == 0) atomicCAS(a.status, 0, kStatusNumeric);
                 } else if (r_res <= a.o.gamma && s_res <= a.o.gamma && (a.o.gamma_max <= 0.0 || v4 <= a.o.gamma_max)) {
                     bool stop = false;
                     if (sc.alpha >= a.o.alpha_target) {
@@ -350,7 +365,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
                 }
                 sc.r = r_res;
                 sc.s = s_res;
-                if (blockIdx.x == 0 && a.trace_cap > 0) {
+                if (cta == 0 && a.trace_cap > 0) {
                     double* t = a.trace + (size_t)((sc.iter_total - 1) % a.trace_cap) * kTraceWidth;
                     t[0] = r_res; t[1] = s_res; t[2] = sc.beta; t[3] = sc.alpha; t[4] = (double)event;
                 }
@@ -376,7 +391,7 @@ __global__ void __launch_bounds__(kIterThreads, 1) k_iter(IterArgs a) {
     }
     __syncthreads();
     for (int e = e_lo + tid; e < e_hi; e += kIterThreads) a.u[e] = s_u[e - e_lo];
-    if (blockIdx.x == 0) {
+    if (cta == 0) {
         for (int e = tid; e < E; e += kIterThreads) a.w[e] = w_s[e];
         if (tid == 0) {
             sc.iters_run = done;
@@ -404,20 +419,36 @@ __global__ void k_init_x(Layout L, float* x) {
 template <int G, bool DET>
 cudaError_t launch_iter_t(const IterArgs& a, int grid, cudaStream_t st) {
     const size_t smem = iter_smem_bytes(a.L.E, grid, DET);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<G, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_iter<G, DET, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     IterArgs args = a;
-    void* params[] = {&args};
-    return cudaLaunchCooperativeKernel((const void*)k_iter<G, DET>, dim3(grid), dim3(kIterThreads), params, smem,
-                                       st);
+    const IterArgs* none = nullptr;
+    int group = 0;
+    void* params[] = {&args, &none, &group};
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G, DET, false>, dim3(grid), dim3(kIterThreads), params,
+                                       smem, st);
+}
+
+template <int G>
+cudaError_t launch_iter_grouped_t(const IterArgs* args_dev, int n, int group, int E, cudaStream_t st) {
+    const size_t smem = iter_smem_bytes(E, group, true);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_iter<G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    IterArgs unused{};
+    void* params[] = {&unused, &args_dev, &group};
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G, true, true>, dim3(n * group), dim3(kIterThreads),
+                                       params, smem, st);
 }
 
 template <int G, bool DET>
 cudaError_t occupancy_t(int E, int grid_hint, int* blocks) {
     const size_t smem = iter_smem_bytes(E, grid_hint, DET);
-    cudaError_t err = cudaFuncSetAttribute(k_iter<G, DET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_iter<G, DET, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G, DET>, kIterThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G, DET, false>, kIterThreads, smem);
 }
 
 }  // namespace
@@ -466,6 +497,15 @@ cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
         case 2: return launch_iter_t<2, false>(a, grid, st);
         case 4: return launch_iter_t<4, false>(a, grid, st);
         default: return launch_iter_t<8, false>(a, grid, st);
+    }
+}
+
+cudaError_t launch_iter_grouped(const IterArgs* args_dev, int n, int group, int G, int E, cudaStream_t st) {
+    switch (G) {
+        case 1: return launch_iter_grouped_t<1>(args_dev, n, group, E, st);
+        case 2: return launch_iter_grouped_t<2>(args_dev, n, group, E, st);
+        case 4: return launch_iter_grouped_t<4>(args_dev, n, group, E, st);
+        default: return launch_iter_grouped_t<8>(args_dev, n, group, E, st);
     }
 }
 

@@ -92,7 +92,8 @@ class te_batch_info_t(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_int64), ("n_paths", ctypes.c_int64), ("id_rows", ctypes.c_int64),
                 ("bytes_per_iter", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("warps_per_cta", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("lanes_per_demand", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("lanes_per_demand", ctypes.c_int32),
+                ("ctas_per_instance", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

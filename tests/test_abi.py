@@ -94,7 +94,8 @@ def test_options_struct_matches_header(te, tmp_path):
     the C header's size and field offsets (compiled here with gcc)."""
     fields = {"te_options": [f for f, _ in te.te_options._fields_],
               "te_solve_result": [f for f, _ in te.te_solve_result._fields_],
-              "te_layout_info": [f for f, _ in te.te_layout_info._fields_]}
+              "te_layout_info": [f for f, _ in te.te_layout_info._fields_],
+              "te_batch_info_t": [f for f, _ in te.te_batch_info_t._fields_]}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "te.h"', 'int main(void) {']
     for st, fs in fields.items():
         lines.append(f'printf("{st} %zu\\n", sizeof({st}));')

@@ -33,7 +33,44 @@ def test_batch_matches_oracle_per_instance(te, tiny):
         s.run(150)
         assert _rel(b.allocation(i, project=te.PROJECT_NONE), s.allocation()) <= 1e-4
     info = b.info()
-    assert info["n_instances"] == 6 and info["warps_per_cta"] in (8, 16)
+    # six instances: te_solve's iteration kernel with SMs / 6 CTAs each
+    assert info["n_instances"] == 6 and info["ctas_per_instance"] >= 2 and info["warps_per_cta"] == 20
+    b.close()
+
+
+def test_batch_kernel_one_instance_per_cta_matches_oracle(te, tiny):
+    """More instances than half the SMs: the batch kernel (one instance per
+    CTA, CUDA graph, autotuned CTA shape) against the oracle per instance."""
+    W = instances.make_what_if(tiny, 40, 2, seed=6, min_fail=1, max_fail=2)
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    b = te.TEBatch(W, **kw)
+    res = b.solve(120)
+    info = b.info()
+    assert info["n_instances"] == 80 and info["ctas_per_instance"] == 0 and info["warps_per_cta"] in (8, 16)
+    assert all(r["iters"] == 120 for r in res)
+    for i in (0, 37, 79):
+        s = O.OracleSolver(W[i], **kw)
+        s.run(120)
+        assert _rel(b.allocation(i, project=te.PROJECT_NONE), s.allocation()) <= 1e-4
+    b.close()
+
+
+def test_grouped_batch_matches_single_engine_bit_for_bit(te, medium):
+    """The grouped launch runs te_solve's own iteration kernel on fewer CTAs
+    per instance; the edge loads are exact integer sums, so after a fixed
+    schedule the rates equal the single engine's bit for bit."""
+    W = instances.make_what_if(medium, 2, 1, seed=8)
+    kw = dict(alpha_target=2.0, alpha_start=2.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    b = te.TEBatch(W, **kw)
+    assert b.info()["ctas_per_instance"] >= 2
+    b.solve(50)
+    for i, inst in enumerate(W):
+        t = te.TE(inst, **kw)
+        t.solve(50)
+        xs = t.allocation(project=te.PROJECT_NONE)
+        xb = b.allocation(i, project=te.PROJECT_NONE)
+        assert np.array_equal(xs.view(np.uint32), xb.view(np.uint32))
+        t.close()
     b.close()
 
 

@@ -124,8 +124,10 @@ typedef struct {
                              exact integer sums of fixed-point rates, so a run
                              is bit-identical for a given instance and device;
                              0: one FP32 shared-memory add per path-edge
-                             incidence instead (faster; the loads, and so the
-                             iterates, may differ in the last bits between runs) */
+                             incidence instead of two integer adds (the loads,
+                             and so the iterates, may differ in the last bits
+                             between runs; measured slower on B300, where an
+                             FP32 shared atomic costs more than two integer ones) */
     int32_t precision;    /* arithmetic of the iteration: TE_PRECISION_FP32
                              (the only value; FP32 rates and prices, FP64
                              residual sums, gap and stop test)                */

@@ -688,12 +688,16 @@ static int keyed_cmp(const void* a, const void* b) {
     return (p->path < q->path) ? -1 : (p->path > q->path);
 }
 
-/* log of score_p = alpha log S_c + log C_p (-inf when the score is 0) */
+/* log of score_p = alpha log S_c + log C_p (-inf when the score is 0),
+ * rounded to FP32: the order of Algorithm 2 is a decision taken on a
+ * floating-point score, so it is taken in the CUDA path's precision (the
+ * FP32 key of the FP64 score, S in caller units) and both sides order
+ * near-equal scores alike */
 static double log_score(double S, int64_t Cp, double alpha) {
     if (Cp <= 0) return -INFINITY;
-    if (alpha == 0.0) return log((double)Cp);
+    if (alpha == 0.0) return (double)(float)log((double)Cp);
     if (!(S > 0.0)) return -INFINITY;
-    return alpha * log(S) + log((double)Cp);
+    return (double)(float)(alpha * log(S) + log((double)Cp));
 }
 
 static void proj_aux(const or_instance* I, const double* x, double* S, double* L, int64_t* Cp) {

@@ -562,7 +562,7 @@ extern "C" te_status te_allocation(te_handle* h, float* x_out, int32_t project, 
     if (project != TE_PROJECT_NONE) {
         A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
         if (project == TE_PROJECT_ALG2) {
-            A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
+            A(te::launch_project(h->L, h->xtmp, h->hsc.alpha, h->scale, h->ps, s));
             h->launches += te::kProjectLaunches;
         } else {
             A(te::launch_project_scale(h->L, h->xtmp, h->ps, s));
@@ -589,7 +589,7 @@ extern "C" te_status te_gap_projected(te_handle* h, int32_t project, double* gap
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
     A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
     if (project == TE_PROJECT_ALG2) {
-        A(te::launch_project(h->L, h->xtmp, (float)h->hsc.alpha, h->ps, s));
+        A(te::launch_project(h->L, h->xtmp, h->hsc.alpha, h->scale, h->ps, s));
         h->launches += te::kProjectLaunches;
     } else {
         A(te::launch_project_scale(h->L, h->xtmp, h->ps, s));

@@ -967,7 +967,7 @@ extern "C" te_status te_batch_allocation(te_batch* b, int32_t i, float* x_out, i
     if (project != TE_PROJECT_NONE) {
         A(cudaMemcpyAsync(b->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
         if (project == TE_PROJECT_ALG2) {
-            A(te::launch_project(V, b->xtmp, (float)b->hsc[i].alpha, b->ps, s));
+            A(te::launch_project(V, b->xtmp, b->hsc[i].alpha, b->scale[i], b->ps, s));
             b->launches += te::kProjectLaunches;
         } else {
             A(te::launch_project_scale(V, b->xtmp, b->ps, s));

@@ -155,7 +155,9 @@ struct ProjScratch {
     double* rem;         // [E] remaining violation per violated edge
     unsigned char* Cp;   // [nslots*32] violated edges per path
 };
-cudaError_t launch_project(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st);
+// alpha and scale (the caller-unit scale of x) form the paths' score keys.
+cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, const ProjScratch& s,
+                           cudaStream_t st);
 constexpr int kProjectLaunches = 26;  // kernels launch_project issues
 
 // Proportional feasibility scaling (not in the paper): x <- max(x, 0); every

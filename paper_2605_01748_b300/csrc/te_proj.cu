@@ -18,7 +18,10 @@
 //      index) finds the threshold path at which the running sum of rates in
 //      key order reaches V_e; paths above it are trimmed in full and the
 //      threshold path by the remainder.
-// Scores are compared as alpha*log(S_c) + log(C_p) in FP32.
+// Scores are compared as keys: alpha*log(S_c) + log(C_p) evaluated in FP64
+// with S_c in the caller's units and rounded to FP32 (the oracle forms the
+// same key, so both order the paths alike up to FP64 rounding at an FP32
+// boundary).
 //
 // Edge loads and the radix-select histograms are sums over many paths; they
 // are accumulated as 64-bit integers in units of 2^-40 (normalised
@@ -177,13 +180,15 @@ __device__ __forceinline__ unsigned orderable(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
-// Key of a path: high word = orderable(alpha log S_c + log C_p), low word =
-// inverted caller path index (lower index ranks first among equal scores).
-__device__ __forceinline__ unsigned long long path_key(double S, int Cp, float alpha, long long user_path) {
+// Key of a path: high word = orderable(FP32 of alpha log S_c + log C_p), S_c
+// in caller units (S normalised times scale), low word = inverted caller
+// path index (lower index ranks first among equal scores).
+__device__ __forceinline__ unsigned long long path_key(double S, int Cp, double alpha, double scale,
+                                                      long long user_path) {
     float ls;
     if (Cp <= 0) ls = -INFINITY;
-    else if (alpha == 0.f) ls = logf((float)Cp);
-    else ls = (S > 0.0) ? fmaf(alpha, logf((float)S), logf((float)Cp)) : -INFINITY;
+    else if (alpha == 0.0) ls = (float)log((double)Cp);
+    else ls = (S > 0.0) ? (float)(alpha * log(S * scale) + log((double)Cp)) : -INFINITY;
     return ((unsigned long long)orderable(ls) << 32) | (unsigned long long)(0xffffffffu - (unsigned)user_path);
 }
 
@@ -192,7 +197,7 @@ __device__ __forceinline__ unsigned long long path_key(double S, int Cp, float a
 template <typename IdT>
 __global__ void k_select_hist(Layout L, const float* x, const double* S, const unsigned char* Cp,
                               const int* vidx, const unsigned long long* prefix, const unsigned char* done,
-                              unsigned long long* hist, float alpha, int pass) {
+                              unsigned long long* hist, double alpha, double scale, int pass) {
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -204,7 +209,7 @@ __global__ void k_select_hist(Layout L, const float* x, const double* S, const u
         const float v = x[sl * kLanes + lane];
         const int c = Cp[sl * kLanes + lane];
         if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha,
+        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha, scale,
                                                 L.slot_path[sl * kLanes + lane]);
         const int digit = (int)((key >> shift) & 0xffull);
         const unsigned long long q = fix_down(v);
@@ -254,7 +259,7 @@ __global__ void k_select_pick(const int* nviol, unsigned long long* hist, unsign
 template <typename IdT>
 __global__ void k_edge_trim(Layout L, float* x, const double* S, const unsigned char* Cp, const int* vidx,
                             const unsigned long long* prefix, const double* rem, const unsigned char* done,
-                            float alpha) {
+                            double alpha, double scale) {
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -265,7 +270,7 @@ __global__ void k_edge_trim(Layout L, float* x, const double* S, const unsigned 
         const float v = x[sl * kLanes + lane];
         const int c = Cp[sl * kLanes + lane];
         if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha,
+        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha, scale,
                                                 L.slot_path[sl * kLanes + lane]);
         double trim = 0.0;
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
@@ -381,7 +386,7 @@ cudaError_t project_scale_t(const Layout& L, float* x, const ProjScratch& s, cud
 }
 
 template <typename IdT>
-cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st) {
+cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, const ProjScratch& s, cudaStream_t st) {
     const long long lanes = (long long)L.nblocks * kLanes;
     const unsigned gl = grid_for(lanes, kThreads);
     const unsigned ge = grid_for(L.E, kThreads);
@@ -403,18 +408,20 @@ cudaError_t project_t(const Layout& L, float* x, float alpha, const ProjScratch&
     if ((err = cudaMemsetAsync(s.hist, 0, sizeof(unsigned long long) * 256 * (size_t)L.E, st)) != cudaSuccess)
         return err;
     for (int pass = 0; pass < 8; ++pass) {
-        k_select_hist<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, done, s.hist, alpha, pass);
+        k_select_hist<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, done, s.hist, alpha, scale,
+                                                    pass);
         k_select_pick<<<ge, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);
     }
-    k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, s.rem, done, alpha);
+    k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, s.rem, done, alpha, scale);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_project(const Layout& L, float* x, float alpha, const ProjScratch& s, cudaStream_t st) {
-    if (L.id_bytes == 2) return project_t<uint16_t>(L, x, alpha, s, st);
-    return project_t<int32_t>(L, x, alpha, s, st);
+cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, const ProjScratch& s,
+                           cudaStream_t st) {
+    if (L.id_bytes == 2) return project_t<uint16_t>(L, x, alpha, scale, s, st);
+    return project_t<int32_t>(L, x, alpha, scale, s, st);
 }
 
 cudaError_t launch_project_scale(const Layout& L, float* x, const ProjScratch& s, cudaStream_t st) {

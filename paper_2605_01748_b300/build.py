@@ -72,6 +72,8 @@ def build_te(force: bool = False, verbose: bool = False, out: str = LIBTE) -> st
         cmd += ["-Xptxas", "-v"]
     if os.environ.get("TE_ITER_THREADS"):
         cmd += [f"-DTE_ITER_THREADS={int(os.environ['TE_ITER_THREADS'])}"]
+    if os.environ.get("TE_ITER_STAGE_ROWS"):
+        cmd += [f"-DTE_ITER_STAGE_ROWS={int(os.environ['TE_ITER_STAGE_ROWS'])}"]
     cmd += [os.path.join(CSRC, s) for s in TE_SOURCES]
     cmd += ["-lcudart"]
     _run(cmd, verbose)

@@ -38,7 +38,10 @@ constexpr int kMaxPathsPerLane = 4;
 #endif
 constexpr int kIterThreads = TE_ITER_THREADS;
 constexpr int kIterWarps = kIterThreads / 32;
-constexpr int kIterStageRows = 40;  // rows of 16-bit ids per staging buffer of the iteration kernel
+#ifndef TE_ITER_STAGE_ROWS
+#define TE_ITER_STAGE_ROWS 40
+#endif
+constexpr int kIterStageRows = TE_ITER_STAGE_ROWS;  // rows of 16-bit ids per staging buffer of the iteration kernel
 constexpr int kStageRows = 48;      // the same for the batch kernel (3 KB)
 constexpr int kTraceWidth = 5;
 constexpr int kPartWidth = 8;  // doubles per CTA in IterArgs::part (5 used)

@@ -395,6 +395,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->ps.prefix, sizeof(unsigned long long) * E));
     A(h->alloc(&h->ps.rem, sizeof(double) * E));
     A(h->alloc(&h->ps.Cp, ns));
+    A(h->alloc(&h->ps.score, sizeof(double) * (ND + 256)));
     if (ce != cudaSuccess) {
         h->err = std::string("device allocation failed: ") + cudaGetErrorString(ce);
         cudaGetLastError();

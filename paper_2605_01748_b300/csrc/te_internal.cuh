@@ -157,11 +157,12 @@ struct ProjScratch {
     unsigned long long* prefix;  // [E] selected key prefix per violated edge
     double* rem;         // [E] remaining violation per violated edge
     unsigned char* Cp;   // [nslots*32] violated edges per path
+    double* score;       // [nblocks*dpb + 256] alpha log(S_c scale) per demand, then log(0..255)
 };
 // alpha and scale (the caller-unit scale of x) form the paths' score keys.
 cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, const ProjScratch& s,
                            cudaStream_t st);
-constexpr int kProjectLaunches = 26;  // kernels launch_project issues
+constexpr int kProjectLaunches = 27;  // kernels launch_project issues
 
 // Proportional feasibility scaling (not in the paper): x <- max(x, 0); every
 // demand with S_c > D_c scaled by D_c / S_c; then every path by the smallest

@@ -180,24 +180,35 @@ __device__ __forceinline__ unsigned orderable(float f) {
     return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
+// The two terms of the paths' scores, formed once per projection (FP64
+// logarithms are slow on this part, and the select passes read the keys nine
+// times): score[c] = alpha log(S_c scale) for every demand c (0 for alpha =
+// 0, -inf for S_c = 0), and score[nd + k] = log(k) for k = 0..255 (C_p is a
+// byte).  One thread per demand; the first 256 threads also fill the table.
+__global__ void k_score_terms(Layout L, const double* S, double alpha, double scale, double* score) {
+    const long long nd = (long long)L.nblocks * L.dpb;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < 256) score[nd + i] = log((double)i);
+    if (i >= nd) return;
+    score[i] = alpha == 0.0 ? 0.0 : (S[i] > 0.0 ? alpha * log(S[i] * scale) : -INFINITY);
+}
+
 // Key of a path: high word = orderable(FP32 of alpha log S_c + log C_p), S_c
 // in caller units (S normalised times scale), low word = inverted caller
-// path index (lower index ranks first among equal scores).
-__device__ __forceinline__ unsigned long long path_key(double S, int Cp, double alpha, double scale,
-                                                      long long user_path) {
-    float ls;
-    if (Cp <= 0) ls = -INFINITY;
-    else if (alpha == 0.0) ls = (float)log((double)Cp);
-    else ls = (S > 0.0) ? (float)(alpha * log(S * scale) + log((double)Cp)) : -INFINITY;
+// path index (lower index ranks first among equal scores).  aS is the
+// demand's score term and logc the table of k_score_terms.
+__device__ __forceinline__ unsigned long long path_key(double aS, int Cp, const double* logc, long long user_path) {
+    const float ls = (Cp <= 0 || aS == -INFINITY) ? -INFINITY : (float)(aS + logc[Cp]);
     return ((unsigned long long)orderable(ls) << 32) | (unsigned long long)(0xffffffffu - (unsigned)user_path);
 }
 
 // One radix-select pass: per violated edge, histogram of the rates of the
 // candidate paths (keys matching the selected prefix) by the next 8-bit digit.
 template <typename IdT>
-__global__ void k_select_hist(Layout L, const float* x, const double* S, const unsigned char* Cp,
+__global__ void k_select_hist(Layout L, const float* x, const double* score, const unsigned char* Cp,
                               const int* vidx, const unsigned long long* prefix, const unsigned char* done,
-                              unsigned long long* hist, double alpha, double scale, int pass) {
+                              unsigned long long* hist, int pass) {
+    const double* logc = score + (size_t)L.nblocks * L.dpb;
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -209,7 +220,7 @@ __global__ void k_select_hist(Layout L, const float* x, const double* S, const u
         const float v = x[sl * kLanes + lane];
         const int c = Cp[sl * kLanes + lane];
         if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha, scale,
+        const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], c, logc,
                                                 L.slot_path[sl * kLanes + lane]);
         const int digit = (int)((key >> shift) & 0xffull);
         const unsigned long long q = fix_down(v);
@@ -257,9 +268,9 @@ __global__ void k_select_pick(const int* nviol, unsigned long long* hist, unsign
 // Apply: every path loses the largest trim planned for it by its violated
 // edges.
 template <typename IdT>
-__global__ void k_edge_trim(Layout L, float* x, const double* S, const unsigned char* Cp, const int* vidx,
-                            const unsigned long long* prefix, const double* rem, const unsigned char* done,
-                            double alpha, double scale) {
+__global__ void k_edge_trim(Layout L, float* x, const double* score, const unsigned char* Cp, const int* vidx,
+                            const unsigned long long* prefix, const double* rem, const unsigned char* done) {
+    const double* logc = score + (size_t)L.nblocks * L.dpb;
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -270,7 +281,7 @@ __global__ void k_edge_trim(Layout L, float* x, const double* S, const unsigned 
         const float v = x[sl * kLanes + lane];
         const int c = Cp[sl * kLanes + lane];
         if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(S[(size_t)b * L.dpb + lane / L.G], c, alpha, scale,
+        const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], c, logc,
                                                 L.slot_path[sl * kLanes + lane]);
         double trim = 0.0;
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
@@ -407,12 +418,13 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, con
     if ((err = cudaMemsetAsync(done, 0, (size_t)L.E, st)) != cudaSuccess) return err;
     if ((err = cudaMemsetAsync(s.hist, 0, sizeof(unsigned long long) * 256 * (size_t)L.E, st)) != cudaSuccess)
         return err;
+    k_score_terms<<<grid_for((long long)L.nblocks * L.dpb > 256 ? (long long)L.nblocks * L.dpb : 256, kThreads),
+                    kThreads, 0, st>>>(L, s.S, alpha, scale, s.score);
     for (int pass = 0; pass < 8; ++pass) {
-        k_select_hist<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, done, s.hist, alpha, scale,
-                                                    pass);
+        k_select_hist<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.prefix, done, s.hist, pass);
         k_select_pick<<<ge, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);
     }
-    k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.S, s.Cp, s.vidx, s.prefix, s.rem, done, alpha, scale);
+    k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.prefix, s.rem, done);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,9 @@ def parse():
                          "workloads against their exact max-min (progressive filling), one JSON line each")
     ap.add_argument("--steady", default="", metavar="ALPHAS",
                     help="steady-state us per iteration at these fixed alphas (comma separated), one JSON line")
+    ap.add_argument("--feasibility", type=int, default=0, metavar="K",
+                    help="time the two feasibility steps (Algorithm 2 and proportional scaling, device output) "
+                         "on the iterate after K iterations of the default solver, one JSON line")
     ap.add_argument("--iters", type=int, default=0,
                     help="profiling runs only: use this K and skip the reference run and the probe")
     return ap.parse_args()
@@ -976,11 +979,45 @@ def run_steady(a):
     print(json.dumps({"mode": "steady", "workload": workload_desc(inst), "us_per_iter": row}), flush=True)
 
 
+def run_feasibility(a):
+    """Time of te_allocation with each feasibility step on one iterate (the
+    default solver after a.feasibility iterations): CUDA events on the
+    handle's stream around one call, best of 5 after one warm-up call;
+    device output, so no host copy is timed.  One JSON line."""
+    import torch
+    from paper_2605_01748_b300 import instances, te
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    inst = instances.make(a.workload, threads=os.cpu_count() or 0)
+    t = te.TE(inst, cuda_stream=st.cuda_stream)
+    r = t.solve(a.feasibility)
+    out = torch.empty(t.n_paths, dtype=torch.float32, device=dev)
+    row = {"mode": "feasibility", "workload": workload_desc(inst), "iters": r["iters"], "alpha": r["alpha"]}
+    for name, proj in (("algorithm2", te.PROJECT_ALG2), ("scaling", te.PROJECT_SCALE)):
+        t.allocation(project=proj, out=out)
+        best = math.inf
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(st)
+            t.allocation(project=proj, out=out)
+            e1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        row[name] = {"ms": round(best, 3), "sum_of_rates": float(out.double().sum())}
+    t.close()
+    print(json.dumps(row), flush=True)
+
+
 def main():
     a = parse()
     ws, rank, local, dist = dist_setup()
     if a.steady:
         run_steady(a)
+    elif a.feasibility > 0:
+        run_feasibility(a)
     elif a.exact_k1:
         run_exact_k1(a)
     elif a.batch > 0:

@@ -137,6 +137,23 @@ __global__ void __launch_bounds__(kIterThreads, 1)
             run_blocks<G, kIterStageRows, true, true, DET>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
                                                 h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
+        {
+            // this warp's residual partials: each lane's compensated sums in
+            // FP64, summed over the warp in a fixed butterfly (done here, so
+            // that warps that finish early do it while the others still run)
+            double t0 = acc.d.value(), t1 = (double)acc.x, t2 = (double)acc.e;
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+                t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+            }
+            if (lane == 0) {
+                s_wred[warp][0] = t0;
+                s_wred[warp][1] = t1;
+                s_wred[warp][2] = t2;
+            }
+        }
         __syncthreads();
         // publish this CTA's partial loads
         if (DET) {
@@ -157,23 +174,9 @@ __global__ void __launch_bounds__(kIterThreads, 1)
             }
         }
         {
-            // this CTA's residual partials: each lane's compensated sums in
-            // FP64, summed over the warp in a fixed butterfly and over the
-            // warps in warp order by thread 0 (the blocks of a warp are fixed
-            // by the interleave, so the totals do not depend on timing)
-            double t0 = acc.d.value(), t1 = (double)acc.x, t2 = (double)acc.e;
-            #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-                t2 += __shfl_xor_sync(0xffffffffu, t2, o);
-            }
-            if (lane == 0) {
-                s_wred[warp][0] = t0;
-                s_wred[warp][1] = t1;
-                s_wred[warp][2] = t2;
-            }
-            __syncthreads();
+            // this CTA's residual partials: the warps' sums added in warp
+            // order by thread 0 (the blocks of a warp are fixed by the
+            // interleave, so the totals do not depend on timing)
             if (tid == 0) {
                 double v0 = 0.0, v1 = 0.0, v2 = 0.0;
                 for (int w = 0; w < kIterWarps; ++w) {
@@ -218,7 +221,9 @@ __global__ void __launch_bounds__(kIterThreads, 1)
                     unsigned long long sh = 0ull, sl = 0ull;
                     if (tid < per * ns) {
                         const int e = c0 + tid % ns;
-                        #pragma unroll 4
+                        // all of a thread's partials in flight at once (about NG /
+                        // per of them: one L2 round trip instead of several)
+                        #pragma unroll 16
                         for (int c = tid / ns; c < NG; c += per) {
                             const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
                             sh += v.x;
@@ -308,6 +313,7 @@ __global__ void __launch_bounds__(kIterThreads, 1)
         if (tid < 32) {
             double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0, v4 = 0.0;
             const double* p = a.part + (size_t)(it & 1) * NG * kPartWidth;
+            #pragma unroll 8  // a lane's loads in flight together (NG / 32 rounds of L2 latency otherwise)
             for (int c = lane; c < NG; c += 32) {
                 v0 += __ldcg(&p[c * kPartWidth + 0]);
                 v1 += __ldcg(&p[c * kPartWidth + 1]);
@@ -373,18 +379,22 @@ __global__ void __launch_bounds__(kIterThreads, 1)
                 s_ctl = ctl;
                 publish_params();
             }
+        } else {
+            // meanwhile the other warps load the next gather weights w = u'
+            // + d (w_s is not read again before phase A)
+            #pragma unroll 4
+            for (int e = tid - 32; e < E; e += kIterThreads - 32) w_s[e] = __ldcg(&a.w_next[e]);
         }
         __syncthreads();
-        // commit the slice's new prices (scaled with beta) and the new gather
-        // weights w = u' + d (the rescale keeps d, a primal quantity)
+        // commit the slice's new prices (scaled with beta); when beta changed,
+        // rescale the gather weights' price part: w = ratio u' + d = w +
+        // (ratio - 1) u' (the rescale keeps d, a primal quantity)
         const float ratio = s_ratio;
         const int ctl = s_ctl;
         for (int e = e_lo + tid; e < e_hi; e += kIterThreads) s_u[e - e_lo] = s_un[e - e_lo] * ratio;
-        #pragma unroll 4
-        for (int e = tid; e < E; e += kIterThreads) {
-            float w = __ldcg(&a.w_next[e]);
-            if (ratio != 1.f) w = fmaf(__ldcg(&a.u_next[e]), ratio - 1.f, w);
-            w_s[e] = w;
+        if (ratio != 1.f) {
+            #pragma unroll 4
+            for (int e = tid; e < E; e += kIterThreads) w_s[e] = fmaf(__ldcg(&a.u_next[e]), ratio - 1.f, w_s[e]);
         }
         __syncthreads();
         if (ctl != 0) break;  // numeric failure (status set) or the stop rule fired

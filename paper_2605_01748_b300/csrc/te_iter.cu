@@ -278,10 +278,12 @@ __global__ void __launch_bounds__(kIterThreads, 1)
                 __syncthreads();  // the next chunk reuses s_L
             }
             double t3 = r2.value();
-            #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                t3 += __shfl_xor_sync(0xffffffffu, t3, o);
-                vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+            if (warp * 32 < min(kIterThreads, e_hi - e_lo)) {  // the other warps hold no edge: 0
+                #pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    t3 += __shfl_xor_sync(0xffffffffu, t3, o);
+                    vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+                }
             }
             if (lane == 0) {
                 s_wred[warp][3] = t3;
@@ -377,12 +379,12 @@ __global__ void __launch_bounds__(kIterThreads, 1)
                 }
                 s_ratio = ratio;
                 s_ctl = ctl;
-                publish_params();
+                if (event & 3) publish_params();  // beta or alpha changed (FP64 log and quotient)
             }
         } else {
             // meanwhile the other warps load the next gather weights w = u'
             // + d (w_s is not read again before phase A)
-            #pragma unroll 4
+            #pragma unroll 16
             for (int e = tid - 32; e < E; e += kIterThreads - 32) w_s[e] = __ldcg(&a.w_next[e]);
         }
         __syncthreads();

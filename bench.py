@@ -256,7 +256,7 @@ def ncu_traffic(workload: str):
     return float(rec["dram_bytes_per_iteration"]), os.path.relpath(NCU_TRAFFIC_JSON, ROOT)
 
 
-def survey_bytes(inst, grid: int) -> int:
+def method_bytes(inst, grid: int) -> int:
     """Algorithmic bytes of one iteration by the per-unit figures of the
     method's traffic with int32 edge ids: 4 B per incidence (the path-edge
     ids), 12 B per path (its rate read and written, its offset), 8 B per
@@ -463,7 +463,7 @@ def run_ours(a, ws, rank, local, dist):
     ms_step, e2e_mean = max_over_ranks([ms_step, statistics.mean(e2e_ms)], dist, dev)
 
     solve_mean = statistics.mean(solve_ms)
-    alg_bytes = survey_bytes(inst, lay["grid"])
+    alg_bytes = method_bytes(inst, lay["grid"])
     achieved = alg_bytes * K / (solve_mean * 1e-3) / 1e9
     moved = lay["bytes_per_iter"] * K / (solve_mean * 1e-3) / 1e9
     traffic_iter, traffic_src = ncu_traffic(a.workload)

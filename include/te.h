@@ -202,8 +202,13 @@ enum {
  * steps sum in FP64 and round their trims and factors toward zero, so the
  * FP32 result satisfies the constraints up to the FP32 rounding of the
  * conversion to caller units.  out_is_device selects whether x_out is a
- * device or a host pointer.  Errors: TE_EINVAL (NULL pointer, unknown
- * project), TE_ECUDA. */
+ * device or a host pointer.  With TE_PROJECT_ALG2 the handle keeps a list of
+ * the violated path-edge incidences (16 bytes each), allocated on the first
+ * call that needs it, grown when a later call needs more and freed by
+ * te_destroy (so the call may allocate device memory; te_gap and
+ * te_gap_projected with TE_PROJECT_ALG2 as well).  Errors: TE_EINVAL (NULL
+ * pointer, unknown project), TE_ECUDA (also when that list cannot be
+ * allocated). */
 te_status te_allocation(te_handle* h, float* x_out, int32_t project, int32_t out_is_device);
 
 /* Duality gap of the projected allocation x^ (caller units, FP64): the

@@ -168,6 +168,7 @@ void te_destroy(te_handle* h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (void* p : h->owned) cudaFree(p);
+    if (h->ps.vlist) cudaFree(h->ps.vlist);
     cudaSetDevice(cur);
     delete h;
 }
@@ -396,6 +397,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->ps.rem, sizeof(double) * E));
     A(h->alloc(&h->ps.Cp, ns));
     A(h->alloc(&h->ps.score, sizeof(double) * (ND + 256)));
+    A(h->alloc(&h->ps.vtotal, 2 * sizeof(unsigned long long)));
     if (ce != cudaSuccess) {
         h->err = std::string("device allocation failed: ") + cudaGetErrorString(ce);
         cudaGetLastError();

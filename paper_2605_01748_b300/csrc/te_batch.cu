@@ -414,6 +414,7 @@ extern "C" void te_batch_destroy(te_batch* b) {
     if (!b) return;
     for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
     for (void* p : b->owned) cudaFree(p);
+    if (b->ps.vlist) cudaFree(b->ps.vlist);
     if (b->own_stream) cudaStreamDestroy(b->own_stream);
     delete b;
 }
@@ -677,6 +678,7 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     A(b->alloc(&b->ps.rem, sizeof(double) * E));
     A(b->alloc(&b->ps.Cp, maxNS));
     A(b->alloc(&b->ps.score, sizeof(double) * (maxND + 256)));
+    A(b->alloc(&b->ps.vtotal, 2 * sizeof(unsigned long long)));
     A(b->alloc(&b->hops, sizeof(unsigned) * (size_t)metas * kLanes));
     // one cooperative launch of the iteration kernel with `group` CTAs per
     // instance when there are fewer instances than half the SMs (one

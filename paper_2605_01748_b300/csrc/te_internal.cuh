@@ -158,11 +158,14 @@ struct ProjScratch {
     double* rem;         // [E] remaining violation per violated edge
     unsigned char* Cp;   // [nslots*32] violated edges per path
     double* score;       // [nblocks*dpb + 256] alpha log(S_c scale) per demand, then log(0..255)
+    unsigned long long* vtotal;  // [2] violated incidences counted, and the fill cursor
+    uint4* vlist;        // [vcap] violated incidences (grown by launch_project as needed; the owner frees it)
+    unsigned long long vcap;
 };
 // alpha and scale (the caller-unit scale of x) form the paths' score keys.
-cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, const ProjScratch& s,
+cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, ProjScratch& s,
                            cudaStream_t st);
-constexpr int kProjectLaunches = 27;  // kernels launch_project issues
+constexpr int kProjectLaunches = 29;  // kernels launch_project issues
 
 // Proportional feasibility scaling (not in the paper): x <- max(x, 0); every
 // demand with S_c > D_c scaled by D_c / S_c; then every path by the smallest

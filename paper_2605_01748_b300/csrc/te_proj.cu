@@ -17,7 +17,9 @@
 //      radix select over the 64-bit key (score bits, then inverted path
 //      index) finds the threshold path at which the running sum of rates in
 //      key order reaches V_e; paths above it are trimmed in full and the
-//      threshold path by the remainder.
+//      threshold path by the remainder.  The select passes read a list of
+//      the violated incidences (one entry per violated edge of a path with
+//      a rate), formed once, instead of walking every path's edge ids.
 // Scores are compared as keys: alpha*log(S_c) + log(C_p) evaluated in FP64
 // with S_c in the caller's units and rounded to FP32 (the oracle forms the
 // same key, so both order the paths alike up to FP64 rounding at an FP32
@@ -202,36 +204,101 @@ __device__ __forceinline__ unsigned long long path_key(double aS, int Cp, const 
     return ((unsigned long long)orderable(ls) << 32) | (unsigned long long)(0xffffffffu - (unsigned)user_path);
 }
 
-// One radix-select pass: per violated edge, histogram of the rates of the
-// candidate paths (keys matching the selected prefix) by the next 8-bit digit.
-template <typename IdT>
-__global__ void k_select_hist(Layout L, const float* x, const double* score, const unsigned char* Cp,
-                              const int* vidx, const unsigned long long* prefix, const unsigned char* done,
-                              unsigned long long* hist, int pass) {
-    const double* logc = score + (size_t)L.nblocks * L.dpb;
-    const IdT* ids = ids_of<IdT>(L);
+// The violated incidences of the capacity step: for every path with a rate
+// and a violated edge, one entry per violated edge on it, (key low word, key
+// high word, rate bits, compact edge index).  k_vlist_total counts them (the
+// sum of C_p over the paths with a rate), k_vlist_fill writes them, each CTA
+// into a range taken with one atomic; the order of the entries therefore
+// varies between runs, but the histograms they feed are integer sums.
+__global__ void k_vlist_total(Layout L, const float* x, const unsigned char* Cp, unsigned long long* total) {
+    __shared__ unsigned long long s_sum;
+    if (threadIdx.x == 0) s_sum = 0ull;
+    __syncthreads();
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)L.nblocks * kLanes) return;
-    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
-    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
-    const int shift = 56 - 8 * pass;
+    unsigned c = 0u;
+    if (i < (long long)L.nblocks * kLanes) {
+        const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+        const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+        for (int j = 0; j < KB; ++j) {
+            const size_t k = (size_t)(s0 + j) * kLanes + lane;
+            if (x[k] != 0.f) c += Cp[k];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c != 0u) atomicAdd(&s_sum, (unsigned long long)c);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_sum != 0ull) atomicAdd(total, s_sum);
+}
+
+template <typename IdT>
+__global__ void k_vlist_fill(Layout L, const float* x, const double* score, const unsigned char* Cp,
+                             const int* vidx, uint4* vlist, unsigned long long cap, unsigned long long* cursor) {
+    __shared__ unsigned s_warp[kThreads / 32];
+    __shared__ unsigned long long s_base;
+    const IdT* ids = ids_of<IdT>(L);
+    const double* logc = score + (size_t)L.nblocks * L.dpb;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool valid = i < (long long)L.nblocks * kLanes;
+    const int b = valid ? (int)(i / kLanes) : 0, lane = (int)(i % kLanes);
+    const int s0 = valid ? L.slotbase[b] : 0, KB = valid ? L.slotbase[b + 1] - s0 : 0;
+    unsigned c = 0u;
+    for (int j = 0; j < KB; ++j) {
+        const size_t k = (size_t)(s0 + j) * kLanes + lane;
+        if (x[k] != 0.f) c += Cp[k];
+    }
+    // this thread's offset in the CTA's range: an exclusive scan over the CTA
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += y;
+    }
+    if (l == 31) s_warp[w] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0ull;
+        for (int k = 0; k < kThreads / 32; ++k) {
+            const unsigned v = s_warp[k];
+            s_warp[k] = (unsigned)t;
+            t += v;
+        }
+        s_base = t != 0ull ? atomicAdd(cursor, t) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long pos = s_base + s_warp[w] + (incl - c);
     for (int j = 0; j < KB; ++j) {
         const size_t sl = (size_t)(s0 + j);
         const float v = x[sl * kLanes + lane];
-        const int c = Cp[sl * kLanes + lane];
-        if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], c, logc,
+        const int cp = Cp[sl * kLanes + lane];
+        if (v == 0.f || cp == 0) continue;
+        const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], cp, logc,
                                                 L.slot_path[sl * kLanes + lane]);
-        const int digit = (int)((key >> shift) & 0xffull);
-        const unsigned long long q = fix_down(v);
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
             if ((int)id == L.E) continue;
             const int vi = vidx[id];
-            if (vi < 0 || done[vi]) continue;
-            if (pass > 0 && ((key ^ prefix[vi]) >> (shift + 8)) != 0ull) continue;
-            atomicAdd(&hist[(size_t)vi * 256 + digit], q);
+            if (vi < 0) continue;
+            if (pos < cap)
+                vlist[pos] = make_uint4((unsigned)key, (unsigned)(key >> 32), __float_as_uint(v), (unsigned)vi);
+            ++pos;
         }
+    }
+}
+
+// One radix-select pass over the violated incidences: per violated edge,
+// histogram of the rates of the candidate paths (keys matching the selected
+// prefix) by the next 8-bit digit.
+__global__ void k_select_hist_list(const uint4* vlist, unsigned long long n, int E, const unsigned char* done,
+                                   const unsigned long long* prefix, unsigned long long* hist, int pass) {
+    const int shift = 56 - 8 * pass;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint4 e = vlist[i];
+        const int vi = (int)e.w;
+        if (vi < 0 || vi >= E || done[vi]) continue;  // (every entry's index is in range by construction)
+        const unsigned long long key = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
+        if (pass > 0 && ((key ^ prefix[vi]) >> (shift + 8)) != 0ull) continue;
+        atomicAdd(&hist[(size_t)vi * 256 + (int)((key >> shift) & 0xffull)], fix_down(__uint_as_float(e.z)));
     }
 }
 
@@ -397,7 +464,7 @@ cudaError_t project_scale_t(const Layout& L, float* x, const ProjScratch& s, cud
 }
 
 template <typename IdT>
-cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, const ProjScratch& s, cudaStream_t st) {
+cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, ProjScratch& s, cudaStream_t st) {
     const long long lanes = (long long)L.nblocks * kLanes;
     const unsigned gl = grid_for(lanes, kThreads);
     const unsigned ge = grid_for(L.E, kThreads);
@@ -420,8 +487,25 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, con
         return err;
     k_score_terms<<<grid_for((long long)L.nblocks * L.dpb > 256 ? (long long)L.nblocks * L.dpb : 256, kThreads),
                     kThreads, 0, st>>>(L, s.S, alpha, scale, s.score);
+    // the violated incidences: count, grow the list if needed (the one
+    // host synchronisation of the projection), fill
+    if ((err = cudaMemsetAsync(s.vtotal, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
+    k_vlist_total<<<gl, kThreads, 0, st>>>(L, x, s.Cp, s.vtotal);
+    unsigned long long total = 0ull;
+    if ((err = cudaMemcpyAsync(&total, s.vtotal, sizeof total, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return err;
+    if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
+    if (total > s.vcap) {
+        if (s.vlist) cudaFree(s.vlist);
+        s.vlist = nullptr;
+        s.vcap = 0;
+        const unsigned long long cap = total + total / 4 + 1024;
+        if ((err = cudaMalloc(&s.vlist, sizeof(uint4) * (size_t)cap)) != cudaSuccess) return err;
+        s.vcap = cap;
+    }
+    k_vlist_fill<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.vcap, s.vtotal + 1);
+    const unsigned gv = grid_for((long long)total, kThreads);
     for (int pass = 0; pass < 8; ++pass) {
-        k_select_hist<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.prefix, done, s.hist, pass);
+        k_select_hist_list<<<gv, kThreads, 0, st>>>(s.vlist, total, L.E, done, s.prefix, s.hist, pass);
         k_select_pick<<<ge, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);
     }
     k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.prefix, s.rem, done);
@@ -430,7 +514,7 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, con
 
 }  // namespace
 
-cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, const ProjScratch& s,
+cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, ProjScratch& s,
                            cudaStream_t st) {
     if (L.id_bytes == 2) return project_t<uint16_t>(L, x, alpha, scale, s, st);
     return project_t<int32_t>(L, x, alpha, scale, s, st);

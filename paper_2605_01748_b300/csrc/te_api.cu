@@ -13,6 +13,7 @@
 #include "te.h"
 #include "te_layout.h"
 #include "te_internal.cuh"
+#include "te_proj.h"
 
 using te::kLanes;
 

@@ -32,6 +32,7 @@
 #include "te.h"
 #include "te_kernels.cuh"
 #include "te_layout.h"
+#include "te_proj.h"
 
 using te::kLanes;
 

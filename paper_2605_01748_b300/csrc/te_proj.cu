@@ -36,6 +36,7 @@
 #include <stdint.h>
 
 #include "te_internal.cuh"
+#include "te_proj.h"
 
 namespace te {
 namespace {

@@ -305,32 +305,59 @@ __global__ void k_select_hist_list(const uint4* vlist, unsigned long long n, int
 
 // Per violated edge: choose the digit at which the running sum (from the top
 // digit down) reaches the remaining violation.  The sums are integers (rates
-// rounded down), compared with the violation rounded up.
+// rounded down), compared with the violation rounded up.  One warp per
+// violated edge: lane l holds the digits 255 - 8l - k, k = 0..7 (so lane
+// order and k follow the scan from the top digit down), the lanes' sums are
+// prefix-summed across the warp, and the first digit with a rate whose
+// running sum reaches the violation is the pick; the sum of the digits above
+// it becomes the part trimmed in full.
 __global__ void k_select_pick(const int* nviol, unsigned long long* hist, unsigned long long* prefix, double* rem,
                               unsigned char* done, int pass) {
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= *nviol || done[v]) return;
+    const int v = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    const int l = threadIdx.x & 31;
+    if (v >= *nviol || done[v]) return;  // (the whole warp)
     const int shift = 56 - 8 * pass;
     unsigned long long* h = hist + (size_t)v * 256;
-    unsigned long long cum = 0ull;
+    unsigned long long c[8], sum = 0ull;
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        c[k] = h[255 - 8 * l - k];
+        sum += c[k];
+    }
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) h[255 - 8 * l - k] = 0ull;  // ready for the next pass
+    unsigned long long incl = sum;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (l >= o) incl += y;
+    }
+    unsigned long long cum = incl - sum;  // the digits above this lane's
     const double need = rem[v];
     const unsigned long long need_q = (unsigned long long)ceil(need * kFixScale);
-    int pick = -1;
-    for (int d = 255; d >= 0; --d) {
-        const unsigned long long c = h[d];
-        h[d] = 0ull;  // ready for the next pass
-        if (pick < 0) {
-            if (cum + c >= need_q && c > 0ull) pick = d;
-            else cum += c;
+    int hit = -1;
+    unsigned long long cum_hit = 0ull;
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (hit < 0 && c[k] > 0ull && cum + c[k] >= need_q) {
+            hit = k;
+            cum_hit = cum;
         }
+        cum += c[k];
     }
-    if (pick < 0) {
+    const unsigned m = __ballot_sync(0xffffffffu, hit >= 0);
+    if (m == 0u) {
         // rounding left the candidates short of V_e: trim all of them in full
-        done[v] = 2;
+        if (l == 0) done[v] = 2;
         return;
     }
-    prefix[v] |= (unsigned long long)pick << shift;
-    rem[v] = need - unfix_down(cum);
+    const int src = __ffs(m) - 1;
+    const int k0 = __shfl_sync(0xffffffffu, hit, src);
+    const unsigned long long cum0 = __shfl_sync(0xffffffffu, cum_hit, src);
+    if (l == 0) {
+        prefix[v] |= (unsigned long long)(255 - 8 * src - k0) << shift;
+        rem[v] = need - unfix_down(cum0);
+    }
 }
 
 // Apply: every path loses the largest trim planned for it by its violated
@@ -505,9 +532,10 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
     }
     k_vlist_fill<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.vcap, s.vtotal + 1);
     const unsigned gv = grid_for((long long)total, kThreads);
+    const unsigned gw = grid_for((long long)L.E * 32, kThreads);  // a warp per (possibly) violated edge
     for (int pass = 0; pass < 8; ++pass) {
         k_select_hist_list<<<gv, kThreads, 0, st>>>(s.vlist, total, L.E, done, s.prefix, s.hist, pass);
-        k_select_pick<<<ge, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);
+        k_select_pick<<<gw, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);
     }
     k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.prefix, s.rem, done);
     return cudaGetLastError();

@@ -398,7 +398,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->ps.rem, sizeof(double) * E));
     A(h->alloc(&h->ps.Cp, ns));
     A(h->alloc(&h->ps.score, sizeof(double) * (ND + 256)));
-    A(h->alloc(&h->ps.vtotal, 2 * sizeof(unsigned long long)));
+    A(h->alloc(&h->ps.vtotal, 3 * sizeof(unsigned long long)));
     if (ce != cudaSuccess) {
         h->err = std::string("device allocation failed: ") + cudaGetErrorString(ce);
         cudaGetLastError();

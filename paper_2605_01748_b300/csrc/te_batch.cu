@@ -679,7 +679,7 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
     A(b->alloc(&b->ps.rem, sizeof(double) * E));
     A(b->alloc(&b->ps.Cp, maxNS));
     A(b->alloc(&b->ps.score, sizeof(double) * (maxND + 256)));
-    A(b->alloc(&b->ps.vtotal, 2 * sizeof(unsigned long long)));
+    A(b->alloc(&b->ps.vtotal, 3 * sizeof(unsigned long long)));
     A(b->alloc(&b->hops, sizeof(unsigned) * (size_t)metas * kLanes));
     // one cooperative launch of the iteration kernel with `group` CTAs per
     // instance when there are fewer instances than half the SMs (one

@@ -231,42 +231,60 @@ __global__ void k_vlist_total(Layout L, const float* x, const unsigned char* Cp,
     if (threadIdx.x == 0 && s_sum != 0ull) atomicAdd(total, s_sum);
 }
 
+// k_vlist_fill also lists the paths with entries, (first entry, number of
+// entries = C_p, position in the sliced layout), for the trim step; a
+// path's entries are contiguous.  cursor[0] counts entries, cursor[1] paths.
 template <typename IdT>
 __global__ void k_vlist_fill(Layout L, const float* x, const double* score, const unsigned char* Cp,
-                             const int* vidx, uint4* vlist, unsigned long long cap, unsigned long long* cursor) {
-    __shared__ unsigned s_warp[kThreads / 32];
-    __shared__ unsigned long long s_base;
+                             const int* vidx, uint4* vlist, uint4* plist, unsigned long long cap,
+                             unsigned long long* cursor) {
+    __shared__ unsigned s_warp[kThreads / 32], s_pwarp[kThreads / 32];
+    __shared__ unsigned long long s_base, s_pbase;
     const IdT* ids = ids_of<IdT>(L);
     const double* logc = score + (size_t)L.nblocks * L.dpb;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const bool valid = i < (long long)L.nblocks * kLanes;
     const int b = valid ? (int)(i / kLanes) : 0, lane = (int)(i % kLanes);
     const int s0 = valid ? L.slotbase[b] : 0, KB = valid ? L.slotbase[b + 1] - s0 : 0;
-    unsigned c = 0u;
+    unsigned c = 0u, pc = 0u;  // this thread's entries and paths
     for (int j = 0; j < KB; ++j) {
         const size_t k = (size_t)(s0 + j) * kLanes + lane;
-        if (x[k] != 0.f) c += Cp[k];
+        if (x[k] != 0.f && Cp[k] != 0) {
+            c += Cp[k];
+            ++pc;
+        }
     }
-    // this thread's offset in the CTA's range: an exclusive scan over the CTA
+    // this thread's offsets in the CTA's ranges: exclusive scans over the CTA
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    unsigned incl = c;
+    unsigned incl = c, pincl = pc;
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (l >= o) incl += y;
+        const unsigned py = __shfl_up_sync(0xffffffffu, pincl, o);
+        if (l >= o) {
+            incl += y;
+            pincl += py;
+        }
     }
-    if (l == 31) s_warp[w] = incl;
+    if (l == 31) {
+        s_warp[w] = incl;
+        s_pwarp[w] = pincl;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long t = 0ull;
+        unsigned long long t = 0ull, pt = 0ull;
         for (int k = 0; k < kThreads / 32; ++k) {
-            const unsigned v = s_warp[k];
+            const unsigned v = s_warp[k], pv = s_pwarp[k];
             s_warp[k] = (unsigned)t;
+            s_pwarp[k] = (unsigned)pt;
             t += v;
+            pt += pv;
         }
-        s_base = t != 0ull ? atomicAdd(cursor, t) : 0ull;
+        s_base = t != 0ull ? atomicAdd(&cursor[0], t) : 0ull;
+        s_pbase = pt != 0ull ? atomicAdd(&cursor[1], pt) : 0ull;
     }
     __syncthreads();
     unsigned long long pos = s_base + s_warp[w] + (incl - c);
+    unsigned long long ppos = s_pbase + s_pwarp[w] + (pincl - pc);
     for (int j = 0; j < KB; ++j) {
         const size_t sl = (size_t)(s0 + j);
         const float v = x[sl * kLanes + lane];
@@ -274,6 +292,8 @@ __global__ void k_vlist_fill(Layout L, const float* x, const double* score, cons
         if (v == 0.f || cp == 0) continue;
         const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], cp, logc,
                                                 L.slot_path[sl * kLanes + lane]);
+        if (ppos < cap) plist[ppos] = make_uint4((unsigned)pos, (unsigned)cp, (unsigned)(sl * kLanes + lane), 0u);
+        ++ppos;
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
             if ((int)id == L.E) continue;
@@ -360,30 +380,24 @@ __global__ void k_select_pick(const int* nviol, unsigned long long* hist, unsign
     }
 }
 
-// Apply: every path loses the largest trim planned for it by its violated
-// edges.
-template <typename IdT>
-__global__ void k_edge_trim(Layout L, float* x, const double* score, const unsigned char* Cp, const int* vidx,
-                            const unsigned long long* prefix, const double* rem, const unsigned char* done) {
-    const double* logc = score + (size_t)L.nblocks * L.dpb;
-    const IdT* ids = ids_of<IdT>(L);
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= (long long)L.nblocks * kLanes) return;
-    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
-    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
-    for (int j = 0; j < KB; ++j) {
-        const size_t sl = (size_t)(s0 + j);
-        const float v = x[sl * kLanes + lane];
-        const int c = Cp[sl * kLanes + lane];
-        if (v == 0.f || c == 0) continue;
-        const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], c, logc,
-                                                L.slot_path[sl * kLanes + lane]);
+// Apply, over the path list: every path with a violated edge loses the
+// largest trim planned for it by its violated edges (a path at or above its
+// edge's threshold key in full, the threshold path by the remainder).
+__global__ void k_edge_trim_list(const uint4* plist, const unsigned long long* npaths, const uint4* vlist,
+                                 unsigned long long cap, int E, float* x, const unsigned long long* prefix,
+                                 const double* rem, const unsigned char* done) {
+    const unsigned long long n = *npaths < cap ? *npaths : cap;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint4 p = plist[i];
+        if ((unsigned long long)p.x + p.y > cap) continue;  // (in range by construction)
+        const float v = __uint_as_float(vlist[p.x].z);
         double trim = 0.0;
-        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
-            const IdT id = ids[(size_t)r * kLanes + lane];
-            if ((int)id == L.E) continue;
-            const int vi = vidx[id];
-            if (vi < 0) continue;
+        for (unsigned k = 0; k < p.y; ++k) {
+            const uint4 e = vlist[p.x + k];
+            const int vi = (int)e.w;
+            if (vi < 0 || vi >= E) continue;
+            const unsigned long long key = (unsigned long long)e.x | ((unsigned long long)e.y << 32);
             double t;
             if (done[vi] == 2) {
                 // all candidates (keys at or above the chosen prefix) in full
@@ -399,7 +413,7 @@ __global__ void k_edge_trim(Layout L, float* x, const double* score, const unsig
         }
         // a full trim leaves exactly zero; a partial one rounds down so the
         // edge ends at or below its capacity
-        x[sl * kLanes + lane] = trim >= (double)v ? 0.f : __double2float_rd((double)v - trim);
+        x[p.z] = trim >= (double)v ? 0.f : __double2float_rd((double)v - trim);
     }
 }
 
@@ -517,27 +531,31 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
                     kThreads, 0, st>>>(L, s.S, alpha, scale, s.score);
     // the violated incidences: count, grow the list if needed (the one
     // host synchronisation of the projection), fill
-    if ((err = cudaMemsetAsync(s.vtotal, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(s.vtotal, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
     k_vlist_total<<<gl, kThreads, 0, st>>>(L, x, s.Cp, s.vtotal);
     unsigned long long total = 0ull;
     if ((err = cudaMemcpyAsync(&total, s.vtotal, sizeof total, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return err;
     if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
+    if (total >= 0xffffffffull) return cudaErrorInvalidValue;  // entry indices are 32-bit
     if (total > s.vcap) {
         if (s.vlist) cudaFree(s.vlist);
         s.vlist = nullptr;
+        s.plist = nullptr;
         s.vcap = 0;
         const unsigned long long cap = total + total / 4 + 1024;
-        if ((err = cudaMalloc(&s.vlist, sizeof(uint4) * (size_t)cap)) != cudaSuccess) return err;
+        // entries, then as many path records (a path has at least one entry)
+        if ((err = cudaMalloc(&s.vlist, 2 * sizeof(uint4) * (size_t)cap)) != cudaSuccess) return err;
+        s.plist = s.vlist + cap;
         s.vcap = cap;
     }
-    k_vlist_fill<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.vcap, s.vtotal + 1);
+    k_vlist_fill<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.plist, s.vcap, s.vtotal + 1);
     const unsigned gv = grid_for((long long)total, kThreads);
     const unsigned gw = grid_for((long long)L.E * 32, kThreads);  // a warp per (possibly) violated edge
     for (int pass = 0; pass < 8; ++pass) {
         k_select_hist_list<<<gv, kThreads, 0, st>>>(s.vlist, total, L.E, done, s.prefix, s.hist, pass);
         k_select_pick<<<gw, kThreads, 0, st>>>(s.nviol, s.hist, s.prefix, s.rem, done, pass);
     }
-    k_edge_trim<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.prefix, s.rem, done);
+    k_edge_trim_list<<<gv, kThreads, 0, st>>>(s.plist, s.vtotal + 2, s.vlist, s.vcap, L.E, x, s.prefix, s.rem, done);
     return cudaGetLastError();
 }
 

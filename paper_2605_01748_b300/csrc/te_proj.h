@@ -23,8 +23,10 @@ struct ProjScratch {
     double* rem;         // [E] remaining violation per violated edge
     unsigned char* Cp;   // [nslots*32] violated edges per path
     double* score;       // [nblocks*dpb + 256] alpha log(S_c scale) per demand, then log(0..255)
-    unsigned long long* vtotal;  // [2] violated incidences counted, and the fill cursor
-    uint4* vlist;        // [vcap] violated incidences (grown by launch_project as needed; the owner frees it)
+    unsigned long long* vtotal;  // [3] violated incidences counted; fill cursors of entries and paths
+    uint4* vlist;        // [vcap] violated incidences, then plist (one allocation, grown by launch_project
+                         // as needed; the owner frees vlist)
+    uint4* plist;        // [vcap] paths with violated incidences: first entry, count, sliced position
     unsigned long long vcap;
 };
 // alpha and scale (the caller-unit scale of x) form the paths' score keys.

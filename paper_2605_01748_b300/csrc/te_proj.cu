@@ -35,6 +35,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "te_internal.cuh"
 #include "te_proj.h"
 
@@ -132,7 +134,10 @@ __global__ void k_viol(Layout L, const unsigned long long* loads, unsigned char*
 
 // C_p = number of violated edges on each path.
 template <typename IdT>
-__global__ void k_count_viol(Layout L, const unsigned char* viol, unsigned char* Cp) {
+// Only paths with a rate are counted (0 for the others): a path without a
+// rate is trimmed by nothing, and the demand step's order among the paths
+// with a rate does not depend on the counts of the others.
+__global__ void k_count_viol(Layout L, const float* x, const unsigned char* viol, unsigned char* Cp) {
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -141,6 +146,10 @@ __global__ void k_count_viol(Layout L, const unsigned char* viol, unsigned char*
     for (int j = 0; j < KB; ++j) {
         const size_t sl = (size_t)(s0 + j);
         int c = 0;
+        if (x[sl * kLanes + lane] == 0.f) {
+            Cp[sl * kLanes + lane] = 0;
+            continue;
+        }
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
             if ((int)id != L.E) c += viol[id];
@@ -211,13 +220,15 @@ __device__ __forceinline__ unsigned long long path_key(double aS, int Cp, const 
 // sum of C_p over the paths with a rate), k_vlist_fill writes them, each CTA
 // into a range taken with one atomic; the order of the entries therefore
 // varies between runs, but the histograms they feed are integer sums.
+// Both run on a grid of a few CTAs per SM, each thread taking lanes i, i +
+// (grid threads), ..., so that the shared counters see one atomic per CTA.
 __global__ void k_vlist_total(Layout L, const float* x, const unsigned char* Cp, unsigned long long* total) {
     __shared__ unsigned long long s_sum;
     if (threadIdx.x == 0) s_sum = 0ull;
     __syncthreads();
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long n = (long long)L.nblocks * kLanes, step = (long long)gridDim.x * blockDim.x;
     unsigned c = 0u;
-    if (i < (long long)L.nblocks * kLanes) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += step) {
         const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
         const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
         for (int j = 0; j < KB; ++j) {
@@ -242,16 +253,18 @@ __global__ void k_vlist_fill(Layout L, const float* x, const double* score, cons
     __shared__ unsigned long long s_base, s_pbase;
     const IdT* ids = ids_of<IdT>(L);
     const double* logc = score + (size_t)L.nblocks * L.dpb;
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const bool valid = i < (long long)L.nblocks * kLanes;
-    const int b = valid ? (int)(i / kLanes) : 0, lane = (int)(i % kLanes);
-    const int s0 = valid ? L.slotbase[b] : 0, KB = valid ? L.slotbase[b + 1] - s0 : 0;
-    unsigned c = 0u, pc = 0u;  // this thread's entries and paths
-    for (int j = 0; j < KB; ++j) {
-        const size_t k = (size_t)(s0 + j) * kLanes + lane;
-        if (x[k] != 0.f && Cp[k] != 0) {
-            c += Cp[k];
-            ++pc;
+    const long long n = (long long)L.nblocks * kLanes, step = (long long)gridDim.x * blockDim.x;
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    unsigned c = 0u, pc = 0u;  // this thread's entries and paths, over all its lanes
+    for (long long i = i0; i < n; i += step) {
+        const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+        const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+        for (int j = 0; j < KB; ++j) {
+            const size_t k = (size_t)(s0 + j) * kLanes + lane;
+            if (x[k] != 0.f && Cp[k] != 0) {
+                c += Cp[k];
+                ++pc;
+            }
         }
     }
     // this thread's offsets in the CTA's ranges: exclusive scans over the CTA
@@ -285,23 +298,27 @@ __global__ void k_vlist_fill(Layout L, const float* x, const double* score, cons
     __syncthreads();
     unsigned long long pos = s_base + s_warp[w] + (incl - c);
     unsigned long long ppos = s_pbase + s_pwarp[w] + (pincl - pc);
-    for (int j = 0; j < KB; ++j) {
-        const size_t sl = (size_t)(s0 + j);
-        const float v = x[sl * kLanes + lane];
-        const int cp = Cp[sl * kLanes + lane];
-        if (v == 0.f || cp == 0) continue;
-        const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], cp, logc,
-                                                L.slot_path[sl * kLanes + lane]);
-        if (ppos < cap) plist[ppos] = make_uint4((unsigned)pos, (unsigned)cp, (unsigned)(sl * kLanes + lane), 0u);
-        ++ppos;
-        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
-            const IdT id = ids[(size_t)r * kLanes + lane];
-            if ((int)id == L.E) continue;
-            const int vi = vidx[id];
-            if (vi < 0) continue;
-            if (pos < cap)
-                vlist[pos] = make_uint4((unsigned)key, (unsigned)(key >> 32), __float_as_uint(v), (unsigned)vi);
-            ++pos;
+    for (long long i = i0; i < n; i += step) {
+        const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+        const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+        for (int j = 0; j < KB; ++j) {
+            const size_t sl = (size_t)(s0 + j);
+            const float v = x[sl * kLanes + lane];
+            const int cp = Cp[sl * kLanes + lane];
+            if (v == 0.f || cp == 0) continue;
+            const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], cp, logc,
+                                                    L.slot_path[sl * kLanes + lane]);
+            if (ppos < cap) plist[ppos] = make_uint4((unsigned)pos, (unsigned)cp, (unsigned)(sl * kLanes + lane), 0u);
+            ++ppos;
+            for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+                const IdT id = ids[(size_t)r * kLanes + lane];
+                if ((int)id == L.E) continue;
+                const int vi = vidx[id];
+                if (vi < 0) continue;
+                if (pos < cap)
+                    vlist[pos] = make_uint4((unsigned)key, (unsigned)(key >> 32), __float_as_uint(v), (unsigned)vi);
+                ++pos;
+            }
         }
     }
 }
@@ -519,7 +536,7 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
         if ((err = cudaMemsetAsync(s.nviol, 0, sizeof(int), st)) != cudaSuccess) return err;
         k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
         k_viol<<<ge, kThreads, 0, st>>>(L, s.loads, s.viol, s.vidx, s.nviol, s.rem, s.prefix);
-        k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, s.viol, s.Cp);
+        k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, x, s.viol, s.Cp);
         if (round == 0) k_demand_trim<<<gd, kThreads, 0, st>>>(L, x, s.S, s.Cp);
     }
     // capacity step: radix select of each violated edge's threshold path
@@ -532,7 +549,11 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
     // the violated incidences: count, grow the list if needed (the one
     // host synchronisation of the projection), fill
     if ((err = cudaMemsetAsync(s.vtotal, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
-    k_vlist_total<<<gl, kThreads, 0, st>>>(L, x, s.Cp, s.vtotal);
+    int nsm = 0, dev = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    const unsigned gp = (unsigned)std::min<long long>((long long)nsm * 8, (long long)gl);  // a few CTAs per SM
+    k_vlist_total<<<gp, kThreads, 0, st>>>(L, x, s.Cp, s.vtotal);
     unsigned long long total = 0ull;
     if ((err = cudaMemcpyAsync(&total, s.vtotal, sizeof total, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return err;
     if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
@@ -548,7 +569,7 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
         s.plist = s.vlist + cap;
         s.vcap = cap;
     }
-    k_vlist_fill<IdT><<<gl, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.plist, s.vcap, s.vtotal + 1);
+    k_vlist_fill<IdT><<<gp, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.plist, s.vcap, s.vtotal + 1);
     const unsigned gv = grid_for((long long)total, kThreads);
     const unsigned gw = grid_for((long long)L.E * 32, kThreads);  // a warp per (possibly) violated edge
     for (int pass = 0; pass < 8; ++pass) {

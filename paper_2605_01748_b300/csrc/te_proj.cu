@@ -134,10 +134,7 @@ __global__ void k_viol(Layout L, const unsigned long long* loads, unsigned char*
 
 // C_p = number of violated edges on each path.
 template <typename IdT>
-// Only paths with a rate are counted (0 for the others): a path without a
-// rate is trimmed by nothing, and the demand step's order among the paths
-// with a rate does not depend on the counts of the others.
-__global__ void k_count_viol(Layout L, const float* x, const unsigned char* viol, unsigned char* Cp) {
+__global__ void k_count_viol(Layout L, const unsigned char* viol, unsigned char* Cp) {
     const IdT* ids = ids_of<IdT>(L);
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * kLanes) return;
@@ -146,10 +143,6 @@ __global__ void k_count_viol(Layout L, const float* x, const unsigned char* viol
     for (int j = 0; j < KB; ++j) {
         const size_t sl = (size_t)(s0 + j);
         int c = 0;
-        if (x[sl * kLanes + lane] == 0.f) {
-            Cp[sl * kLanes + lane] = 0;
-            continue;
-        }
         for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
             const IdT id = ids[(size_t)r * kLanes + lane];
             if ((int)id != L.E) c += viol[id];
@@ -171,7 +164,11 @@ __global__ void k_demand_trim(Layout L, float* x, const double* S, const unsigne
     if (!(Ec > 0.0) || D <= 0.0) return;
     const int s0 = L.slotbase[b];
     const int np = L.np[i];
+    // paths without a rate lose nothing; leaving them out does not change
+    // the order of the others
     unsigned taken = 0u;  // np <= 32
+    for (int p = 0; p < np; ++p)
+        if (x[(size_t)(s0 + p / L.G) * kLanes + t * L.G + p % L.G] == 0.f) taken |= 1u << p;
     for (int k = 0; k < np && Ec > 0.0; ++k) {
         int best = -1, bc = -1;
         for (int p = 0; p < np; ++p) {
@@ -179,6 +176,7 @@ __global__ void k_demand_trim(Layout L, float* x, const double* S, const unsigne
             const int c = Cp[(size_t)(s0 + p / L.G) * kLanes + t * L.G + p % L.G];
             if (c > bc) { bc = c; best = p; }
         }
+        if (best < 0) break;
         taken |= 1u << best;
         float* q = &x[(size_t)(s0 + best / L.G) * kLanes + t * L.G + best % L.G];
         const double d = fmin(Ec, (double)*q);
@@ -536,7 +534,7 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
         if ((err = cudaMemsetAsync(s.nviol, 0, sizeof(int), st)) != cudaSuccess) return err;
         k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
         k_viol<<<ge, kThreads, 0, st>>>(L, s.loads, s.viol, s.vidx, s.nviol, s.rem, s.prefix);
-        k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, x, s.viol, s.Cp);
+        k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, s.viol, s.Cp);
         if (round == 0) k_demand_trim<<<gd, kThreads, 0, st>>>(L, x, s.S, s.Cp);
     }
     // capacity step: radix select of each violated edge's threshold path

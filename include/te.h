@@ -293,9 +293,9 @@ te_status te_layout(const te_handle* h, te_layout_info* info);
  * is recomputed forward before it is reversed.  The normalisation unit is
  * held fixed (create with scale_mode 2 for caller units, so that the
  * function differentiated does not move the unit).  Forward states are the
- * FP32 iterates; adjoints are FP64, and the per-edge weight adjoints are
- * summed with FP64 atomic additions, so the last bits of the gradient may
- * differ between calls (J does not).  Uses device memory of about
+ * FP32 iterates; adjoints are FP64, and J and the per-edge weight adjoints
+ * are summed with FP64 atomic additions, so the last bits of J and of the
+ * gradient may differ between calls.  Uses device memory of about
  * (K/checkpoint_every + checkpoint_every + 2) times the iterate (released
  * before returning).  The handle's state afterwards is that of an
  * intermediate iteration: call te_reset before solving again. */

@@ -223,6 +223,36 @@ def test_projection_parity_and_feasibility(te, tiny, medium):
         t.close()
 
 
+def test_projection_list_empty_and_growing(te, tiny, medium):
+    """Algorithm 2 with no violated edge (the list of violated incidences is
+    empty) and on one handle first with few violations, then with many (the
+    list grows between calls): each against the oracle's projection."""
+    import dataclasses
+    roomy = dataclasses.replace(tiny, capacity=tiny.capacity * 1e4)
+    t = te.TE(roomy, gamma=-1.0)
+    t.solve(5)
+    x = t.allocation(project=False)
+    xg = t.allocation(project=True)
+    alpha = t.solve(0)["alpha"]
+    assert (O.edge_loads(roomy, x.astype(np.float64)) <= roomy.capacity).all()  # nothing to trim on edges
+    assert _rel_inf(xg, O.project(roomy, x.astype(np.float64), alpha)) <= TOL
+    t.close()
+    t = te.TE(medium, gamma=-1.0)
+    for iters in (600, 0):  # late iterate (few violations), then the initial one (many)
+        if iters:
+            t.solve(iters)
+        else:
+            t.reset()
+            t.solve(1)
+        x = t.allocation(project=False)
+        xg = t.allocation(project=True)
+        alpha = t.solve(0)["alpha"]
+        xo = O.project(medium, x.astype(np.float64), alpha)
+        assert _rel_inf(xg, xo) <= TOL, (iters, _rel_inf(xg, xo))
+        assert (O.edge_loads(medium, xg) <= medium.capacity * (1 + 1e-5)).all()
+    t.close()
+
+
 def test_gap_parity(te, tiny):
     for alpha in (0.0, 1.0):
         t = te.TE(tiny, alpha_target=alpha, alpha_start=alpha, gamma=1e-5)

@@ -19,12 +19,17 @@
 //   its multiplier: binding iff beta nu <= U'(D_c))
 //   dnu/dm_s = -alpha nu / (S + alpha nu H); mb_s = gb_s + G dnu/dm_s on A, 0 off A
 //   xb = mb;  ub_e += sum_{r ni e} (-mb_r/n_r);  db_e = the same sum
+// The last sums (the adjoint of w) are exact 64-bit fixed-point integer sums
+// of the terms -mb_r/n_r, each rounded to the nearest multiple of 2^-k where
+// 2^k is the largest power of two that keeps every edge's sum below 2^61
+// given the step's largest term: order-free, so te_gradient is
+// deterministic.  The objective J is summed in a fixed order.
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
 
-#include "te_internal.cuh"
+#include "te_adjoint.h"
 
 namespace te {
 namespace {
@@ -55,11 +60,12 @@ __global__ void k_adj_edges_in(int E, double* ub, double* db, const float* u1, c
 }
 
 // per-demand step: one thread per demand slot.  xb (per path lane) is read
-// as the adjoint of x' and overwritten with the adjoint of x; wbar collects
-// the adjoint of w (zeroed by the caller).
+// as the adjoint of x' and overwritten with the adjoint of x; qb receives
+// each path's term of the adjoint of w (-mb/n, 0 off the active set) and
+// qmax the largest |qb| (zeroed by the caller).
 __global__ void k_adj_demands(Layout L, const float* __restrict__ x1, const float* __restrict__ lam1,
-                              const double* __restrict__ Lb, double* xb, double* wbar, double* Db, float beta,
-                              float alpha) {
+                              const double* __restrict__ Lb, double* xb, double* qb, unsigned long long* qmax,
+                              double* Db, float beta, float alpha) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * L.dpb) return;
     const int np = L.np[i];
@@ -129,30 +135,66 @@ __global__ void k_adj_demands(Layout L, const float* __restrict__ x1, const floa
             mb = g + G * dnu;
         }
         xb[at] = mb;
-        if (mb != 0.0) {
-            const double qb = -mb / (double)n;
-            for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
-                const int id = ids[(size_t)r * kLanes + lane];
-                if (id != L.E) atomicAdd(&wbar[id], qb);
-            }
+        const double q = mb != 0.0 ? -mb / (double)n : 0.0;
+        qb[at] = q;
+        // |q| as the bits of a non-negative double: their order is the
+        // numbers' order, so the maximum does not depend on the order either
+        if (q != 0.0) atomicMax(qmax, (unsigned long long)__double_as_longlong(fabs(q)));
+    }
+}
+
+// The fixed-point scale 2^k of a step: the largest k with 2^k max|qb| <
+// 2^(61 - deg_bits), so that each term is below 2^(61 - deg_bits) and each
+// edge's sum of at most 2^deg_bits terms below 2^61 in magnitude.  0 when
+// every term is 0; NaN when a term is not finite (the gradient then is NaN).
+__device__ __forceinline__ double adj_scale(unsigned long long qmax_bits, int deg_bits) {
+    const double m = __longlong_as_double((long long)qmax_bits);
+    if (!(m < INFINITY)) return NAN;
+    if (!(m > 0.0)) return 0.0;
+    int e = 0;
+    frexp(m, &e);  // m < 2^e
+    return ldexp(1.0, min(61 - deg_bits - e, 1000));
+}
+
+// the adjoint of w per edge: one thread per path lane adds its paths' terms
+// as fixed-point integers
+__global__ void k_adj_scatter(Layout L, const double* __restrict__ qb, const unsigned long long* qmax, int deg_bits,
+                              unsigned long long* wfix) {
+    const double scale = adj_scale(*qmax, deg_bits);
+    if (!(scale > 0.0)) return;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)L.nblocks * kLanes) return;
+    const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
+    const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
+    const uint16_t* ids = static_cast<const uint16_t*>(L.ids);
+    for (int j = 0; j < KB; ++j) {
+        const size_t sl = (size_t)(s0 + j);
+        const double v = qb[sl * kLanes + lane];
+        if (v == 0.0) continue;
+        const unsigned long long q = (unsigned long long)llrint(v * scale);  // two's complement
+        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+            const int id = ids[(size_t)r * kLanes + lane];
+            if (id != L.E) atomicAdd(&wfix[id], q);
         }
     }
 }
 
 // per-edge part after the per-demand step: w = u + d
-__global__ void k_adj_edges_out(int E, double* ub, double* db, double* wbar) {
+__global__ void k_adj_edges_out(int E, double* ub, double* db, unsigned long long* wfix,
+                                const unsigned long long* qmax, int deg_bits) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
-    ub[e] += wbar[e];
-    db[e] = wbar[e];
-    wbar[e] = 0.0;
+    const double scale = adj_scale(*qmax, deg_bits);
+    const double wb = scale > 0.0 ? (double)(long long)wfix[e] / scale : (scale == 0.0 ? 0.0 : scale);
+    ub[e] += wb;
+    db[e] = wb;
+    wfix[e] = 0ull;
 }
 
-// objective J = sum_c U_alpha(scale S_c) of the iterate x, and the adjoint
-// dJ/dx_r = scale U'(scale S_c) on every path of demand c; J accumulates
-// into acc[0]
+// objective terms U_alpha(scale S_c) of the iterate x into Uc, and the
+// adjoint dJ/dx_r = scale U'(scale S_c) on every path of demand c
 __global__ void k_adj_objective(Layout L, const float* __restrict__ x, double alpha, double scale, double* xb,
-                                double* acc) {
+                                double* Uc) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)L.nblocks * L.dpb) return;
     const int np = L.np[i];
@@ -165,7 +207,22 @@ __global__ void k_adj_objective(Layout L, const float* __restrict__ x, double al
     const double U = alpha == 1.0 ? log(v) : (pow(v, 1.0 - alpha) - 1.0) / (1.0 - alpha);
     const double g = scale * (alpha == 0.0 ? 1.0 : exp(-alpha * log(v)));
     for (int p = 0; p < np; ++p) xb[(size_t)(s0 + p / L.G) * kLanes + t * L.G + p % L.G] = g;
-    atomicAdd(acc, U);
+    Uc[i] = U;
+}
+
+// acc[0] = sum of v[0..n) in a fixed order (one CTA: strided sums per
+// thread, then the threads' sums in thread order)
+__global__ void k_sum_ordered(const double* v, long long n, double* acc) {
+    __shared__ double part[kThreads];
+    double a = 0.0;
+    for (long long i = threadIdx.x; i < n; i += kThreads) a += v[i];
+    part[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kThreads; ++k) t += part[k];
+        acc[0] = t;
+    }
 }
 
 // initial state x^0_r = D_c / |P_c|: its adjoint into the demand's
@@ -198,15 +255,20 @@ cudaError_t adjoint_step(const Layout& L, const float* xk, const float* x1, cons
     k_adj_edges_in<<<grid_for(L.E), kThreads, 0, st>>>(L.E, B.ub, B.db, uk1, L.ne_f, L.inv_ne, B.Lb, B.Cb);
     (void)xk;
     (void)wk;
-    k_adj_demands<<<grid_for((long long)L.nblocks * L.dpb), kThreads, 0, st>>>(L, x1, lam1, B.Lb, B.xb, B.wbar, B.Db,
-                                                                             beta, alpha);
-    k_adj_edges_out<<<grid_for(L.E), kThreads, 0, st>>>(L.E, B.ub, B.db, B.wbar);
+    cudaError_t err = cudaMemsetAsync(B.qmax, 0, sizeof(unsigned long long), st);
+    if (err != cudaSuccess) return err;
+    k_adj_demands<<<grid_for((long long)L.nblocks * L.dpb), kThreads, 0, st>>>(L, x1, lam1, B.Lb, B.xb, B.qb, B.qmax,
+                                                                             B.Db, beta, alpha);
+    k_adj_scatter<<<grid_for((long long)L.nblocks * kLanes), kThreads, 0, st>>>(L, B.qb, B.qmax, B.deg_bits, B.wfix);
+    k_adj_edges_out<<<grid_for(L.E), kThreads, 0, st>>>(L.E, B.ub, B.db, B.wfix, B.qmax, B.deg_bits);
     return cudaGetLastError();
 }
 
 cudaError_t adjoint_objective(const Layout& L, const float* x, double alpha, double scale, AdjointBuffers& B,
                               cudaStream_t st) {
-    k_adj_objective<<<grid_for((long long)L.nblocks * L.dpb), kThreads, 0, st>>>(L, x, alpha, scale, B.xb, B.acc);
+    const long long nd = (long long)L.nblocks * L.dpb;
+    k_adj_objective<<<grid_for(nd), kThreads, 0, st>>>(L, x, alpha, scale, B.xb, B.Uc);
+    k_sum_ordered<<<1, kThreads, 0, st>>>(B.Uc, nd, B.acc);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 #include "te_layout.h"
 #include "te_internal.cuh"
 #include "te_proj.h"
+#include "te_adjoint.h"
 
 using te::kLanes;
 
@@ -783,9 +784,22 @@ extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint
     B.db = (double*)dalloc(sizeof(double) * E);
     B.Lb = (double*)dalloc(sizeof(double) * E);
     B.Cb = (double*)dalloc(sizeof(double) * E);
-    B.wbar = (double*)dalloc(sizeof(double) * E);
+    B.qb = (double*)dalloc(sizeof(double) * ns);
+    B.wfix = (unsigned long long*)dalloc(sizeof(unsigned long long) * E);
+    B.qmax = (unsigned long long*)dalloc(sizeof(unsigned long long));
     B.Db = (double*)dalloc(sizeof(double) * ND);
+    B.Uc = (double*)dalloc(sizeof(double) * ND);
     B.acc = (double*)dalloc(sizeof(double));
+    {
+        // the fixed-point range of the weight adjoint sums: at most (largest
+        // number of path-edge incidences on one edge) terms per edge
+        std::vector<float> ne((size_t)E);
+        A(cudaMemcpy(ne.data(), L.ne_f, sizeof(float) * E, cudaMemcpyDeviceToHost));
+        double mx = 1.0;
+        for (float v : ne) mx = std::max(mx, (double)v);
+        B.deg_bits = 1;
+        while (B.deg_bits < 60 && std::ldexp(1.0, B.deg_bits) <= mx) ++B.deg_bits;
+    }
     double* gC = out_is_device ? dJ_dC : (double*)dalloc(sizeof(double) * E);
     double* gD = out_is_device ? dJ_dD : (double*)dalloc(sizeof(double) * (size_t)L.K);
     if (ce != cudaSuccess) {
@@ -821,11 +835,13 @@ extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint
     A(cudaMemsetAsync(B.ub, 0, sizeof(double) * E, s));
     A(cudaMemsetAsync(B.db, 0, sizeof(double) * E, s));
     A(cudaMemsetAsync(B.Cb, 0, sizeof(double) * E, s));
-    A(cudaMemsetAsync(B.wbar, 0, sizeof(double) * E, s));
+    A(cudaMemsetAsync(B.wfix, 0, sizeof(unsigned long long) * E, s));
+    A(cudaMemsetAsync(B.qb, 0, sizeof(double) * ns, s));
     A(cudaMemsetAsync(B.Db, 0, sizeof(double) * ND, s));
+    A(cudaMemsetAsync(B.Uc, 0, sizeof(double) * ND, s));
     A(cudaMemsetAsync(B.acc, 0, sizeof(double), s));
     A(te::adjoint_objective(L, h->x + (size_t)h->hsc.xbuf * ns, h->hsc.alpha, h->scale, B, s));
-    h->launches += 1;
+    h->launches += te::kAdjointObjectiveLaunches;
     // reverse, one checkpoint segment at a time (each recomputed forward first)
     for (long long k0 = K > 0 ? ((K - 1) / ck) * ck : -1; k0 >= 0 && ce == cudaSuccess; k0 -= ck) {
         const long long k1 = std::min(k0 + ck, K);

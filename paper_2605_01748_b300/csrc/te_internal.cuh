@@ -154,31 +154,6 @@ cudaError_t launch_gap_impl(const Layout& L, const float* x, const float* u, dou
                             double scale, const double* Dc, double* acc, double* slots, cudaStream_t st);
 constexpr int kGapLaunches = 3;
 
-// Reverse-mode step of one fixed-schedule iteration (te_adjoint.cu): FP64
-// adjoints of the rates (per path lane of the sliced layout), of the edge
-// prices u and differences d, of the loads, capacities and demands.
-struct AdjointBuffers {
-    double* xb;    // [nslots*32]
-    double* ub;    // [E]
-    double* db;    // [E]
-    double* Lb;    // [E]
-    double* Cb;    // [E]
-    double* wbar;  // [E], zero between steps
-    double* Db;    // [nblocks*dpb]
-    double* acc;   // [1] objective
-};
-// xk, wk: rates and gather weights entering the iteration; x1, uk1, lam1:
-// rates, prices and per-demand multipliers (beta nu) it produced.
-cudaError_t adjoint_step(const Layout& L, const float* xk, const float* x1, const float* uk1, const float* wk,
-                         const float* lam1, float beta, float alpha, AdjointBuffers& B, cudaStream_t st);
-// J of the rates x into acc and its adjoint into xb
-cudaError_t adjoint_objective(const Layout& L, const float* x, double alpha, double scale, AdjointBuffers& B,
-                              cudaStream_t st);
-// the initial state's dependence on the demands, then the gradients in
-// caller order and units (gC [E], gD [K], device)
-cudaError_t adjoint_finish(const Layout& L, double scale, AdjointBuffers& B, double* gC, double* gD,
-                           cudaStream_t st);
-constexpr int kAdjointStepLaunches = 3;
 
 // p_out[e] = pscale * u[e] (FP64).
 cudaError_t launch_prices(int E, const float* u, double pscale, double* p_out, cudaStream_t st);

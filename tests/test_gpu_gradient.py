@@ -75,6 +75,20 @@ def test_gradient_matches_oracle_medium(te, medium, alpha, K):
     t.close()
 
 
+def test_gradient_is_bit_identical_across_calls(te, medium):
+    """J is summed in a fixed order and the weight adjoints as fixed-point
+    integers, so two te_gradient calls on one handle return the same bits."""
+    b0 = _beta0(medium)
+    t = _fixed(te, medium, 1.0, b0)
+    J1, gC1, gD1 = t.gradient(60, 20)
+    J2, gC2, gD2 = t.gradient(60, 20)
+    t.close()
+    assert J1 == J2
+    assert np.array_equal(np.asarray(gC1).view(np.uint64), np.asarray(gC2).view(np.uint64))
+    assert np.array_equal(np.asarray(gD1).view(np.uint64), np.asarray(gD2).view(np.uint64))
+    assert np.abs(gC1).max() > 0
+
+
 def test_autograd_function(te, tiny):
     import torch
     K, b0 = 30, _beta0(tiny)

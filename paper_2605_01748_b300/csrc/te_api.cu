@@ -567,8 +567,9 @@ extern "C" te_status te_allocation(te_handle* h, float* x_out, int32_t project, 
     if (project != TE_PROJECT_NONE) {
         A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
         if (project == TE_PROJECT_ALG2) {
-            A(te::launch_project(h->L, h->xtmp, h->hsc.alpha, h->scale, h->ps, s));
-            h->launches += te::kProjectLaunches;
+            int np_ = 0;
+            A(te::launch_project(h->L, h->xtmp, h->hsc.alpha, h->scale, h->ps, s, &np_));
+            h->launches += np_;
         } else {
             A(te::launch_project_scale(h->L, h->xtmp, h->ps, s));
             h->launches += te::kProjectScaleLaunches;
@@ -594,8 +595,9 @@ extern "C" te_status te_gap_projected(te_handle* h, int32_t project, double* gap
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
     A(cudaMemcpyAsync(h->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
     if (project == TE_PROJECT_ALG2) {
-        A(te::launch_project(h->L, h->xtmp, h->hsc.alpha, h->scale, h->ps, s));
-        h->launches += te::kProjectLaunches;
+        int np_ = 0;
+        A(te::launch_project(h->L, h->xtmp, h->hsc.alpha, h->scale, h->ps, s, &np_));
+        h->launches += np_;
     } else {
         A(te::launch_project_scale(h->L, h->xtmp, h->ps, s));
         h->launches += te::kProjectScaleLaunches;

@@ -971,8 +971,9 @@ extern "C" te_status te_batch_allocation(te_batch* b, int32_t i, float* x_out, i
     if (project != TE_PROJECT_NONE) {
         A(cudaMemcpyAsync(b->xtmp, src, sizeof(float) * ns, cudaMemcpyDeviceToDevice, s));
         if (project == TE_PROJECT_ALG2) {
-            A(te::launch_project(V, b->xtmp, b->hsc[i].alpha, b->scale[i], b->ps, s));
-            b->launches += te::kProjectLaunches;
+            int np_ = 0;
+            A(te::launch_project(V, b->xtmp, b->hsc[i].alpha, b->scale[i], b->ps, s, &np_));
+            b->launches += np_;
         } else {
             A(te::launch_project_scale(V, b->xtmp, b->ps, s));
             b->launches += te::kProjectScaleLaunches;

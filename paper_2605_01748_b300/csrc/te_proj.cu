@@ -212,37 +212,108 @@ __device__ __forceinline__ unsigned long long path_key(double aS, int Cp, const 
     return ((unsigned long long)orderable(ls) << 32) | (unsigned long long)(0xffffffffu - (unsigned)user_path);
 }
 
-// The violated incidences of the capacity step: for every path with a rate
-// and a violated edge, one entry per violated edge on it, (key low word, key
-// high word, rate bits, compact edge index).  k_vlist_total counts them (the
-// sum of C_p over the paths with a rate), k_vlist_fill writes them, each CTA
-// into a range taken with one atomic; the order of the entries therefore
-// varies between runs, but the histograms they feed are integer sums.
-// Both run on a grid of a few CTAs per SM, each thread taking lanes i, i +
-// (grid threads), ..., so that the shared counters see one atomic per CTA.
-__global__ void k_vlist_total(Layout L, const float* x, const unsigned char* Cp, unsigned long long* total) {
-    __shared__ unsigned long long s_sum;
-    if (threadIdx.x == 0) s_sum = 0ull;
-    __syncthreads();
-    const long long n = (long long)L.nblocks * kLanes, step = (long long)gridDim.x * blockDim.x;
-    unsigned c = 0u;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += step) {
-        const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
-        const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
-        for (int j = 0; j < KB; ++j) {
-            const size_t k = (size_t)(s0 + j) * kLanes + lane;
-            if (x[k] != 0.f) c += Cp[k];
+// The second round's count of violated edges per path fused with the list
+// of violated incidences (see below): each thread counts its paths' violated
+// edges, the CTA takes its ranges with one atomic each, and the thread walks
+// the rows of its counted paths again (just read) to write their entries and
+// path records, but only as far as cap: cursor[0] and cursor[1] end as the
+// totals, and when cursor[0] exceeds cap the caller grows the list and
+// fills it with k_vlist_fill.
+template <typename IdT>
+__global__ void k_count_fill(Layout L, const float* x, const unsigned char* viol, const int* vidx,
+                             const double* score, unsigned char* Cp, uint4* vlist, uint4* plist,
+                             unsigned long long cap, unsigned long long* cursor) {
+    constexpr int KL = kMaxPathsPerLane;
+    __shared__ unsigned s_warp[kThreads / 32], s_pwarp[kThreads / 32];
+    __shared__ unsigned long long s_base, s_pbase;
+    const IdT* ids = ids_of<IdT>(L);
+    const double* logc = score + (size_t)L.nblocks * L.dpb;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool valid = i < (long long)L.nblocks * kLanes;
+    const int b = valid ? (int)(i / kLanes) : 0, lane = (int)(i % kLanes);
+    const int s0 = valid ? L.slotbase[b] : 0, KB = valid ? L.slotbase[b + 1] - s0 : 0;
+    int cnt[KL];
+    unsigned c = 0u, pc = 0u;  // this thread's entries and paths
+    #pragma unroll
+    for (int j = 0; j < KL; ++j) {
+        cnt[j] = 0;
+        if (j < KB) {
+            const size_t sl = (size_t)(s0 + j);
+            int n = 0;
+            for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+                const IdT id = ids[(size_t)r * kLanes + lane];
+                if ((int)id != L.E) n += viol[id];
+            }
+            n = n > 255 ? 255 : n;
+            Cp[sl * kLanes + lane] = (unsigned char)n;
+            if (n != 0 && x[sl * kLanes + lane] != 0.f) {
+                cnt[j] = n;
+                c += (unsigned)n;
+                ++pc;
+            }
         }
     }
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c != 0u) atomicAdd(&s_sum, (unsigned long long)c);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    unsigned incl = c, pincl = pc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        const unsigned py = __shfl_up_sync(0xffffffffu, pincl, o);
+        if (l >= o) {
+            incl += y;
+            pincl += py;
+        }
+    }
+    if (l == 31) {
+        s_warp[w] = incl;
+        s_pwarp[w] = pincl;
+    }
     __syncthreads();
-    if (threadIdx.x == 0 && s_sum != 0ull) atomicAdd(total, s_sum);
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0ull, pt = 0ull;
+        for (int k = 0; k < kThreads / 32; ++k) {
+            const unsigned v = s_warp[k], pv = s_pwarp[k];
+            s_warp[k] = (unsigned)t;
+            s_pwarp[k] = (unsigned)pt;
+            t += v;
+            pt += pv;
+        }
+        s_base = t != 0ull ? atomicAdd(&cursor[0], t) : 0ull;
+        s_pbase = pt != 0ull ? atomicAdd(&cursor[1], pt) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long pos = s_base + s_warp[w] + (incl - c);
+    unsigned long long ppos = s_pbase + s_pwarp[w] + (pincl - pc);
+    if (pos + c > cap) return;  // the list is too short: the caller fills it again
+    #pragma unroll
+    for (int j = 0; j < KL; ++j) {
+        if (cnt[j] == 0) continue;
+        const size_t sl = (size_t)(s0 + j);
+        const float v = x[sl * kLanes + lane];
+        const unsigned long long key = path_key(score[(size_t)b * L.dpb + lane / L.G], cnt[j], logc,
+                                                L.slot_path[sl * kLanes + lane]);
+        if (ppos < cap) plist[ppos] = make_uint4((unsigned)pos, (unsigned)cnt[j], (unsigned)(sl * kLanes + lane), 0u);
+        ++ppos;
+        for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
+            const IdT id = ids[(size_t)r * kLanes + lane];
+            if ((int)id == L.E) continue;
+            const int vi = vidx[id];
+            if (vi < 0) continue;
+            if (pos < cap)
+                vlist[pos] = make_uint4((unsigned)key, (unsigned)(key >> 32), __float_as_uint(v), (unsigned)vi);
+            ++pos;
+        }
+    }
 }
 
-// k_vlist_fill also lists the paths with entries, (first entry, number of
-// entries = C_p, position in the sliced layout), for the trim step; a
-// path's entries are contiguous.  cursor[0] counts entries, cursor[1] paths.
+// The violated incidences of the capacity step: for every path with a rate
+// and a violated edge, one entry per violated edge on it, (key low word, key
+// high word, rate bits, compact edge index), as many as the sum of C_p over
+// the paths with a rate.  k_count_fill and k_vlist_fill write them, each CTA
+// into a range taken with one atomic; the order of the entries therefore
+// varies between runs, but the histograms they feed are integer sums.
+// k_vlist_fill runs on a grid of a few CTAs per SM, each thread taking lanes
+// i, i + (grid threads), ..., so that the shared counters see one atomic per
+// CTA.
 template <typename IdT>
 __global__ void k_vlist_fill(Layout L, const float* x, const double* score, const unsigned char* Cp,
                              const int* vidx, uint4* vlist, uint4* plist, unsigned long long cap,
@@ -521,7 +592,8 @@ cudaError_t project_scale_t(const Layout& L, float* x, const ProjScratch& s, cud
 }
 
 template <typename IdT>
-cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, ProjScratch& s, cudaStream_t st) {
+cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, ProjScratch& s, cudaStream_t st,
+                      int* launched_out) {
     const long long lanes = (long long)L.nblocks * kLanes;
     const unsigned gl = grid_for(lanes, kThreads);
     const unsigned ge = grid_for(L.E, kThreads);
@@ -534,26 +606,25 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
         if ((err = cudaMemsetAsync(s.nviol, 0, sizeof(int), st)) != cudaSuccess) return err;
         k_loads<IdT><<<gl, kThreads, 0, st>>>(L, x, s.loads);
         k_viol<<<ge, kThreads, 0, st>>>(L, s.loads, s.viol, s.vidx, s.nviol, s.rem, s.prefix);
-        k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, s.viol, s.Cp);
-        if (round == 0) k_demand_trim<<<gd, kThreads, 0, st>>>(L, x, s.S, s.Cp);
+        if (round == 0) {
+            k_count_viol<IdT><<<gl, kThreads, 0, st>>>(L, s.viol, s.Cp);
+            k_demand_trim<<<gd, kThreads, 0, st>>>(L, x, s.S, s.Cp);
+        }
     }
     // capacity step: radix select of each violated edge's threshold path
-    unsigned char* done = s.viol;  // reuse: per violated-edge flags (E bytes >= nviol)
-    if ((err = cudaMemsetAsync(done, 0, (size_t)L.E, st)) != cudaSuccess) return err;
-    if ((err = cudaMemsetAsync(s.hist, 0, sizeof(unsigned long long) * 256 * (size_t)L.E, st)) != cudaSuccess)
-        return err;
+    unsigned char* done = s.viol;  // reuse: per violated-edge flags (E bytes >= nviol), set after the count
     k_score_terms<<<grid_for((long long)L.nblocks * L.dpb > 256 ? (long long)L.nblocks * L.dpb : 256, kThreads),
                     kThreads, 0, st>>>(L, s.S, alpha, scale, s.score);
-    // the violated incidences: count, grow the list if needed (the one
-    // host synchronisation of the projection), fill
+    // the second round's counts and the violated incidences in one walk;
+    // the totals come back to the host (the one synchronisation of the
+    // projection), and a list too short is grown and filled again
     if ((err = cudaMemsetAsync(s.vtotal, 0, 3 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
-    int nsm = 0, dev = 0;
-    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
-    if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
-    const unsigned gp = (unsigned)std::min<long long>((long long)nsm * 8, (long long)gl);  // a few CTAs per SM
-    k_vlist_total<<<gp, kThreads, 0, st>>>(L, x, s.Cp, s.vtotal);
+    k_count_fill<IdT><<<gl, kThreads, 0, st>>>(L, x, s.viol, s.vidx, s.score, s.Cp, s.vlist, s.plist, s.vcap,
+                                               s.vtotal + 1);
+    int launched = kProjectLaunches;
     unsigned long long total = 0ull;
-    if ((err = cudaMemcpyAsync(&total, s.vtotal, sizeof total, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return err;
+    if ((err = cudaMemcpyAsync(&total, s.vtotal + 1, sizeof total, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return err;
     if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
     if (total >= 0xffffffffull) return cudaErrorInvalidValue;  // entry indices are 32-bit
     if (total > s.vcap) {
@@ -566,8 +637,18 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
         if ((err = cudaMalloc(&s.vlist, 2 * sizeof(uint4) * (size_t)cap)) != cudaSuccess) return err;
         s.plist = s.vlist + cap;
         s.vcap = cap;
+        if ((err = cudaMemsetAsync(s.vtotal + 1, 0, 2 * sizeof(unsigned long long), st)) != cudaSuccess) return err;
+        int nsm = 0, dev = 0;
+        if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+        if ((err = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+        const unsigned gp = (unsigned)std::min<long long>((long long)nsm * 8, (long long)gl);  // a few CTAs per SM
+        k_vlist_fill<IdT><<<gp, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.plist, s.vcap, s.vtotal + 1);
+        ++launched;
     }
-    k_vlist_fill<IdT><<<gp, kThreads, 0, st>>>(L, x, s.score, s.Cp, s.vidx, s.vlist, s.plist, s.vcap, s.vtotal + 1);
+    if (launched_out) *launched_out = launched;
+    if ((err = cudaMemsetAsync(done, 0, (size_t)L.E, st)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(s.hist, 0, sizeof(unsigned long long) * 256 * (size_t)L.E, st)) != cudaSuccess)
+        return err;
     const unsigned gv = grid_for((long long)total, kThreads);
     const unsigned gw = grid_for((long long)L.E * 32, kThreads);  // a warp per (possibly) violated edge
     for (int pass = 0; pass < 8; ++pass) {
@@ -581,9 +662,9 @@ cudaError_t project_t(const Layout& L, float* x, double alpha, double scale, Pro
 }  // namespace
 
 cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, ProjScratch& s,
-                           cudaStream_t st) {
-    if (L.id_bytes == 2) return project_t<uint16_t>(L, x, alpha, scale, s, st);
-    return project_t<int32_t>(L, x, alpha, scale, s, st);
+                           cudaStream_t st, int* launched) {
+    if (L.id_bytes == 2) return project_t<uint16_t>(L, x, alpha, scale, s, st, launched);
+    return project_t<int32_t>(L, x, alpha, scale, s, st, launched);
 }
 
 cudaError_t launch_project_scale(const Layout& L, float* x, const ProjScratch& s, cudaStream_t st) {

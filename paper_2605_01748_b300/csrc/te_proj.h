@@ -30,9 +30,11 @@ struct ProjScratch {
     unsigned long long vcap;
 };
 // alpha and scale (the caller-unit scale of x) form the paths' score keys.
+// *launched (may be NULL) receives the number of kernels launched:
+// kProjectLaunches, one more when the list of violated incidences grew.
 cudaError_t launch_project(const Layout& L, float* x, double alpha, double scale, ProjScratch& s,
-                           cudaStream_t st);
-constexpr int kProjectLaunches = 29;  // kernels launch_project issues
+                           cudaStream_t st, int* launched);
+constexpr int kProjectLaunches = 27;
 
 // Proportional feasibility scaling (not in the paper): x <- max(x, 0); every
 // demand with S_c > D_c scaled by D_c / S_c; then every path by the smallest

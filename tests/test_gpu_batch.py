@@ -88,6 +88,26 @@ def test_batch_matches_single_engine_with_adaptive_beta(te, medium):
     b.close()
 
 
+def test_batch_projection_matches_oracle_per_instance(te, tiny):
+    """Algorithm 2 on each instance of a batch (one list of violated
+    incidences for all instances, grown when an instance needs more) against
+    the oracle's projection of that instance's iterate."""
+    W = instances.make_what_if(tiny, 4, 2, seed=3, min_fail=1, max_fail=2)
+    b = te.TEBatch(W, gamma=-1.0)
+    b.solve(20)
+    res = b.solve(0)
+    trimmed = 0
+    for i, inst in enumerate(W):
+        x = b.allocation(i, project=te.PROJECT_NONE).astype(np.float64)
+        xg = b.allocation(i, project=te.PROJECT_ALG2)
+        xo = O.project(inst, x, res[i]["alpha"])
+        assert _rel(xg, xo) <= 1e-4, (i, _rel(xg, xo))
+        assert (O.edge_loads(inst, xg) <= inst.capacity * (1 + 1e-5) + 1e-9).all()
+        trimmed += int((xg < x.astype(np.float32)).any())
+    assert trimmed > 0  # the iterates had violations to trim
+    b.close()
+
+
 def test_batch_stops_each_instance_by_its_own_rule(te, tiny):
     W = instances.make_what_if(tiny, 4, 1, seed=4)
     b = te.TEBatch(W, gamma=1e-3)

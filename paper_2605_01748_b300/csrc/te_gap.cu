@@ -1,4 +1,6 @@
-// Duality gap of a feasible allocation (FP64), for te_gap.
+// Duality gap of a feasible allocation (FP64, with the sums over a demand's
+// paths and their edges in pairs of FP32 numbers of about 48 bits), for
+// te_gap.
 //
 // For edge prices p_e >= 0 the Lagrangian dual of the TE problem (Eqs. 1-4)
 //   g(p) = sum_e p_e C_e + sum_c max_{0 <= S <= D_c} [U_alpha(S) - pi_c S],
@@ -36,6 +38,21 @@ __device__ __forceinline__ double conj_term(double D, double pi, double alpha) {
     else S = fmin(D, exp(-log(pi) / alpha));
     if (S <= 0.0) return utility(0.0, alpha);
     return utility(S, alpha) - pi * S;
+}
+
+// (hi, lo) += v as an unevaluated FP32 pair: two-sum of hi and v, the
+// rounding error added into lo
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
+    const float t = hi + v, bv = t - hi;
+    lo += (hi - (t - bv)) + (v - bv);
+    hi = t;
+}
+// hi + lo unchanged, |lo| at most half an ulp of hi (fast two-sum; |hi| >=
+// |lo| holds for the sums above)
+__device__ __forceinline__ void normalise(float& hi, float& lo) {
+    const float t = hi + lo;
+    lo = lo - (t - hi);
+    hi = t;
 }
 
 // CTA-wide sums of (a, b) in a fixed order: lanes by a butterfly, warps in
@@ -76,18 +93,32 @@ __global__ void k_gap_demands(Layout L, const float* x, const float* u, double p
         const int np = L.np[i];
         if (np > 0) {
             const int s0 = L.slotbase[b];
-            double S = 0.0, pi = INFINITY;
+            // The sums below are unevaluated pairs hi + lo of FP32 numbers
+            // (the rates and prices are FP32): each addition is split exactly
+            // into its rounded sum and its rounding error (Knuth's two-sum),
+            // the errors added into lo; a pair is then normalised (|lo| at
+            // most half an ulp of hi), so that pairs compare in the order of
+            // their values.  About 48 bits, near FP64, on the FP32 units:
+            // FP64 is a small fraction of them on this part, and these sums
+            // are most of the kernel's work.
+            float Sh = 0.f, Sl = 0.f, pih = INFINITY, pil = 0.f;
             for (int p = 0; p < np; ++p) {
                 const int lane = t * L.G + p % L.G;
                 const size_t sl = (size_t)(s0 + p / L.G);
-                S += (double)x[sl * kLanes + lane];
-                double q = 0.0;
+                two_sum_add(Sh, Sl, x[sl * kLanes + lane]);
+                float hi = 0.f, lo = 0.f;  // the path's price sum
                 for (unsigned r = L.rowoff[sl]; r < L.rowoff[sl + 1]; ++r) {
                     const IdT id = ids[(size_t)r * kLanes + lane];
-                    if ((int)id != L.E) q += (double)u[id];
+                    if ((int)id != L.E) two_sum_add(hi, lo, u[id]);
                 }
-                pi = fmin(pi, q);
+                normalise(hi, lo);
+                if (hi < pih || (hi == pih && lo < pil)) {
+                    pih = hi;
+                    pil = lo;
+                }
             }
+            normalise(Sh, Sl);
+            const double S = (double)Sh + (double)Sl, pi = (double)pih + (double)pil;
             pr = utility(S * scale, alpha);
             du = conj_term(Dc[i], pi * pscale, alpha);
         }

@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--feasibility", type=int, default=0, metavar="K",
                     help="time the two feasibility steps (Algorithm 2 and proportional scaling, device output) "
                          "on the iterate after K iterations of the default solver, one JSON line")
+    ap.add_argument("--alpha-fair", default="", metavar="ALPHAS",
+                    help="time to a duality-gap certificate of --cert-eps at each fixed alpha (e.g. 1,2)")
+    ap.add_argument("--cert-eps", type=float, default=1e-3)
     ap.add_argument("--iters", type=int, default=0,
                     help="profiling runs only: use this K and skip the reference run and the probe")
     return ap.parse_args()
@@ -949,6 +952,127 @@ def run_reference(a, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+def certified_eps(gap: float, primal: float, dual: float, alpha: float, n_demands: int) -> float:
+    """Unit-free bound on the distance of a feasible allocation to the exact
+    alpha-fair optimum U*, from the weak-duality bracket primal <= U* <= dual
+    (te_gap_projected).  alpha = 1: gap / n_demands bounds the mean of
+    log(S*_c / S_c) over demands (U is a sum of logarithms, so only its
+    differences are free of units).  alpha != 1: U_alpha(S) = (S^(1-alpha) -
+    1) / (1 - alpha) carries a constant -1 / (1 - alpha) per demand, which
+    the gap does not see; without it the objective is homogeneous in the
+    rates, so gap / min(|primal_h|, |dual_h|) with that constant removed
+    bounds (U*_h - U_h) / |U*_h| whatever the units (U_h and the bracket
+    share one sign)."""
+    if not math.isfinite(gap):
+        return math.inf
+    if alpha == 1.0:
+        return gap / max(n_demands, 1)
+    shift = n_demands / (1.0 - alpha)
+    lo, hi = primal + shift, dual + shift
+    if lo * hi <= 0.0:
+        return math.inf
+    return gap / min(abs(lo), abs(hi))
+
+
+def run_alpha_fair(a):
+    """alpha-fair objectives at fixed alpha (Eq. 4; no continuation) against
+    their exact optimum, certified by the duality gap: the Lagrangian dual at
+    the solver's prices bounds U* from above and the proportionally scaled
+    allocation from below, so certified_eps is an upper bound on the
+    distance to the exact optimum that needs no reference solve.  For each
+    alpha: the default solver with the stop rule off, probed every
+    --probe-every iterations (te_gap_projected) until certified_eps <=
+    --cert-eps, refined in steps of --refine-every, and that many iterations
+    timed as one step (te_reset, te_solve(K), te_allocation with scaling into
+    device memory, te_gap_projected: the certificate is part of the result);
+    beside it what the paper's stop rule (gamma 1e-3) leaves.  On the 200-node
+    and smaller workloads the FP64 oracle runs the same K iterations and its
+    certificate and allocation are compared.  One JSON line."""
+    import numpy as np
+    import torch
+    from paper_2605_01748_b300 import instances, te
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    inst = instances.make(a.workload, threads=os.cpu_count() or 0)
+    x = torch.empty(inst.n_paths, dtype=torch.float32, device=dev)
+    line = {"mode": "alpha-fair", "workload": workload_desc(inst),
+            "metric": f"ms to a duality-gap certificate within {a.cert_eps:g} of the exact alpha-fair optimum",
+            "unit": "ms", "certificate": "alpha = 1: gap / n_demands (mean log-ratio to the optimum); "
+                                         "else gap / min(|primal|, |dual|) (relative objective)"}
+    for alpha in [float(v) for v in a.alpha_fair.split(",")]:
+        fixed = dict(alpha_target=alpha, alpha_start=alpha, continuation=0)
+
+        def cert(t):
+            g, pr, du = t.gap(project=te.PROJECT_SCALE)
+            return certified_eps(g, pr, du, alpha, inst.n_demands), (g, pr, du)
+
+        row = {}
+        t = te.TE(inst, cuda_stream=st.cuda_stream, **fixed)
+        r = t.solve(a.ref_iters)
+        e_stop, _ = cert(t)
+        row["paper_stop_rule"] = {"iters": r["iters"], "converged": bool(r["converged"]), "certified_eps": e_stop}
+        t.close()
+        t = te.TE(inst, cuda_stream=st.cuda_stream, gamma=-1.0, **fixed)
+        first, lo, trace = None, 0, []
+        while True:
+            n = int(t.solve(a.probe_every)["total_iters"])
+            e, _ = cert(t)
+            trace.append((n, e))
+            if e <= a.cert_eps:
+                first = n
+                break
+            lo = n
+            if n >= a.ref_iters:
+                break
+        row["probe_tail"] = trace[-3:]
+        if first is not None:
+            t.reset()
+            t.solve(lo)
+            n = lo
+            while n < first:
+                n += a.refine_every
+                t.solve(a.refine_every)
+                if cert(t)[0] <= a.cert_eps:
+                    first = n
+                    break
+            ms = []
+            for i in range(a.warmup + a.steps):
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                t.reset()
+                rr = t.solve(first)
+                t.allocation(project=te.PROJECT_SCALE, out=x)
+                e, bracket = cert(t)
+                e1.record(st)
+                torch.cuda.synchronize()
+                if i >= a.warmup:
+                    ms.append(e0.elapsed_time(e1))
+            v = statistics.mean(ms)
+            row.update({"iters": first, "value": round(v, 3), "certified_eps": e,
+                        "gap_primal_dual": bracket, "iters_per_s": round(first / (v / 1e3), 1)})
+            if inst.n_paths <= 1_000_000:
+                from oracle import oracle as O
+                s = O.OracleSolver(inst, gamma=-1.0, threads=os.cpu_count() or 0, **fixed)
+                s.run(first)
+                xo = O.project_scale(inst, s.allocation())
+                go, pro, duo = O.gap(inst, xo, s.prices(), alpha)
+                xg = x.cpu().numpy().astype(np.float64)
+                Sg, So = O.demand_totals(inst, xg), O.demand_totals(inst, xo)
+                row["oracle_same_iters"] = {
+                    "certified_eps": certified_eps(go, pro, duo, alpha, inst.n_demands),
+                    "max_rel_err_rates": float(np.max(np.abs(xg - xo)) / max(np.max(np.abs(xo)), 1e-300)),
+                    "max_rel_err_demand_totals": float(np.max(np.abs(Sg - So)) / max(np.max(So), 1e-300)),
+                    "beta_gpu_oracle": [rr["beta"], s.beta]}
+        else:
+            row.update({"iters": None, "value": None})
+        t.close()
+        line[f"alpha={alpha:g}"] = row
+    print(json.dumps(line), flush=True)
+
+
 def run_steady(a):
     """Steady-state time per iteration of the iteration kernel at fixed
     alphas (no continuation, no stop, adaptive beta): CUDA events around
@@ -1020,6 +1144,8 @@ def main():
         run_feasibility(a)
     elif a.exact_k1:
         run_exact_k1(a)
+    elif a.alpha_fair:
+        run_alpha_fair(a)
     elif a.batch > 0:
         run_batch(a, ws, rank, dist)
     elif a.ablation:

@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--feasibility", type=int, default=0, metavar="K",
                     help="time the two feasibility steps (Algorithm 2 and proportional scaling, device output) "
                          "on the iterate after K iterations of the default solver, one JSON line")
+    ap.add_argument("--edge-mode", choices=["auto", "global"], default="auto",
+                    help="--steady: per-edge arrays of the iteration kernel in shared memory when they fit "
+                         "(auto) or always in global memory")
     ap.add_argument("--alpha-fair", default="", metavar="ALPHAS",
                     help="time to a duality-gap certificate of --cert-eps at each fixed alpha (e.g. 1,2)")
     ap.add_argument("--cert-eps", type=float, default=1e-3)
@@ -1087,7 +1090,8 @@ def run_steady(a):
     inst = instances.make(a.workload, threads=os.cpu_count() or 0)
     row = {}
     for alpha in [float(v) for v in a.steady.split(",")]:
-        t = te.TE(inst, alpha_target=alpha, alpha_start=alpha, gamma=-1.0, cuda_stream=st.cuda_stream)
+        t = te.TE(inst, alpha_target=alpha, alpha_start=alpha, gamma=-1.0, cuda_stream=st.cuda_stream,
+                  edge_mode=te.EDGES_GLOBAL if a.edge_mode == "global" else te.EDGES_AUTO)
         t.solve(60)
         best = math.inf
         for _ in range(3):
@@ -1100,7 +1104,8 @@ def run_steady(a):
             best = min(best, e0.elapsed_time(e1) * 1e3 / r["iters"])
         row[f"{alpha:g}"] = round(best, 1)
         t.close()
-    print(json.dumps({"mode": "steady", "workload": workload_desc(inst), "us_per_iter": row}), flush=True)
+    print(json.dumps({"mode": "steady", "workload": workload_desc(inst), "edge_mode": a.edge_mode,
+                      "us_per_iter": row}), flush=True)
 
 
 def run_feasibility(a):

@@ -131,7 +131,16 @@ typedef struct {
     int32_t precision;    /* arithmetic of the iteration: TE_PRECISION_FP32
                              (the only value; FP32 rates and prices, FP64
                              residual sums, gap and stop test)                */
-    int32_t reserved;
+    int32_t edge_mode;    /* where the iteration kernel keeps each CTA's copy
+                             of the per-edge arrays (gather weights w_e and the
+                             load histogram of Eq. 9): TE_EDGES_AUTO (0,
+                             default) shared memory when they fit (about
+                             10,770 edges), else global memory (L2);
+                             TE_EDGES_GLOBAL (1) global memory always.  Both
+                             give the same bits; the global mode takes one
+                             64-bit L2 atomic per path-edge incidence instead
+                             of two shared-memory ones and needs
+                             deterministic = 1 (else TE_EUNSUPPORTED)        */
     void* cuda_stream;    /* cudaStream_t to run on; NULL = default stream     */
 } te_options;
 
@@ -141,6 +150,12 @@ enum {
                               demand multipliers); the residual norms (Eqs.
                               15-16), their cross-CTA sums, the balancing and
                               stop decisions (Eqs. 17-18) and the gap in FP64 */
+};
+
+/* te_options.edge_mode */
+enum {
+    TE_EDGES_AUTO = 0,   /* shared memory when the per-edge arrays fit, else global */
+    TE_EDGES_GLOBAL = 1  /* global memory (L2) always                             */
 };
 
 /* Outcome of a te_solve call. */
@@ -165,9 +180,11 @@ void te_default_options(te_options* opt);
  * input buffer (they are copied).  demands: host [n_demands], finite and
  * > 0; capacities: host [n_edges], finite and >= 0, and > 0 on every edge
  * used by a path (Slater's condition, Appendix C).  Limits: at most 32 paths
- * per demand, at most 255 edges per path, at most about 10,770 edges (the
- * iteration kernel keeps the per-edge weights and load histograms of every
- * edge in each CTA's shared memory; more return TE_EUNSUPPORTED).  On success *out
+ * per demand, at most 255 edges per path, at most 65,534 edges (the device
+ * layout stores 16-bit edge ids; more return TE_EUNSUPPORTED).  Above about
+ * 10,770 edges the per-edge arrays of the iteration kernel no longer fit a
+ * CTA's shared memory and it keeps them in global memory (edge_mode; such
+ * instances need deterministic = 1).  On success *out
  * receives a new handle.  Errors: TE_EINVAL (bad input; message names the
  * first offending index), TE_EUNSUPPORTED, TE_ENOMEM, TE_ECUDA. */
 te_status te_create(const te_topology* topo, const te_paths* paths, const double* demands,

@@ -88,6 +88,9 @@ struct te_handle {
     float* u_next = nullptr;  // [E]
     float* w_next = nullptr;  // [E]
     uint2* loads = nullptr;   // [grid*E] per-CTA partial loads
+    bool wide = false;        // per-edge arrays of the iteration kernel in global memory
+    unsigned long long* hist64 = nullptr;  // [grid*(E+1)] wide mode: per-CTA load histograms
+    float* wpriv = nullptr;                // [grid*(E+1)] wide mode: per-CTA gather weights
     double* part = nullptr;   // [2*grid*kPartWidth]
     unsigned* barrier = nullptr;
     int* status = nullptr;
@@ -155,6 +158,7 @@ void te_default_options(te_options* o) {
     o->test_withhold_cta = 0;
     o->deterministic = 1;
     o->precision = TE_PRECISION_FP32;
+    o->edge_mode = TE_EDGES_AUTO;
     o->cuda_stream = nullptr;
 }
 
@@ -258,6 +262,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     if (opt_in) opt = *opt_in; else te_default_options(&opt);
     if (!(opt.gamma == opt.gamma) || !(opt.beta0 == opt.beta0) || !(opt.balance_floor >= 0.0) || !(opt.gamma_max == opt.gamma_max) || !(opt.beta_max >= 0.0) || !(opt.C > 1.0) || !(opt.A > 0.0) ||
         (opt.scale_mode < 0 || opt.scale_mode > 2) || (opt.deterministic != 0 && opt.deterministic != 1) ||
+        (opt.edge_mode != TE_EDGES_AUTO && opt.edge_mode != TE_EDGES_GLOBAL) ||
         !(opt.alpha_step > 0.0) || opt.alpha_start < 0.0 || opt.alpha_target < 0.0 || opt.alpha_max < 0.0) {
         g_create_error = "invalid options";
         return TE_EINVAL;
@@ -331,11 +336,19 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     te_status st;
     if ((st = h->cuda(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device), "device query")))
         return bail(st);
-    if (te::iter_smem_bytes(E, nsm, opt.deterministic != 0) > 227 * 1024) {
-        h->err = fmt("n_edges = %lld needs more shared memory than a CTA has (limit about 10770 edges)", E);
+    // per-edge arrays of the iteration kernel in shared memory when they fit,
+    // else (or when asked) in global memory
+    h->wide = opt.edge_mode == TE_EDGES_GLOBAL || te::iter_smem_bytes(E, nsm, opt.deterministic != 0) > 227 * 1024;
+    if (h->wide && opt.deterministic == 0) {
+        h->err = fmt("n_edges = %lld: the per-edge arrays exceed a CTA's shared memory (about 10770 edges) or "
+                     "edge_mode asks for global memory, which needs deterministic = 1", E);
         return bail(TE_EUNSUPPORTED);
     }
-    if ((st = h->cuda(te::iter_occupancy(G, opt.deterministic != 0, E, nsm, &bps), "occupancy query"))) return bail(st);
+    if (h->wide) {
+        if ((st = h->cuda(te::iter_occupancy_wide(G, E, nsm, &bps), "occupancy query"))) return bail(st);
+    } else if ((st = h->cuda(te::iter_occupancy(G, opt.deterministic != 0, E, nsm, &bps), "occupancy query"))) {
+        return bail(st);
+    }
     if (bps < 1) { h->err = "iteration kernel does not fit on an SM"; return bail(TE_EUNSUPPORTED); }
     h->grid = nsm * bps;
 
@@ -369,7 +382,12 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     A(h->alloc(&h->w, sizeof(float) * E));
     A(h->alloc(&h->u_next, sizeof(float) * E));
     A(h->alloc(&h->w_next, sizeof(float) * E));
-    A(h->alloc(&h->loads, sizeof(uint2) * (size_t)h->grid * (size_t)E));
+    if (h->wide) {
+        A(h->alloc(&h->hist64, sizeof(unsigned long long) * (size_t)h->grid * (size_t)(E + 1)));
+        A(h->alloc(&h->wpriv, sizeof(float) * (size_t)h->grid * (size_t)(E + 1)));
+    } else {
+        A(h->alloc(&h->loads, sizeof(uint2) * (size_t)h->grid * (size_t)E));
+    }
     A(h->alloc(&h->part, sizeof(double) * 2 * te::kPartWidth * (size_t)h->grid));
     A(h->alloc(&h->barrier, sizeof(unsigned)));
     A(h->alloc(&h->status, sizeof(int)));
@@ -509,6 +527,8 @@ extern "C" te_status te_solve(te_handle* h, int64_t max_iters, double tol, te_so
         a.u = h->u;
         a.w = h->w;
         a.loads = h->loads;
+        a.hist64 = h->hist64;
+        a.wpriv = h->wpriv;
         a.part = h->part;
         a.barrier = h->barrier;
         a.status = h->status;

@@ -127,6 +127,12 @@ struct IterArgs {
     long long max_iters;
     long long timeout_ns;  // bound on every wait (the grid barriers)
     long long xstride;     // floats between the two rate buffers (0: nslots*32)
+    // wide-edge mode (instances whose per-edge arrays do not fit a CTA's
+    // shared memory): each CTA's load histogram, one 64-bit fixed-point word
+    // per edge in units of 2^-24, and its copy of the gather weights live in
+    // global memory; nullptr otherwise
+    unsigned long long* hist64;  // [grid*(E+1)]
+    float* wpriv;                // [grid*(E+1)]
 };
 
 // Device status codes (mirror te_status).
@@ -135,7 +141,10 @@ constexpr int kStatusNumeric = 5;
 
 // Launchers (host side), defined in te_iter.cu / te_proj.cu / te_gap.cu.
 size_t iter_smem_bytes(int E, int grid, bool det);
+// The same for the wide-edge mode (staging buffers and the price slice only).
+size_t iter_smem_bytes_wide(int E, int grid);
 cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_per_sm);
+cudaError_t iter_occupancy_wide(int G, int E, int grid_hint, int* blocks_per_sm);
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st);
 // Several independent instances in one cooperative launch of the iteration
 // kernel (deterministic loads): instance i runs on CTAs i*group ..

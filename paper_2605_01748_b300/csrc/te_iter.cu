@@ -48,9 +48,17 @@ namespace {
 // CTA c takes instance c / group, whose arguments it reads from group_args
 // (each instance has its own barrier counter, scalars and scratch); else the
 // whole grid runs the one instance of a_param.
-template <int G, bool DET, bool GROUPED>
+// WIDE (with DET, not GROUPED): the wide-edge mode for instances whose
+// per-edge arrays do not fit shared memory.  Each CTA keeps its gather
+// weights (a.wpriv) and its load histogram (a.hist64: one 64-bit
+// fixed-point word per edge, units of 2^-24, one 64-bit atomic per
+// incidence into L2) in its own slice of global memory; phase B sums the
+// CTAs' words exactly, so the loads, and the whole run, are bit-identical
+// to the shared-memory mode on the same instance.
+template <int G, bool DET, bool GROUPED, bool WIDE = false>
 __global__ void __launch_bounds__(kIterThreads, 1)
     k_iter(IterArgs a_param, const IterArgs* __restrict__ group_args, int group) {
+    static_assert(!WIDE || (DET && !GROUPED), "the wide-edge mode has deterministic loads and one instance");
     extern __shared__ __align__(128) unsigned smem[];
     __shared__ IterArgs s_args;
     if (GROUPED) {
@@ -62,11 +70,16 @@ __global__ void __launch_bounds__(kIterThreads, 1)
     const int NG = GROUPED ? group : (int)gridDim.x;  // CTAs of this instance
     const int cta = GROUPED ? (int)(blockIdx.x % group) : (int)blockIdx.x;  // this CTA's rank among them
     // dynamic shared memory: histogram, gather weights, staging, price slice
-    unsigned* h_hi = smem;                                           // [E+1] units of 2^-12 (DET), else FP32
-    unsigned* h_lo = DET ? h_hi + (E + 1) : nullptr;                 // [E+1] units of 2^-24 (DET)
-    float* w_s = reinterpret_cast<float*>(h_hi + (DET ? 2 : 1) * (E + 1));  // [E+1], w_s[E] = 0
-    uint16_t* stage = reinterpret_cast<uint16_t*>(
-        reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) & ~uintptr_t(127));  // [warps][2][kIterStageRows*32]
+    // (WIDE: staging and price slice; histogram and weights in global memory)
+    unsigned* h_hi = WIDE ? reinterpret_cast<unsigned*>(a.hist64 + (size_t)cta * (E + 1))
+                          : smem;                                    // [E+1] units of 2^-12 (DET), else FP32
+    unsigned long long* h64 = WIDE ? a.hist64 + (size_t)cta * (E + 1) : nullptr;  // [E+1] units of 2^-24 (WIDE)
+    unsigned* h_lo = (DET && !WIDE) ? h_hi + (E + 1) : nullptr;      // [E+1] units of 2^-24 (DET)
+    float* w_s = WIDE ? a.wpriv + (size_t)cta * (E + 1)
+                      : reinterpret_cast<float*>(h_hi + (DET ? 2 : 1) * (E + 1));  // [E+1], w_s[E] = 0
+    uint16_t* stage = WIDE ? reinterpret_cast<uint16_t*>(smem)
+                           : reinterpret_cast<uint16_t*>(reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) &
+                                                         ~uintptr_t(127));  // [warps][2][kIterStageRows*32]
     float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kIterStageRows * kLanes);  // price slice
     const int e_lo = (int)((long long)cta * E / NG), e_hi = (int)((long long)(cta + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
@@ -87,14 +100,22 @@ __global__ void __launch_bounds__(kIterThreads, 1)
 
     for (int e = tid; e < E; e += kIterThreads) {
         w_s[e] = a.w[e];
-        h_hi[e] = 0u;  // also FP32 +0
-        if (DET) h_lo[e] = 0u;
+        if (WIDE) {
+            h64[e] = 0ull;
+        } else {
+            h_hi[e] = 0u;  // also FP32 +0
+            if (DET) h_lo[e] = 0u;
+        }
     }
     for (int e = e_lo + tid; e < e_hi; e += kIterThreads) s_u[e - e_lo] = a.u[e];
     if (tid == 0) {
         w_s[E] = 0.f;
-        h_hi[E] = 0u;
-        if (DET) h_lo[E] = 0u;
+        if (WIDE) {
+            h64[E] = 0ull;
+        } else {
+            h_hi[E] = 0u;
+            if (DET) h_lo[E] = 0u;
+        }
     }
     // the scalar state is kept by thread 0, which takes the control
     // decisions (FP64 is slow on this part: one thread does it and the CTA
@@ -134,8 +155,8 @@ __global__ void __launch_bounds__(kIterThreads, 1)
         LaneRes acc;
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.hops, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows, true, true, DET>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws, w_s,
-                                                h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
+            run_blocks<G, kIterStageRows, true, true, DET, WIDE>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws,
+                                                w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         {
             // this warp's residual partials: each lane's compensated sums in
@@ -155,8 +176,10 @@ __global__ void __launch_bounds__(kIterThreads, 1)
             }
         }
         __syncthreads();
-        // publish this CTA's partial loads
-        if (DET) {
+        // publish this CTA's partial loads (WIDE: they are in global memory
+        // already, and are cleared after the second grid barrier)
+        if (WIDE) {
+        } else if (DET) {
             uint2* Lp = a.loads + (size_t)cta * E;
             #pragma unroll 4
             for (int e = tid; e < E; e += kIterThreads) {
@@ -223,11 +246,17 @@ __global__ void __launch_bounds__(kIterThreads, 1)
                         const int e = c0 + tid % ns;
                         // all of a thread's partials in flight at once (about NG /
                         // per of them: one L2 round trip instead of several)
-                        #pragma unroll 16
-                        for (int c = tid / ns; c < NG; c += per) {
-                            const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
-                            sh += v.x;
-                            sl += v.y;
+                        if (WIDE) {
+                            // the CTAs' words in units of 2^-24 (sh); sl stays 0
+                            #pragma unroll 16
+                            for (int c = tid / ns; c < NG; c += per) sh += __ldcg(&a.hist64[(size_t)c * (E + 1) + e]);
+                        } else {
+                            #pragma unroll 16
+                            for (int c = tid / ns; c < NG; c += per) {
+                                const uint2 v = __ldcg(&a.loads[(size_t)c * E + e]);
+                                sh += v.x;
+                                sl += v.y;
+                            }
                         }
                     }
                     s_L[tid] = sh;
@@ -263,8 +292,12 @@ __global__ void __launch_bounds__(kIterThreads, 1)
                     const int e = c0 + tid;
                     const float ne = __ldg(&a.L.ne_f[e]);
                     const float u = s_u[e - e_lo];
-                    const float L = DET ? (float)((double)s_L[tid] * 0x1p-12 + (double)s_L[kIterThreads + tid] * 0x1p-24)
-                                        : (float)s_Ld[tid];
+                    // (WIDE: one exact sum in units of 2^-24; the same value as the
+                    // split sum, both being the correctly rounded FP64 of the
+                    // same integer multiple of 2^-24)
+                    const float L = WIDE  ? (float)((double)s_L[tid] * 0x1p-24)
+                                    : DET ? (float)((double)s_L[tid] * 0x1p-12 + (double)s_L[kIterThreads + tid] * 0x1p-24)
+                                          : (float)s_Ld[tid];
                     float un = 0.f;
                     const float cap = __ldg(&a.L.cap_n[e]);
                     if (ne > 0.f) un = fmaxf(0.f, fmaf(L - cap, __ldg(&a.L.inv_ne[e]), u));
@@ -383,9 +416,13 @@ __global__ void __launch_bounds__(kIterThreads, 1)
             }
         } else {
             // meanwhile the other warps load the next gather weights w = u'
-            // + d (w_s is not read again before phase A)
+            // + d (w_s is not read again before phase A); WIDE: and clear
+            // this CTA's histogram, which every CTA has read in phase B
             #pragma unroll 16
-            for (int e = tid - 32; e < E; e += kIterThreads - 32) w_s[e] = __ldcg(&a.w_next[e]);
+            for (int e = tid - 32; e < E; e += kIterThreads - 32) {
+                w_s[e] = __ldcg(&a.w_next[e]);
+                if (WIDE) __stcg(&h64[e], 0ull);
+            }
         }
         __syncthreads();
         // commit the slice's new prices (scaled with beta); when beta changed,
@@ -443,6 +480,29 @@ cudaError_t launch_iter_t(const IterArgs& a, int grid, cudaStream_t st) {
 }
 
 template <int G>
+cudaError_t launch_iter_wide_t(const IterArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = iter_smem_bytes_wide(a.L.E, grid);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_iter<G, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    IterArgs args = a;
+    const IterArgs* none = nullptr;
+    int group = 0;
+    void* params[] = {&args, &none, &group};
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G, true, false, true>, dim3(grid), dim3(kIterThreads),
+                                       params, smem, st);
+}
+
+template <int G>
+cudaError_t occupancy_wide_t(int E, int grid_hint, int* blocks) {
+    const size_t smem = iter_smem_bytes_wide(E, grid_hint);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_iter<G, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G, true, false, true>, kIterThreads, smem);
+}
+
+template <int G>
 cudaError_t launch_iter_grouped_t(const IterArgs* args_dev, int n, int group, int E, cudaStream_t st) {
     const size_t smem = iter_smem_bytes(E, group, true);
     cudaError_t err =
@@ -478,6 +538,22 @@ size_t iter_smem_bytes(int E, int grid, bool det) {
     return b;
 }
 
+size_t iter_smem_bytes_wide(int E, int grid) {
+    size_t b = (size_t)kIterWarps * 2 * kIterStageRows * kLanes * sizeof(uint16_t);
+    const int slice = (E + grid - 1) / (grid > 0 ? grid : 1) + 1;
+    b += 2 * (size_t)slice * sizeof(float);
+    return b;
+}
+
+cudaError_t iter_occupancy_wide(int G, int E, int grid_hint, int* blocks_per_sm) {
+    switch (G) {
+        case 1: return occupancy_wide_t<1>(E, grid_hint, blocks_per_sm);
+        case 2: return occupancy_wide_t<2>(E, grid_hint, blocks_per_sm);
+        case 4: return occupancy_wide_t<4>(E, grid_hint, blocks_per_sm);
+        default: return occupancy_wide_t<8>(E, grid_hint, blocks_per_sm);
+    }
+}
+
 cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_per_sm) {
     if (det) {
         switch (G) {
@@ -496,6 +572,14 @@ cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_pe
 }
 
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
+    if (a.hist64) {
+        switch (a.L.G) {
+            case 1: return launch_iter_wide_t<1>(a, grid, st);
+            case 2: return launch_iter_wide_t<2>(a, grid, st);
+            case 4: return launch_iter_wide_t<4>(a, grid, st);
+            default: return launch_iter_wide_t<8>(a, grid, st);
+        }
+    }
     if (a.o.deterministic) {
         switch (a.L.G) {
             case 1: return launch_iter_t<1, true>(a, grid, st);

@@ -312,7 +312,10 @@ __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int l
 // integer atomics per incidence, order-free); else h_hi is an FP32
 // histogram and each rate is added by one FP32 shared atomic per incidence
 // (the sum then depends on the order of the atomics in its last bits).
-template <int G, bool STAGED, bool ACC, bool HOPS, bool DET>
+// GH (with DET): the histogram is one 64-bit word per edge in global memory,
+// h_hi read as unsigned long long*, and each rate adds the same fixed-point
+// value hi * 2^12 + lo (units of 2^-24) by one 64-bit atomic; h_lo unused.
+template <int G, bool STAGED, bool ACC, bool HOPS, bool DET, bool GH = false>
 __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane, const uint16_t* bids, int s0,
                                               unsigned counts, int KB, const BlockIn& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
@@ -396,11 +399,18 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
                 // no per-row branch: padding entries (the sentinel id E) add
                 // into the unused histogram slot E.  Unrolled by 8 (measured:
                 // 1.5-3 % less time per iteration than by 4 or 6)
-                #pragma unroll 8
-                for (unsigned r = 0; r < cnt; ++r) {
-                    const uint16_t id = id_at(rs + r);
-                    atomicAdd(&h_hi[id], hi);
-                    atomicAdd(&h_lo[id], lo);
+                if (GH) {
+                    unsigned long long* h64 = reinterpret_cast<unsigned long long*>(h_hi);
+                    const unsigned long long v = ((unsigned long long)hi << 12) + lo;
+                    #pragma unroll 8
+                    for (unsigned r = 0; r < cnt; ++r) atomicAdd(&h64[id_at(rs + r)], v);
+                } else {
+                    #pragma unroll 8
+                    for (unsigned r = 0; r < cnt; ++r) {
+                        const uint16_t id = id_at(rs + r);
+                        atomicAdd(&h_hi[id], hi);
+                        atomicAdd(&h_lo[id], lo);
+                    }
                 }
             }
             rs += cnt;
@@ -465,8 +475,8 @@ __device__ __forceinline__ uint16_t* stage_buf(const WarpStage& ws, int k) {
 //
 // ACC (see process_block): the residual terms of the warp's blocks are summed
 // per lane into acc (compensated), in the fixed order of the interleave.  HOPS
-// and DET: see process_block.
-template <int G, int ROWS, bool ACC, bool HOPS, bool DET>
+// and DET: see process_block.  GH: see process_block.
+template <int G, int ROWS, bool ACC, bool HOPS, bool DET, bool GH = false>
 __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __restrict__ blkmeta,
                            const uint16_t* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
@@ -539,11 +549,11 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
             // lane; the __syncwarp makes each lane's copies visible to all
             cp_async_wait_prev();
             __syncwarp();
-            process_block<G, true, ACC, HOPS, DET>(bc, b0, lane, stage_buf<ROWS>(ws, cur), s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
+            process_block<G, true, ACC, HOPS, DET, GH>(bc, b0, lane, stage_buf<ROWS>(ws, cur), s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                         inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         } else {
             const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
-            process_block<G, false, ACC, HOPS, DET>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
+            process_block<G, false, ACC, HOPS, DET, GH>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
                                          w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         b0 = b1;

@@ -29,6 +29,8 @@ TE_OK, TE_EINVAL, TE_ENOMEM, TE_ECUDA, TE_ETIMEOUT, TE_ENUMERIC, TE_ENOTCONVERGE
 PROJECT_NONE, PROJECT_ALG2, PROJECT_SCALE = 0, 1, 2
 # te_options.precision
 PRECISION_FP32 = 0
+# te_options.edge_mode: per-edge arrays of the iteration kernel in shared memory when they fit, or always global
+EDGES_AUTO, EDGES_GLOBAL = 0, 1
 STATUS_NAMES = {0: "TE_OK", 1: "TE_EINVAL", 2: "TE_ENOMEM", 3: "TE_ECUDA", 4: "TE_ETIMEOUT",
                 5: "TE_ENUMERIC", 6: "TE_ENOTCONVERGED", 7: "TE_EUNSUPPORTED"}
 
@@ -65,7 +67,7 @@ class te_options(ctypes.Structure):
                 ("adapt_beta", ctypes.c_int32), ("continuation", ctypes.c_int32),
                 ("scale_mode", ctypes.c_int32), ("wait_timeout_ms", ctypes.c_int32),
                 ("test_withhold_cta", ctypes.c_int32), ("deterministic", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("edge_mode", ctypes.c_int32),
                 ("cuda_stream", ctypes.c_void_p)]
 
 

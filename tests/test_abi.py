@@ -131,6 +131,14 @@ def test_create_rejects_unsupported_precision(te, tiny):
     assert ei.value.status == te.TE_EINVAL
 
 
+def test_edge_mode_default_and_checked(te, tiny):
+    o = te.te_default_options()
+    assert o.edge_mode == te.EDGES_AUTO
+    with pytest.raises(te.TEError) as ei:
+        te.te_create(tiny, te.te_default_options(edge_mode=2))
+    assert ei.value.status == te.TE_EINVAL
+
+
 def test_solve_rejects_null_handle(te):
     res = te.te_solve_result()
     assert te.lib().te_solve(None, 10, -1.0, ctypes.byref(res)) == te.TE_EINVAL

@@ -1,0 +1,137 @@
+"""The iteration kernel with its per-edge arrays in global memory (the wide-
+edge mode, te_options.edge_mode), through the C-ABI.
+
+On instances that also fit shared memory, the global mode must give the same
+bits as the shared-memory mode: the loads of Eq. 9 are exact integer sums in
+both, so the whole run (rates, prices, beta and alpha decisions, residuals)
+is identical.  On instances with more edges than a CTA's shared memory holds
+(about 10,770), te_create takes the global mode by itself, and the iterate
+must match the FP64 oracle within the 1e-4 bar of the other parity tests.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def te():
+    from paper_2605_01748_b300 import build
+    build.build_te()
+    from paper_2605_01748_b300 import te as te_mod
+    return te_mod
+
+
+def _rel_inf(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _scaled(inst, name):
+    # demands scaled to half the total capacity, as the generator does for
+    # all pairs, so that capacities bind on the subset too
+    D = inst.demand * (0.5 * inst.capacity.sum() / inst.demand.sum())
+    return dataclasses.replace(inst, name=name, demand=D)
+
+
+@pytest.fixture(scope="module")
+def wide_11k():
+    # 1000-node WAN, 5,713 links = 11,426 directed edges, all pairs, k = 2
+    from paper_2605_01748_b300 import instances
+    return instances.make_waxman("wide-11k", 1000, 5800, 2, seed=0, locality=instances.LARGE_LOCALITY)
+
+
+@pytest.fixture(scope="module")
+def wide_30k():
+    # 3000-node WAN, 15,111 links = 30,222 directed edges; 60,000 of its
+    # 9M ordered pairs (k = 1), demands rescaled to half the total capacity
+    from paper_2605_01748_b300 import instances
+    full = instances.make_waxman("wide-30k", 3000, 15000, 1, seed=1, locality=instances.LARGE_LOCALITY)
+    rng = np.random.default_rng(0)
+    sub = instances.subset(full, np.sort(rng.choice(full.n_demands, 60000, replace=False)))
+    return _scaled(sub, "wide-30k-sub")
+
+
+def _same_run(te, inst, iters, **kw):
+    a = te.TE(inst, **kw)
+    b = te.TE(inst, edge_mode=te.EDGES_GLOBAL, **kw)
+    ra, rb = a.solve(iters), b.solve(iters)
+    for k in ("iters", "total_iters", "r", "s", "beta", "alpha", "converged"):
+        assert ra[k] == rb[k], (k, ra[k], rb[k])
+    xa, xb = a.allocation(project=te.PROJECT_NONE), b.allocation(project=te.PROJECT_NONE)
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(a.prices(), b.prices())
+    assert np.array_equal(a.trace(), b.trace())
+    # the feasibility steps and the gap read only the iterate and the prices
+    for proj in (te.PROJECT_ALG2, te.PROJECT_SCALE):
+        assert np.array_equal(a.allocation(project=proj), b.allocation(project=proj))
+    assert a.gap(project=te.PROJECT_SCALE) == b.gap(project=te.PROJECT_SCALE)
+    a.close()
+    b.close()
+
+
+def test_global_mode_bit_identical_tiny(te, tiny):
+    _same_run(te, tiny, 3000)
+
+
+def test_global_mode_bit_identical_medium(te, medium):
+    _same_run(te, medium, 600)
+
+
+@pytest.mark.parametrize("alpha", [0.0, 1.0, 2.0])
+def test_wide_instance_fixed_schedule_parity(te, wide_11k, alpha):
+    assert wide_11k.n_edges > 10770
+    kw = dict(alpha_target=alpha, alpha_start=alpha, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t = te.TE(wide_11k, **kw)
+    assert t.solve(40)["iters"] == 40
+    s = O.OracleSolver(wide_11k, **kw)
+    s.run(40)
+    x, xr = t.allocation(project=te.PROJECT_NONE), s.allocation()
+    assert _rel_inf(x, xr) <= TOL
+    Sg, Sr = O.demand_totals(wide_11k, x), O.demand_totals(wide_11k, xr)
+    assert (np.abs(Sg - Sr) / np.maximum(Sr, 1e-2 * Sr.max())).max() <= TOL
+    assert _rel_inf(t.prices(), s.prices()) <= TOL
+    t.close()
+
+
+def test_wide_instance_parity_and_feasibility(te, wide_30k):
+    assert wide_30k.n_edges > 30000
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t = te.TE(wide_30k, **kw)
+    t.solve(40)
+    s = O.OracleSolver(wide_30k, **kw)
+    s.run(40)
+    assert _rel_inf(t.allocation(project=te.PROJECT_NONE), s.allocation()) <= TOL
+    assert _rel_inf(t.prices(), s.prices()) <= TOL
+    t.close()
+    # the default solve (balancing, continuation, stop rule), then both
+    # feasibility steps on its iterate
+    t = te.TE(wide_30k)
+    t.solve(5000)
+    x = t.allocation(project=te.PROJECT_NONE)
+    for proj in (te.PROJECT_ALG2, te.PROJECT_SCALE):
+        xp = t.allocation(project=proj).astype(np.float64)
+        loads = O.edge_loads(wide_30k, xp)
+        assert (xp >= 0).all() and (loads <= wide_30k.capacity * (1 + 1e-5)).all()
+        assert (O.demand_totals(wide_30k, xp) <= wide_30k.demand * (1 + 1e-5)).all()
+    xs = O.project_scale(wide_30k, x.astype(np.float64))
+    assert _rel_inf(t.allocation(project=te.PROJECT_SCALE), xs) <= 1e-5
+    t.close()
+
+
+def test_global_mode_needs_deterministic_loads(te, tiny, wide_30k):
+    # FP32 histograms (4 B per edge instead of 8) fit shared memory up to
+    # about 15,600 edges; 30,222 do not, and the global mode has no FP32 form
+    with pytest.raises(te.TEError) as ei:
+        te.TE(wide_30k, deterministic=0)
+    assert ei.value.status == te.TE_EUNSUPPORTED
+    with pytest.raises(te.TEError) as ei:
+        te.TE(tiny, deterministic=0, edge_mode=te.EDGES_GLOBAL)
+    assert ei.value.status == te.TE_EUNSUPPORTED

@@ -140,7 +140,8 @@ typedef struct {
                              give the same bits; the global mode takes one
                              64-bit L2 atomic per path-edge incidence instead
                              of two shared-memory ones and needs
-                             deterministic = 1 (else TE_EUNSUPPORTED)        */
+                             deterministic = 1 (else TE_EUNSUPPORTED); above
+                             65,534 edges (32-bit ids) it is the only mode   */
     void* cuda_stream;    /* cudaStream_t to run on; NULL = default stream     */
 } te_options;
 
@@ -180,11 +181,11 @@ void te_default_options(te_options* opt);
  * input buffer (they are copied).  demands: host [n_demands], finite and
  * > 0; capacities: host [n_edges], finite and >= 0, and > 0 on every edge
  * used by a path (Slater's condition, Appendix C).  Limits: at most 32 paths
- * per demand, at most 255 edges per path, at most 65,534 edges (the device
- * layout stores 16-bit edge ids; more return TE_EUNSUPPORTED).  Above about
- * 10,770 edges the per-edge arrays of the iteration kernel no longer fit a
- * CTA's shared memory and it keeps them in global memory (edge_mode; such
- * instances need deterministic = 1).  On success *out
+ * per demand, at most 255 edges per path.  Above about 10,770 edges the
+ * per-edge arrays of the iteration kernel no longer fit a CTA's shared
+ * memory and it keeps them in global memory (edge_mode; such instances need
+ * deterministic = 1); above 65,534 edges the device layout stores 32-bit
+ * edge ids instead of 16-bit ones.  On success *out
  * receives a new handle.  Errors: TE_EINVAL (bad input; message names the
  * first offending index), TE_EUNSUPPORTED, TE_ENOMEM, TE_ECUDA. */
 te_status te_create(const te_topology* topo, const te_paths* paths, const double* demands,
@@ -317,7 +318,8 @@ te_status te_layout(const te_handle* h, te_layout_info* info);
  * time.  Uses device memory of about
  * (K/checkpoint_every + checkpoint_every + 2) times the iterate (released
  * before returning).  The handle's state afterwards is that of an
- * intermediate iteration: call te_reset before solving again. */
+ * intermediate iteration: call te_reset before solving again.  Instances of
+ * more than 65,534 edges return TE_EUNSUPPORTED. */
 te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint_every, double* J_out, double* dJ_dC,
                       double* dJ_dD, int32_t out_is_device);
 

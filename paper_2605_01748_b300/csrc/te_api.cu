@@ -322,13 +322,15 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     // ---------------- sliced layout ----------------
     te::HostLayout hl;
     {
-        const te_status ls = te::build_host_layout(topo, P, D, C, scale, 1, hl);
+        const te_status ls = te::build_host_layout(topo, P, D, C, scale, 1, hl, 4);
         if (ls != TE_OK) { h->err = hl.err; return bail(ls); }
     }
     const int G = hl.G, DPB = hl.dpb, kl = hl.kl, kmax = hl.kmax, nblocks = hl.nblocks;
     const int max_block_rows = hl.max_block_rows;
     const long long nslots = hl.nslots, nrows = hl.nrows;
-    const int id_bytes = 2;
+    const int id_bytes = hl.id_bytes;  // 4 above 65,534 edges (wide-edge mode only)
+    const size_t n_ids = id_bytes == 4 ? hl.ids32.size() : hl.ids.size();
+    const void* h_ids = id_bytes == 4 ? (const void*)hl.ids32.data() : (const void*)hl.ids.data();
     const size_t ND = (size_t)nblocks * DPB;  // demand slots
 
     // ---------------- persistent grid ----------------
@@ -338,14 +340,15 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
         return bail(st);
     // per-edge arrays of the iteration kernel in shared memory when they fit,
     // else (or when asked) in global memory
-    h->wide = opt.edge_mode == TE_EDGES_GLOBAL || te::iter_smem_bytes(E, nsm, opt.deterministic != 0) > 227 * 1024;
+    h->wide = opt.edge_mode == TE_EDGES_GLOBAL || id_bytes == 4 ||
+              te::iter_smem_bytes(E, nsm, opt.deterministic != 0) > 227 * 1024;
     if (h->wide && opt.deterministic == 0) {
         h->err = fmt("n_edges = %lld: the per-edge arrays exceed a CTA's shared memory (about 10770 edges) or "
                      "edge_mode asks for global memory, which needs deterministic = 1", E);
         return bail(TE_EUNSUPPORTED);
     }
     if (h->wide) {
-        if ((st = h->cuda(te::iter_occupancy_wide(G, E, nsm, &bps), "occupancy query"))) return bail(st);
+        if ((st = h->cuda(te::iter_occupancy_wide(G, id_bytes, E, nsm, &bps), "occupancy query"))) return bail(st);
     } else if ((st = h->cuda(te::iter_occupancy(G, opt.deterministic != 0, E, nsm, &bps), "occupancy query"))) {
         return bail(st);
     }
@@ -364,7 +367,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     const size_t ns = (size_t)nslots * kLanes;
     cudaError_t ce = cudaSuccess;
     auto A = [&](cudaError_t e) { if (ce == cudaSuccess) ce = e; };
-    A(h->alloc(&d_ids, sizeof(uint16_t) * hl.ids.size()));
+    A(h->alloc(&d_ids, (size_t)id_bytes * n_ids));
     A(h->alloc(&d_rowoff, sizeof(unsigned) * hl.rowoff.size()));
     A(h->alloc(&d_slotbase, sizeof(int) * hl.slotbase.size()));
     A(h->alloc(&d_demand_of, sizeof(int) * ND));
@@ -424,7 +427,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
         return bail(ce == cudaErrorMemoryAllocation ? TE_ENOMEM : TE_ECUDA);
     }
     cudaStream_t s = h->stream;
-    A(cudaMemcpyAsync(d_ids, hl.ids.data(), sizeof(uint16_t) * hl.ids.size(), cudaMemcpyHostToDevice, s));
+    A(cudaMemcpyAsync(d_ids, h_ids, (size_t)id_bytes * n_ids, cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_rowoff, hl.rowoff.data(), sizeof(unsigned) * hl.rowoff.size(), cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_slotbase, hl.slotbase.data(), sizeof(int) * hl.slotbase.size(), cudaMemcpyHostToDevice, s));
     A(cudaMemcpyAsync(d_demand_of, hl.demand_of.data(), sizeof(int) * ND, cudaMemcpyHostToDevice, s));
@@ -472,7 +475,7 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
     // algorithmic traffic of one iteration: the edge ids once, the rates read
     // and written, per demand its value and its multiplier read and written,
     // per block its metadata record and its lanes' hop counts
-    h->bytes_per_iter = (long long)(sizeof(uint16_t) * hl.ids.size()) + 2LL * (long long)sizeof(float) * (long long)ns +
+    h->bytes_per_iter = (long long)((size_t)id_bytes * n_ids) + 2LL * (long long)sizeof(float) * (long long)ns +
                         3LL * (long long)sizeof(float) * (long long)ND +
                         (long long)sizeof(te::BlockMeta) * (long long)nblocks +
                         (long long)sizeof(unsigned) * (long long)hl.hops.size();
@@ -777,6 +780,7 @@ extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint
         h->o.alpha_start != h->o.alpha_target)
         return h->fail(TE_EINVAL, "te_gradient needs the fixed schedule: adapt_beta = 0, continuation = 0, "
                                   "gamma < 0, alpha_start = alpha_target (finite)");
+    if (h->L.id_bytes != 2) return h->fail(TE_EUNSUPPORTED, "te_gradient takes at most 65,534 edges (16-bit ids)");
     te_status st = te_reset(h);
     if (st != TE_OK) return st;
     cudaStream_t s = h->stream;

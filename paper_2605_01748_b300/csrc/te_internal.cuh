@@ -141,10 +141,11 @@ constexpr int kStatusNumeric = 5;
 
 // Launchers (host side), defined in te_iter.cu / te_proj.cu / te_gap.cu.
 size_t iter_smem_bytes(int E, int grid, bool det);
-// The same for the wide-edge mode (staging buffers and the price slice only).
-size_t iter_smem_bytes_wide(int E, int grid);
+// The same for the wide-edge mode (staging buffers for ids of id_bytes
+// bytes, and the price slice).
+size_t iter_smem_bytes_wide(int E, int grid, int id_bytes);
 cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_per_sm);
-cudaError_t iter_occupancy_wide(int G, int E, int grid_hint, int* blocks_per_sm);
+cudaError_t iter_occupancy_wide(int G, int id_bytes, int E, int grid_hint, int* blocks_per_sm);
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st);
 // Several independent instances in one cooperative launch of the iteration
 // kernel (deterministic loads): instance i runs on CTAs i*group ..

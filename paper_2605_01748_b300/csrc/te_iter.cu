@@ -55,10 +55,15 @@ namespace {
 // incidence into L2) in its own slice of global memory; phase B sums the
 // CTAs' words exactly, so the loads, and the whole run, are bit-identical
 // to the shared-memory mode on the same instance.
-template <int G, bool DET, bool GROUPED, bool WIDE = false>
+// IdT: the layout's edge id type; 32-bit ids (above 65,534 edges) only in
+// the wide-edge mode, where the staging buffers take the room of the
+// per-edge arrays.
+template <int G, bool DET, bool GROUPED, bool WIDE = false, typename IdT = uint16_t>
 __global__ void __launch_bounds__(kIterThreads, 1)
     k_iter(IterArgs a_param, const IterArgs* __restrict__ group_args, int group) {
     static_assert(!WIDE || (DET && !GROUPED), "the wide-edge mode has deterministic loads and one instance");
+    static_assert(sizeof(IdT) == 2 || WIDE, "32-bit edge ids only in the wide-edge mode");
+    constexpr size_t kIdHalves = sizeof(IdT) / sizeof(uint16_t);  // staging size in 16-bit units per id
     extern __shared__ __align__(128) unsigned smem[];
     __shared__ IterArgs s_args;
     if (GROUPED) {
@@ -80,7 +85,7 @@ __global__ void __launch_bounds__(kIterThreads, 1)
     uint16_t* stage = WIDE ? reinterpret_cast<uint16_t*>(smem)
                            : reinterpret_cast<uint16_t*>(reinterpret_cast<uintptr_t>(w_s + (E + 1) + 31) &
                                                          ~uintptr_t(127));  // [warps][2][kIterStageRows*32]
-    float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kIterStageRows * kLanes);  // price slice
+    float* s_u = reinterpret_cast<float*>(stage + (size_t)kIterWarps * 2 * kIterStageRows * kLanes * kIdHalves);  // price slice
     const int e_lo = (int)((long long)cta * E / NG), e_hi = (int)((long long)(cta + 1) * E / NG);
     float* s_un = s_u + (e_hi - e_lo);                               // next prices of the slice
     __shared__ double s_wred[kIterWarps][4];  // per-warp FP64 partials of the residual sums
@@ -94,9 +99,9 @@ __global__ void __launch_bounds__(kIterThreads, 1)
     // that every CTA gets a sample of all kinds of blocks)
     const int b_hi = a.L.nblocks;  // block indices >= b_hi mean "none"
     const int nbc = cta < b_hi ? (b_hi - cta + NG - 1) / NG : 0;
-    const uint16_t* ids = static_cast<const uint16_t*>(a.L.ids);
+    const IdT* ids = static_cast<const IdT*>(a.L.ids);
     WarpStage ws;
-    ws.base = stage + (size_t)(warp * 2) * kIterStageRows * kLanes;
+    ws.base = stage + (size_t)(warp * 2) * kIterStageRows * kLanes * kIdHalves;
 
     for (int e = tid; e < E; e += kIterThreads) {
         w_s[e] = a.w[e];
@@ -155,7 +160,7 @@ __global__ void __launch_bounds__(kIterThreads, 1)
         LaneRes acc;
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.hops, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows, true, true, DET, WIDE>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws,
+            run_blocks<G, kIterStageRows, true, true, DET, WIDE, IdT>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws,
                                                 w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         {
@@ -479,27 +484,28 @@ cudaError_t launch_iter_t(const IterArgs& a, int grid, cudaStream_t st) {
                                        smem, st);
 }
 
-template <int G>
+template <int G, typename IdT>
 cudaError_t launch_iter_wide_t(const IterArgs& a, int grid, cudaStream_t st) {
-    const size_t smem = iter_smem_bytes_wide(a.L.E, grid);
-    cudaError_t err =
-        cudaFuncSetAttribute(k_iter<G, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = iter_smem_bytes_wide(a.L.E, grid, (int)sizeof(IdT));
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G, true, false, true, IdT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     IterArgs args = a;
     const IterArgs* none = nullptr;
     int group = 0;
     void* params[] = {&args, &none, &group};
-    return cudaLaunchCooperativeKernel((const void*)k_iter<G, true, false, true>, dim3(grid), dim3(kIterThreads),
-                                       params, smem, st);
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G, true, false, true, IdT>, dim3(grid),
+                                       dim3(kIterThreads), params, smem, st);
 }
 
-template <int G>
+template <int G, typename IdT>
 cudaError_t occupancy_wide_t(int E, int grid_hint, int* blocks) {
-    const size_t smem = iter_smem_bytes_wide(E, grid_hint);
-    cudaError_t err =
-        cudaFuncSetAttribute(k_iter<G, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = iter_smem_bytes_wide(E, grid_hint, (int)sizeof(IdT));
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G, true, false, true, IdT>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G, true, false, true>, kIterThreads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_iter<G, true, false, true, IdT>, kIterThreads,
+                                                         smem);
 }
 
 template <int G>
@@ -538,19 +544,27 @@ size_t iter_smem_bytes(int E, int grid, bool det) {
     return b;
 }
 
-size_t iter_smem_bytes_wide(int E, int grid) {
-    size_t b = (size_t)kIterWarps * 2 * kIterStageRows * kLanes * sizeof(uint16_t);
+size_t iter_smem_bytes_wide(int E, int grid, int id_bytes) {
+    size_t b = (size_t)kIterWarps * 2 * kIterStageRows * kLanes * (size_t)id_bytes;
     const int slice = (E + grid - 1) / (grid > 0 ? grid : 1) + 1;
     b += 2 * (size_t)slice * sizeof(float);
     return b;
 }
 
-cudaError_t iter_occupancy_wide(int G, int E, int grid_hint, int* blocks_per_sm) {
+cudaError_t iter_occupancy_wide(int G, int id_bytes, int E, int grid_hint, int* blocks_per_sm) {
+    if (id_bytes == 4) {
+        switch (G) {
+            case 1: return occupancy_wide_t<1, uint32_t>(E, grid_hint, blocks_per_sm);
+            case 2: return occupancy_wide_t<2, uint32_t>(E, grid_hint, blocks_per_sm);
+            case 4: return occupancy_wide_t<4, uint32_t>(E, grid_hint, blocks_per_sm);
+            default: return occupancy_wide_t<8, uint32_t>(E, grid_hint, blocks_per_sm);
+        }
+    }
     switch (G) {
-        case 1: return occupancy_wide_t<1>(E, grid_hint, blocks_per_sm);
-        case 2: return occupancy_wide_t<2>(E, grid_hint, blocks_per_sm);
-        case 4: return occupancy_wide_t<4>(E, grid_hint, blocks_per_sm);
-        default: return occupancy_wide_t<8>(E, grid_hint, blocks_per_sm);
+        case 1: return occupancy_wide_t<1, uint16_t>(E, grid_hint, blocks_per_sm);
+        case 2: return occupancy_wide_t<2, uint16_t>(E, grid_hint, blocks_per_sm);
+        case 4: return occupancy_wide_t<4, uint16_t>(E, grid_hint, blocks_per_sm);
+        default: return occupancy_wide_t<8, uint16_t>(E, grid_hint, blocks_per_sm);
     }
 }
 
@@ -572,14 +586,23 @@ cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_pe
 }
 
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
-    if (a.hist64) {
+    if (a.hist64 && a.L.id_bytes == 4) {
         switch (a.L.G) {
-            case 1: return launch_iter_wide_t<1>(a, grid, st);
-            case 2: return launch_iter_wide_t<2>(a, grid, st);
-            case 4: return launch_iter_wide_t<4>(a, grid, st);
-            default: return launch_iter_wide_t<8>(a, grid, st);
+            case 1: return launch_iter_wide_t<1, uint32_t>(a, grid, st);
+            case 2: return launch_iter_wide_t<2, uint32_t>(a, grid, st);
+            case 4: return launch_iter_wide_t<4, uint32_t>(a, grid, st);
+            default: return launch_iter_wide_t<8, uint32_t>(a, grid, st);
         }
     }
+    if (a.hist64) {
+        switch (a.L.G) {
+            case 1: return launch_iter_wide_t<1, uint16_t>(a, grid, st);
+            case 2: return launch_iter_wide_t<2, uint16_t>(a, grid, st);
+            case 4: return launch_iter_wide_t<4, uint16_t>(a, grid, st);
+            default: return launch_iter_wide_t<8, uint16_t>(a, grid, st);
+        }
+    }
+    if (a.L.id_bytes != 2) return cudaErrorInvalidValue;
     if (a.o.deterministic) {
         switch (a.L.G) {
             case 1: return launch_iter_t<1, true>(a, grid, st);

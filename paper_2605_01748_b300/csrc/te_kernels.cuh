@@ -257,6 +257,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// 32-bit load from a 32-bit shared-memory address
+__device__ __forceinline__ uint32_t lds_u32(unsigned addr) {
+    unsigned v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
 // 16-bit load from a 32-bit shared-memory address
 __device__ __forceinline__ uint16_t lds_u16(unsigned addr) {
     unsigned short v;
@@ -315,14 +321,17 @@ __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int l
 // GH (with DET): the histogram is one 64-bit word per edge in global memory,
 // h_hi read as unsigned long long*, and each rate adds the same fixed-point
 // value hi * 2^12 + lo (units of 2^-24) by one 64-bit atomic; h_lo unused.
-template <int G, bool STAGED, bool ACC, bool HOPS, bool DET, bool GH = false>
-__device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane, const uint16_t* bids, int s0,
+// IdT: the layout's edge id type (uint16_t, or uint32_t above 65,534 edges,
+// where the hop counts come with the block: HOPS).
+template <int G, bool STAGED, bool ACC, bool HOPS, bool DET, bool GH = false, typename IdT = uint16_t>
+__device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane, const IdT* bids, int s0,
                                               unsigned counts, int KB, const BlockIn& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
                                               unsigned* h_lo, float inv_beta, float logbeta,
                                               float beta_f, float alpha, float inv_alpha, LaneRes& acc) {
     constexpr int KL = kMaxPathsPerLane;
-    const uint16_t sentinel = a.sentinel;
+    static_assert(sizeof(IdT) == 2 || (sizeof(IdT) == 4 && HOPS), "32-bit ids come with stored hop counts");
+    const IdT sentinel = (IdT)a.sentinel;
     const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const size_t di = (size_t)b * a.dpb + lane / G;
     const float D = in.D;
@@ -332,9 +341,13 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
     for (int j = 0; j < KL; ++j) xo[j] = in.x[j];
     // staged ids: 32-bit shared address of this lane's entry in the block's
     // first row (an explicit shared load per row, no generic addressing)
-    const unsigned sb = STAGED ? smem_u32(bids) + 2u * (unsigned)lane : 0u;
-    auto id_at = [&](unsigned row) -> uint16_t {
-        if (STAGED) return lds_u16(sb + row * (unsigned)(kLanes * sizeof(uint16_t)));
+    const unsigned sb = STAGED ? smem_u32(bids) + (unsigned)sizeof(IdT) * (unsigned)lane : 0u;
+    auto id_at = [&](unsigned row) -> IdT {
+        if (STAGED) {
+            const unsigned at = sb + row * (unsigned)(kLanes * sizeof(IdT));
+            if (sizeof(IdT) == 2) return (IdT)lds_u16(at);
+            return (IdT)lds_u32(at);
+        }
         return __ldg(&bids[(size_t)row * kLanes + lane]);
     };
     unsigned rs = 0;                      // first row of slot j within the block
@@ -349,7 +362,7 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
             int n = HOPS ? (int)((nbits >> (8 * j)) & 0xffu) : 0;
             #pragma unroll 4
             for (unsigned r = 0; r < cnt; ++r) {
-                const uint16_t id = id_at(rs + r);
+                const IdT id = id_at(rs + r);
                 q += w_s[id];
                 if (!HOPS) n += (id != sentinel);
             }
@@ -407,7 +420,7 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
                 } else {
                     #pragma unroll 8
                     for (unsigned r = 0; r < cnt; ++r) {
-                        const uint16_t id = id_at(rs + r);
+                        const IdT id = id_at(rs + r);
                         atomicAdd(&h_hi[id], hi);
                         atomicAdd(&h_lo[id], lo);
                     }
@@ -452,9 +465,9 @@ __device__ __forceinline__ unsigned rows_of(unsigned counts) {
 struct WarpStage {
     uint16_t* base;
 };
-template <int ROWS>
-__device__ __forceinline__ uint16_t* stage_buf(const WarpStage& ws, int k) {
-    return ws.base + (k ? ROWS * kLanes : 0);
+template <int ROWS, typename IdT = uint16_t>
+__device__ __forceinline__ IdT* stage_buf(const WarpStage& ws, int k) {
+    return reinterpret_cast<IdT*>(ws.base) + (k ? ROWS * kLanes : 0);
 }
 
 // Phase A of one iteration for one warp: takes blocks start + v * stride
@@ -475,10 +488,11 @@ __device__ __forceinline__ uint16_t* stage_buf(const WarpStage& ws, int k) {
 //
 // ACC (see process_block): the residual terms of the warp's blocks are summed
 // per lane into acc (compensated), in the fixed order of the interleave.  HOPS
-// and DET: see process_block.  GH: see process_block.
-template <int G, int ROWS, bool ACC, bool HOPS, bool DET, bool GH = false>
+// and DET: see process_block.  GH, IdT: see process_block (with 32-bit ids a
+// warp's two staging buffers take twice the bytes: ws.base must have room).
+template <int G, int ROWS, bool ACC, bool HOPS, bool DET, bool GH = false, typename IdT = uint16_t>
 __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __restrict__ blkmeta,
-                           const uint16_t* __restrict__ ids, const float* __restrict__ xin,
+                           const IdT* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
                            unsigned* h_hi, unsigned* h_lo, float inv_beta, float logbeta, float beta_f,
                            float alpha, float inv_alpha, LaneRes& acc) {
@@ -506,13 +520,13 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
         const unsigned rows = rows_of(counts);
         if (rows > (unsigned)ROWS || rows == 0) return false;
         __syncwarp();
-        const unsigned bytes = rows * kLanes * (unsigned)sizeof(uint16_t);  // a multiple of 64
+        const unsigned bytes = rows * kLanes * (unsigned)sizeof(IdT);  // a multiple of 64
         const char* src = reinterpret_cast<const char*>(ids + (size_t)row0 * kLanes);
-        const unsigned dst = smem_u32(stage_buf<ROWS>(ws, k));
+        const unsigned dst = smem_u32(stage_buf<ROWS, IdT>(ws, k));
         // at most ROWS rows of 64 B: a fixed number of predicated copies per
         // lane (no loop branch)
-        constexpr int kCopies = ROWS * kLanes * (int)sizeof(uint16_t) / (16 * kLanes);
-        static_assert(ROWS * (int)sizeof(uint16_t) % 16 == 0, "a staging buffer is whole 16-byte copies per lane");
+        constexpr int kCopies = ROWS * kLanes * (int)sizeof(IdT) / (16 * kLanes);
+        static_assert(ROWS * (int)sizeof(IdT) % 16 == 0, "a staging buffer is whole 16-byte copies per lane");
         #pragma unroll
         for (int i = 0; i < kCopies; ++i) {
             const unsigned off = 16u * ((unsigned)lane + (unsigned)i * kLanes);
@@ -549,11 +563,11 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
             // lane; the __syncwarp makes each lane's copies visible to all
             cp_async_wait_prev();
             __syncwarp();
-            process_block<G, true, ACC, HOPS, DET, GH>(bc, b0, lane, stage_buf<ROWS>(ws, cur), s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
+            process_block<G, true, ACC, HOPS, DET, GH, IdT>(bc, b0, lane, stage_buf<ROWS, IdT>(ws, cur), s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                         inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         } else {
             const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
-            process_block<G, false, ACC, HOPS, DET, GH>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
+            process_block<G, false, ACC, HOPS, DET, GH, IdT>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
                                          w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         b0 = b1;

@@ -25,7 +25,7 @@ std::string fmt(const char* f, long long a, long long b = 0) {
 }  // namespace
 
 te_status build_host_layout(const te_topology* topo, const te_paths* P, const double* D, const double* C,
-                            double scale, int g_min, HostLayout& out) {
+                            double scale, int g_min, HostLayout& out, int max_id_bytes) {
     const int E = topo->n_edges;
     const int K = P->n_demands;
     (void)C;
@@ -101,11 +101,14 @@ te_status build_host_layout(const te_topology* topo, const te_paths* P, const do
         max_block_rows = std::max<int>(max_block_rows, (int)(rowoff[slotbase[b + 1]] - rowoff[slotbase[b]]));
     }
     const long long nrows = rowoff[nslots];
-    if (E + 1 > 65535) {
-        out.err = fmt("n_edges = %lld: the iteration kernel takes 16-bit edge ids (at most 65534 edges)", E); return TE_EUNSUPPORTED;
+    const bool ids32 = E + 1 > 65535;
+    if (ids32 && max_id_bytes < 4) {
+        out.err = fmt("n_edges = %lld: this kernel takes 16-bit edge ids (at most 65534 edges)", E); return TE_EUNSUPPORTED;
     }
+    out.id_bytes = ids32 ? 4 : 2;
     const size_t ND = (size_t)nblocks * DPB;  // demand slots
-    out.ids.assign((size_t)nrows * kLanes, (uint16_t)E);
+    if (ids32) out.ids32.assign((size_t)nrows * kLanes, (uint32_t)E);
+    else out.ids.assign((size_t)nrows * kLanes, (uint16_t)E);
     std::vector<long long> slot_path((size_t)nslots * kLanes, -1);
     std::vector<unsigned> hops((size_t)nblocks * kLanes, 0u);
     std::vector<int> demand_of(ND, -1);
@@ -130,13 +133,14 @@ te_status build_host_layout(const te_topology* topo, const te_paths* P, const do
                 hops[(size_t)b * kLanes + lane] |= (unsigned)n << (8 * (p / G));
                 for (long long k = 0; k < n; ++k) {
                     const size_t at = ((size_t)rowoff[s] + (size_t)k) * kLanes + lane;
-                    out.ids[at] = (uint16_t)P->path_edges[i0 + k];
+                    if (ids32) out.ids32[at] = (uint32_t)P->path_edges[i0 + k];
+                    else out.ids[at] = (uint16_t)P->path_edges[i0 + k];
                 }
             }
         }
     }
     // hop order within each slot: spread every row's ids over the shared-memory banks
-    {
+    if (!ids32) {
         uint16_t* q = out.ids.data();
         const unsigned hw = std::thread::hardware_concurrency();
         const long long nt = std::max<long long>(1, std::min<long long>({hw ? (long long)hw : 1LL, 64LL, nslots}));

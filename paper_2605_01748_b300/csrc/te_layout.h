@@ -18,7 +18,9 @@ struct HostLayout {
     long long P = 0, nnz = 0;
     int G = 1, dpb = 32, kl = 0, kmax = 0, nblocks = 0, max_block_rows = 0;
     long long nslots = 0, nrows = 0;
-    std::vector<uint16_t> ids;           // [nrows*32]
+    int id_bytes = 2;                    // 2: ids below, 4: ids32 (more than 65,534 edges)
+    std::vector<uint16_t> ids;           // [nrows*32] (id_bytes 2)
+    std::vector<uint32_t> ids32;         // [nrows*32] (id_bytes 4)
     std::vector<unsigned> rowoff;        // [nslots+1]
     std::vector<int> slotbase;           // [nblocks+1]
     std::vector<BlockMeta> blkmeta;      // [nblocks]
@@ -36,8 +38,11 @@ struct HostLayout {
 // sorted by their path lengths into blocks of 32/G demands (G >= g_min lanes
 // per demand, at most kMaxPathsPerLane paths per lane), each path's hops
 // ordered within its slot to spread every row over the shared-memory banks,
-// values normalised by scale.  Returns TE_OK, or TE_EUNSUPPORTED with err set.
+// values normalised by scale.  Edge ids are 16-bit, or 32-bit (hops in path
+// order, no bank order: only the wide-edge mode reads them, from global
+// memory) when there are more than 65,534 edges and max_id_bytes is 4.
+// Returns TE_OK, or TE_EUNSUPPORTED with err set.
 te_status build_host_layout(const te_topology* topo, const te_paths* P, const double* D, const double* C,
-                            double scale, int g_min, HostLayout& out);
+                            double scale, int g_min, HostLayout& out, int max_id_bytes = 2);
 
 }  // namespace te

@@ -69,13 +69,17 @@ int main(int argc, char** argv) {
     P.path_edge_off = peo.data();
     P.path_edges = pe.data();
     te::HostLayout L;
-    const te_status st = te::build_host_layout(&topo, &P, dem.data(), cap.data(), 1.0, 1, L);
+    // 32-bit ids allowed (taken only above 65,534 edges)
+    const te_status st = te::build_host_layout(&topo, &P, dem.data(), cap.data(), 1.0, 1, L, 4);
     CHECK(st == TE_OK, "build_host_layout returned %d: %s", (int)st, L.err.c_str());
 
     const int G = L.G, DPB = L.dpb;
     CHECK(G * DPB == te::kLanes, "G %d x demands per block %d != 32", G, DPB);
     CHECK((long long)L.rowoff.size() == L.nslots + 1 && L.rowoff[0] == 0, "row offsets");
-    CHECK((long long)L.ids.size() == L.nrows * te::kLanes, "id array size");
+    const bool ids32 = L.id_bytes == 4;
+    CHECK(ids32 == (E > 65534) && (L.id_bytes == 2 || ids32), "id width %d for %d edges", L.id_bytes, E);
+    CHECK((long long)(ids32 ? L.ids32.size() : L.ids.size()) == L.nrows * te::kLanes, "id array size");
+    auto id_of = [&](size_t at) -> long long { return ids32 ? (long long)L.ids32[at] : (long long)L.ids[at]; };
     CHECK((int)L.hops.size() == L.nblocks * te::kLanes, "hop-count array size");
     std::vector<int> seen(K, 0);
     long long pad = 0, paths_seen = 0;
@@ -113,7 +117,7 @@ int main(int argc, char** argv) {
                 const long long r = L.slot_path[s * te::kLanes + lane];
                 std::vector<int> got;
                 for (unsigned row = L.rowoff[s]; row < L.rowoff[s + 1]; ++row) {
-                    const int id = L.ids[(size_t)row * te::kLanes + lane];
+                    const int id = (int)id_of((size_t)row * te::kLanes + lane);
                     if (id == E) {
                         ++pad;
                         continue;

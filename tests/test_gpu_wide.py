@@ -59,6 +59,92 @@ def wide_30k():
     return _scaled(sub, "wide-30k-sub")
 
 
+def _torus(n, n_local, n_far, seed=0):
+    """n x n torus of links (node (i, j) = i*n + j; link i*n + j to the right
+    neighbour, n*n + i*n + j to the one below; edge 2l runs right or down,
+    2l + 1 back), E = 4 n^2 directed edges.  Demands between n_local pairs
+    at most 4 rows and columns apart and n_far random pairs, each with two
+    paths (along the row, then the column, and the other way round; one path
+    when the pair shares a row or column), every move the shorter way round.
+    Capacities on {100, 200, 400}, lognormal demands scaled so that the paths
+    carry twice the capacity of the edges they use."""
+    from paper_2605_01748_b300.instances import Instance
+    rng = np.random.default_rng(seed)
+    N, NL = n * n, 2 * n * n
+    a = np.arange(N)
+    right = (a // n) * n + (a % n + 1) % n
+    down = ((a // n + 1) % n) * n + a % n
+    lsrc = np.concatenate([a, a]).astype(np.int32)
+    ldst = np.concatenate([right, down]).astype(np.int32)
+    esrc = np.empty(2 * NL, np.int32)
+    edst = np.empty(2 * NL, np.int32)
+    esrc[0::2], edst[0::2] = lsrc, ldst
+    esrc[1::2], edst[1::2] = ldst, lsrc
+    cap = np.repeat(rng.choice([100.0, 200.0, 400.0], NL), 2)
+
+    def steps(i, j, d, axis):
+        # edge ids of |d| moves from (i, j) along the axis (0: along the row)
+        out = []
+        for _ in range(abs(d)):
+            if axis == 0:
+                if d > 0:
+                    out.append(2 * (i * n + j)); j = (j + 1) % n
+                else:
+                    j = (j - 1) % n; out.append(2 * (i * n + j) + 1)
+            else:
+                if d > 0:
+                    out.append(2 * (N + i * n + j)); i = (i + 1) % n
+                else:
+                    i = (i - 1) % n; out.append(2 * (N + i * n + j) + 1)
+        return out, i, j
+
+    def short(d):
+        d %= n
+        return d if d <= n // 2 else d - n
+
+    pairs = set()
+    while len(pairs) < n_local:
+        s = int(rng.integers(N))
+        di, dj = rng.integers(-4, 5, 2)
+        if di or dj:
+            pairs.add((s, ((s // n + di) % n) * n + (s % n + dj) % n))
+    while len(pairs) < n_local + n_far:
+        s, t = (int(v) for v in rng.integers(N, size=2))
+        if s != t:
+            pairs.add((s, t))
+    dsrc, ddst, dpo, peo, pe = [], [], [0], [0], []
+    for s, t in sorted(pairs):
+        si, sj, ti, tj = s // n, s % n, t // n, t % n
+        dI, dJ = short(ti - si), short(tj - sj)
+        h1, i1, j1 = steps(si, sj, dJ, 0)
+        v1, _, _ = steps(i1, j1, dI, 1)
+        paths = [h1 + v1]
+        if dI and dJ:
+            v2, i2, j2 = steps(si, sj, dI, 1)
+            h2, _, _ = steps(i2, j2, dJ, 0)
+            paths.append(v2 + h2)
+        for p in paths:
+            pe.extend(p)
+            peo.append(len(pe))
+        dsrc.append(s)
+        ddst.append(t)
+        dpo.append(len(peo) - 1)
+    pe = np.asarray(pe, np.int32)
+    dpo, peo = np.asarray(dpo, np.int64), np.asarray(peo, np.int64)
+    D = rng.lognormal(0.0, 1.0, len(dsrc))
+    hops = np.add.reduceat(np.diff(peo), dpo[:-1]) / np.diff(dpo)
+    used = np.unique(pe)
+    D *= 2.0 * cap[used].sum() / float((D * hops).sum())
+    return Instance(f"torus-{n}", N, esrc, edst, cap, np.asarray(dsrc, np.int32), np.asarray(ddst, np.int32),
+                    D, dpo, peo, pe, {"family": "torus", "n": n})
+
+
+@pytest.fixture(scope="module")
+def torus_67k():
+    # 130 x 130 torus: 67,600 directed edges, beyond 16-bit ids
+    return _torus(130, 18000, 2000)
+
+
 def _same_run(te, inst, iters, **kw):
     a = te.TE(inst, **kw)
     b = te.TE(inst, edge_mode=te.EDGES_GLOBAL, **kw)
@@ -128,10 +214,61 @@ def test_wide_instance_parity_and_feasibility(te, wide_30k):
 
 def test_global_mode_needs_deterministic_loads(te, tiny, wide_30k):
     # FP32 histograms (4 B per edge instead of 8) fit shared memory up to
-    # about 15,600 edges; 30,222 do not, and the global mode has no FP32 form
+    # about 16,100 edges; 30,222 do not, and the global mode has no FP32 form
     with pytest.raises(te.TEError) as ei:
         te.TE(wide_30k, deterministic=0)
     assert ei.value.status == te.TE_EUNSUPPORTED
     with pytest.raises(te.TEError) as ei:
         te.TE(tiny, deterministic=0, edge_mode=te.EDGES_GLOBAL)
+    assert ei.value.status == te.TE_EUNSUPPORTED
+
+
+def test_32bit_ids_layout_and_walks(te, torus_67k):
+    # the generator's paths are walks of the topology (te_create checks them)
+    assert torus_67k.n_edges == 67600
+    t = te.TE(torus_67k)
+    info = t.layout()
+    assert info["id_bytes"] == 4
+    t.close()
+
+
+@pytest.mark.parametrize("alpha", [0.0, 1.0, 2.0])
+def test_32bit_ids_fixed_schedule_parity(te, torus_67k, alpha):
+    kw = dict(alpha_target=alpha, alpha_start=alpha, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t = te.TE(torus_67k, **kw)
+    t.solve(40)
+    s = O.OracleSolver(torus_67k, **kw)
+    s.run(40)
+    x, xr = t.allocation(project=te.PROJECT_NONE), s.allocation()
+    assert _rel_inf(x, xr) <= TOL
+    Sg, Sr = O.demand_totals(torus_67k, x), O.demand_totals(torus_67k, xr)
+    assert (np.abs(Sg - Sr) / np.maximum(Sr, 1e-2 * Sr.max())).max() <= TOL
+    assert _rel_inf(t.prices(), s.prices()) <= TOL
+    t.close()
+
+
+def test_32bit_ids_feasibility_gap_and_refusals(te, torus_67k):
+    t = te.TE(torus_67k, alpha_target=1.0, alpha_start=1.0, continuation=0)
+    t.solve(3000)
+    x = t.allocation(project=te.PROJECT_NONE).astype(np.float64)
+    for proj in (te.PROJECT_ALG2, te.PROJECT_SCALE):
+        xp = t.allocation(project=proj).astype(np.float64)
+        loads = O.edge_loads(torus_67k, xp)
+        assert (xp >= 0).all() and (loads <= torus_67k.capacity * (1 + 1e-5)).all()
+        assert (O.demand_totals(torus_67k, xp) <= torus_67k.demand * (1 + 1e-5)).all()
+    xs = O.project_scale(torus_67k, x)
+    assert _rel_inf(t.allocation(project=te.PROJECT_SCALE), xs) <= 1e-5
+    g, pr, du = t.gap(project=te.PROJECT_SCALE)
+    xsg = t.allocation(project=te.PROJECT_SCALE).astype(np.float64)
+    go, pro, duo = O.gap(torus_67k, xsg, t.prices(), 1.0)
+    assert abs(du - duo) <= 1e-7 * abs(duo)
+    assert abs(pr - pro) <= 2.0 ** -21 * torus_67k.n_demands
+    t.close()
+    t = te.TE(torus_67k, alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    with pytest.raises(te.TEError) as ei:
+        t.gradient(10)
+    assert ei.value.status == te.TE_EUNSUPPORTED
+    t.close()
+    with pytest.raises(te.TEError) as ei:
+        te.TE(torus_67k, deterministic=0)
     assert ei.value.status == te.TE_EUNSUPPORTED

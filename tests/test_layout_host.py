@@ -68,3 +68,10 @@ def test_layout_of_the_200_node_instance(checker, tmp_path):
 @pytest.mark.parametrize("seed,max_paths,max_hops", [(1, 4, 12), (2, 16, 9), (3, 32, 40), (4, 7, 255)])
 def test_layout_of_ragged_instances(checker, tmp_path, seed, max_paths, max_hops):
     _run(checker, _ragged(seed, 300, max_paths, max_hops), tmp_path)
+
+
+@pytest.mark.parametrize("n_edges", [65534, 65535, 200000])
+def test_layout_id_width_at_the_16_bit_limit(checker, tmp_path, n_edges):
+    # 16-bit ids up to 65,534 edges (the sentinel E must fit), 32-bit above;
+    # the checker asserts the width and reads every id back
+    _run(checker, _ragged(5, 400, 8, 30, n_edges=n_edges), tmp_path)

@@ -99,8 +99,8 @@ def parse():
                     help="time the two feasibility steps (Algorithm 2 and proportional scaling, device output) "
                          "on the iterate after K iterations of the default solver, one JSON line")
     ap.add_argument("--edge-mode", choices=["auto", "global"], default="auto",
-                    help="--steady: per-edge arrays of the iteration kernel in shared memory when they fit "
-                         "(auto) or always in global memory")
+                    help="the timed handle's (and --steady's) per-edge arrays of the iteration kernel: in "
+                         "shared memory when they fit (auto) or always in global memory")
     ap.add_argument("--alpha-fair", default="", metavar="ALPHAS",
                     help="time to a duality-gap certificate of --cert-eps at each fixed alpha (e.g. 1,2)")
     ap.add_argument("--cert-eps", type=float, default=1e-3)
@@ -338,7 +338,8 @@ def run_ours(a, ws, rank, local, dist):
 
     inst = instances.make(a.workload, threads=os.cpu_count() or 0)
     stream = torch.cuda.current_stream(dev)
-    t = te.TE(inst, cuda_stream=stream.cuda_stream)
+    edge_mode = te.EDGES_GLOBAL if a.edge_mode == "global" else te.EDGES_AUTO
+    t = te.TE(inst, cuda_stream=stream.cuda_stream, edge_mode=edge_mode)
     lay = t.layout()
     xdev = torch.empty(inst.n_paths, dtype=torch.float32, device=dev)
     opt = Optimality(inst, dev)
@@ -473,6 +474,8 @@ def run_ours(a, ws, rank, local, dist):
     achieved = alg_bytes * K / (solve_mean * 1e-3) / 1e9
     moved = lay["bytes_per_iter"] * K / (solve_mean * 1e-3) / 1e9
     traffic_iter, traffic_src = ncu_traffic(a.workload)
+    if a.edge_mode == "global":
+        traffic_iter, traffic_src = None, "the capture is of the shared-memory edge arrays"
     l2_resident = lay["bytes_per_iter"] < 126e6
     out = {
         "metric": METRIC,
@@ -508,6 +511,7 @@ def run_ours(a, ws, rank, local, dist):
                   "no flush: every iteration streams the sliced incidence (> 126 MB L2)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
             "step": "te_reset + te_solve(K) (one persistent launch) + te_allocation(PROJECT_SCALE, device out)",
+            "edge_arrays": "global memory (edge_mode)" if a.edge_mode == "global" else "shared memory",
         },
         "iters_per_s": round(K / (solve_mean * 1e-3), 1),
         "solve_ms": round(solve_mean, 4),

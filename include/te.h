@@ -138,8 +138,8 @@ typedef struct {
                              10,770 edges), else global memory (L2);
                              TE_EDGES_GLOBAL (1) global memory always.  Both
                              give the same bits; the global mode takes one
-                             64-bit L2 atomic per path-edge incidence instead
-                             of two shared-memory ones and needs
+                             64-bit L2 reduction per path-edge incidence
+                             instead of two shared-memory atomics and needs
                              deterministic = 1 (else TE_EUNSUPPORTED); above
                              65,534 edges (32-bit ids) it is the only mode   */
     void* cuda_stream;    /* cudaStream_t to run on; NULL = default stream     */

@@ -51,7 +51,7 @@ namespace {
 // WIDE (with DET, not GROUPED): the wide-edge mode for instances whose
 // per-edge arrays do not fit shared memory.  Each CTA keeps its gather
 // weights (a.wpriv) and its load histogram (a.hist64: one 64-bit
-// fixed-point word per edge, units of 2^-24, one 64-bit atomic per
+// fixed-point word per edge, units of 2^-24, one 64-bit reduction per
 // incidence into L2) in its own slice of global memory; phase B sums the
 // CTAs' words exactly, so the loads, and the whole run, are bit-identical
 // to the shared-memory mode on the same instance.

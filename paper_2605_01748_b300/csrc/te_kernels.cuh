@@ -257,6 +257,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// 64-bit integer add into global memory with no value returned (a reduction
+// the L2 performs; the caller does not wait for it)
+__device__ __forceinline__ void red_add_global_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "l"(v) : "memory");
+}
 // 32-bit load from a 32-bit shared-memory address
 __device__ __forceinline__ uint32_t lds_u32(unsigned addr) {
     unsigned v;
@@ -320,7 +325,8 @@ __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int l
 // (the sum then depends on the order of the atomics in its last bits).
 // GH (with DET): the histogram is one 64-bit word per edge in global memory,
 // h_hi read as unsigned long long*, and each rate adds the same fixed-point
-// value hi * 2^12 + lo (units of 2^-24) by one 64-bit atomic; h_lo unused.
+// value hi * 2^12 + lo (units of 2^-24) by one 64-bit L2 reduction (red:
+// no value returned, so the warp does not wait for it); h_lo unused.
 // IdT: the layout's edge id type (uint16_t, or uint32_t above 65,534 edges,
 // where the hop counts come with the block: HOPS).
 template <int G, bool STAGED, bool ACC, bool HOPS, bool DET, bool GH = false, typename IdT = uint16_t>
@@ -416,7 +422,7 @@ __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane
                     unsigned long long* h64 = reinterpret_cast<unsigned long long*>(h_hi);
                     const unsigned long long v = ((unsigned long long)hi << 12) + lo;
                     #pragma unroll 8
-                    for (unsigned r = 0; r < cnt; ++r) atomicAdd(&h64[id_at(rs + r)], v);
+                    for (unsigned r = 0; r < cnt; ++r) red_add_global_u64(&h64[id_at(rs + r)], v);
                 } else {
                     #pragma unroll 8
                     for (unsigned r = 0; r < cnt; ++r) {

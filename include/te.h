@@ -318,8 +318,7 @@ te_status te_layout(const te_handle* h, te_layout_info* info);
  * time.  Uses device memory of about
  * (K/checkpoint_every + checkpoint_every + 2) times the iterate (released
  * before returning).  The handle's state afterwards is that of an
- * intermediate iteration: call te_reset before solving again.  Instances of
- * more than 65,534 edges return TE_EUNSUPPORTED. */
+ * intermediate iteration: call te_reset before solving again. */
 te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint_every, double* J_out, double* dJ_dC,
                       double* dJ_dD, int32_t out_is_device);
 

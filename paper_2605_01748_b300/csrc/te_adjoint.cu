@@ -63,6 +63,7 @@ __global__ void k_adj_edges_in(int E, double* ub, double* db, const float* u1, c
 // as the adjoint of x' and overwritten with the adjoint of x; qb receives
 // each path's term of the adjoint of w (-mb/n, 0 off the active set) and
 // qmax the largest |qb| (zeroed by the caller).
+template <typename IdT>
 __global__ void k_adj_demands(Layout L, const float* __restrict__ x1, const float* __restrict__ lam1,
                               const double* __restrict__ Lb, double* xb, double* qb, unsigned long long* qmax,
                               double* Db, float beta, float alpha) {
@@ -72,7 +73,7 @@ __global__ void k_adj_demands(Layout L, const float* __restrict__ x1, const floa
     if (np == 0) return;
     const int b = (int)(i / L.dpb), t = (int)(i % L.dpb);
     const int s0 = L.slotbase[b];
-    const uint16_t* ids = static_cast<const uint16_t*>(L.ids);
+    const IdT* ids = static_cast<const IdT*>(L.ids);
     // pass 1: active set sums
     double S = 0.0, H = 0.0, G = 0.0;
     int na = 0;
@@ -158,6 +159,7 @@ __device__ __forceinline__ double adj_scale(unsigned long long qmax_bits, int de
 
 // the adjoint of w per edge: one thread per path lane adds its paths' terms
 // as fixed-point integers
+template <typename IdT>
 __global__ void k_adj_scatter(Layout L, const double* __restrict__ qb, const unsigned long long* qmax, int deg_bits,
                               unsigned long long* wfix) {
     const double scale = adj_scale(*qmax, deg_bits);
@@ -166,7 +168,7 @@ __global__ void k_adj_scatter(Layout L, const double* __restrict__ qb, const uns
     if (i >= (long long)L.nblocks * kLanes) return;
     const int b = (int)(i / kLanes), lane = (int)(i % kLanes);
     const int s0 = L.slotbase[b], KB = L.slotbase[b + 1] - s0;
-    const uint16_t* ids = static_cast<const uint16_t*>(L.ids);
+    const IdT* ids = static_cast<const IdT*>(L.ids);
     for (int j = 0; j < KB; ++j) {
         const size_t sl = (size_t)(s0 + j);
         const double v = qb[sl * kLanes + lane];
@@ -257,9 +259,14 @@ cudaError_t adjoint_step(const Layout& L, const float* xk, const float* x1, cons
     (void)wk;
     cudaError_t err = cudaMemsetAsync(B.qmax, 0, sizeof(unsigned long long), st);
     if (err != cudaSuccess) return err;
-    k_adj_demands<<<grid_for((long long)L.nblocks * L.dpb), kThreads, 0, st>>>(L, x1, lam1, B.Lb, B.xb, B.qb, B.qmax,
-                                                                             B.Db, beta, alpha);
-    k_adj_scatter<<<grid_for((long long)L.nblocks * kLanes), kThreads, 0, st>>>(L, B.qb, B.qmax, B.deg_bits, B.wfix);
+    const unsigned gd = grid_for((long long)L.nblocks * L.dpb), gs = grid_for((long long)L.nblocks * kLanes);
+    if (L.id_bytes == 4) {  // more than 65,534 edges
+        k_adj_demands<uint32_t><<<gd, kThreads, 0, st>>>(L, x1, lam1, B.Lb, B.xb, B.qb, B.qmax, B.Db, beta, alpha);
+        k_adj_scatter<uint32_t><<<gs, kThreads, 0, st>>>(L, B.qb, B.qmax, B.deg_bits, B.wfix);
+    } else {
+        k_adj_demands<uint16_t><<<gd, kThreads, 0, st>>>(L, x1, lam1, B.Lb, B.xb, B.qb, B.qmax, B.Db, beta, alpha);
+        k_adj_scatter<uint16_t><<<gs, kThreads, 0, st>>>(L, B.qb, B.qmax, B.deg_bits, B.wfix);
+    }
     k_adj_edges_out<<<grid_for(L.E), kThreads, 0, st>>>(L.E, B.ub, B.db, B.wfix, B.qmax, B.deg_bits);
     return cudaGetLastError();
 }

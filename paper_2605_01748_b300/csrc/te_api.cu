@@ -780,7 +780,6 @@ extern "C" te_status te_gradient(te_handle* h, int64_t iters, int32_t checkpoint
         h->o.alpha_start != h->o.alpha_target)
         return h->fail(TE_EINVAL, "te_gradient needs the fixed schedule: adapt_beta = 0, continuation = 0, "
                                   "gamma < 0, alpha_start = alpha_target (finite)");
-    if (h->L.id_bytes != 2) return h->fail(TE_EUNSUPPORTED, "te_gradient takes at most 65,534 edges (16-bit ids)");
     te_status st = te_reset(h);
     if (st != TE_OK) return st;
     cudaStream_t s = h->stream;

@@ -247,7 +247,7 @@ def test_32bit_ids_fixed_schedule_parity(te, torus_67k, alpha):
     t.close()
 
 
-def test_32bit_ids_feasibility_gap_and_refusals(te, torus_67k):
+def test_32bit_ids_feasibility_gap_and_refusal(te, torus_67k):
     t = te.TE(torus_67k, alpha_target=1.0, alpha_start=1.0, continuation=0)
     t.solve(3000)
     x = t.allocation(project=te.PROJECT_NONE).astype(np.float64)
@@ -264,11 +264,58 @@ def test_32bit_ids_feasibility_gap_and_refusals(te, torus_67k):
     assert abs(du - duo) <= 1e-7 * abs(duo)
     assert abs(pr - pro) <= 2.0 ** -21 * torus_67k.n_demands
     t.close()
-    t = te.TE(torus_67k, alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
-    with pytest.raises(te.TEError) as ei:
-        t.gradient(10)
-    assert ei.value.status == te.TE_EUNSUPPORTED
-    t.close()
     with pytest.raises(te.TEError) as ei:
         te.TE(torus_67k, deterministic=0)
     assert ei.value.status == te.TE_EUNSUPPORTED
+
+
+def test_32bit_ids_gradient_matches_oracle(te, torus_67k):
+    # the differentiated form (fixed schedule, caller units) through 40
+    # iterations with checkpoints every 7, against the oracle's reverse pass
+    inst = torus_67k
+    K, b0 = 40, inst.n_paths ** 2 / (inst.nnz * inst.demand.sum())
+    t = te.TE(inst, alpha_target=1.0, alpha_start=1.0, beta0=b0, adapt_beta=0, continuation=0, gamma=-1.0,
+              scale_mode=2)
+    J, gC, gD = t.gradient(K, 7)
+    Jo, gCo, gDo = O.gradient(inst, 1.0, b0, K)
+    assert abs(J - Jo) <= 1e-5 * abs(Jo)
+    g, go = np.concatenate([gC, gD]), np.concatenate([gCo, gDo])
+    assert np.max(np.abs(g - go)) <= 1e-3 * np.max(np.abs(go))
+    t.close()
+
+
+def test_wide_mode_streaming_and_warm_start(te, wide_11k):
+    # capacity change then reset equals a fresh handle on the changed
+    # instance, bit for bit, in the global mode; a warm start after a demand
+    # change keeps the run identical to the shared-memory mode's
+    rng = np.random.default_rng(7)
+    C2 = wide_11k.capacity * rng.uniform(0.5, 1.5, wide_11k.n_edges)
+    a = te.TE(wide_11k)
+    a.solve(100)
+    a.set_capacities(C2)
+    a.reset()
+    ra = a.solve(200)
+    b = te.TE(dataclasses.replace(wide_11k, capacity=C2))
+    rb = b.solve(200)
+    assert ra == rb
+    assert np.array_equal(a.allocation(project=te.PROJECT_NONE), b.allocation(project=te.PROJECT_NONE))
+    D2 = wide_11k.demand * rng.uniform(0.8, 1.2, wide_11k.n_demands)
+    b.set_demands(D2)
+    rb2 = b.solve(200)
+    a.close()
+    b.close()
+    # the same sequence on an instance small enough for both modes
+    from paper_2605_01748_b300 import instances
+    m = instances.make_medium()
+    D3 = m.demand * np.random.default_rng(8).uniform(0.8, 1.2, m.n_demands)
+    runs = []
+    for mode in (te.EDGES_AUTO, te.EDGES_GLOBAL):
+        t = te.TE(m, edge_mode=mode)
+        t.solve(300)
+        t.set_demands(D3)
+        r = t.solve(300)
+        runs.append((r, t.allocation(project=te.PROJECT_NONE), t.prices()))
+        t.close()
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
+    assert rb2["iters"] > 0

@@ -1007,7 +1007,8 @@ def run_alpha_fair(a):
     line = {"mode": "alpha-fair", "workload": workload_desc(inst),
             "metric": f"ms to a duality-gap certificate within {a.cert_eps:g} of the exact alpha-fair optimum",
             "unit": "ms", "certificate": "alpha = 1: gap / n_demands (mean log-ratio to the optimum); "
-                                         "else gap / min(|primal|, |dual|) (relative objective)"}
+                                         "else gap / min(|primal_h|, |dual_h|), _h: without U_alpha's "
+                                         "constant -1/(1-alpha) per demand (relative objective)"}
     for alpha in [float(v) for v in a.alpha_fair.split(",")]:
         fixed = dict(alpha_target=alpha, alpha_start=alpha, continuation=0)
 

@@ -295,6 +295,10 @@ typedef struct {
     int64_t bytes_per_iter;
     int64_t device_bytes;
     int64_t kernel_launches;  /* kernels this handle has launched so far */
+    int32_t edges_global;     /* 1: the iteration kernel keeps its per-edge
+                                 arrays in global memory (te_options.edge_mode
+                                 asked for it, or they exceed shared memory) */
+    int32_t reserved;
 } te_layout_info;
 te_status te_layout(const te_handle* h, te_layout_info* info);
 

@@ -710,6 +710,8 @@ extern "C" te_status te_layout(const te_handle* h, te_layout_info* info) {
     info->bytes_per_iter = h->bytes_per_iter;
     info->device_bytes = h->device_bytes;
     info->kernel_launches = h->launches;
+    info->edges_global = h->wide ? 1 : 0;
+    info->reserved = 0;
     return TE_OK;
 }
 

@@ -84,7 +84,8 @@ class te_layout_info(ctypes.Structure):
     _fields_ = [("n_demands", ctypes.c_int64), ("n_paths", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("id_rows", ctypes.c_int64), ("slots", ctypes.c_int64), ("id_bytes", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("bytes_per_iter", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("edges_global", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

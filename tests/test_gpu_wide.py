@@ -148,6 +148,7 @@ def torus_67k():
 def _same_run(te, inst, iters, **kw):
     a = te.TE(inst, **kw)
     b = te.TE(inst, edge_mode=te.EDGES_GLOBAL, **kw)
+    assert a.layout()["edges_global"] == 0 and b.layout()["edges_global"] == 1
     ra, rb = a.solve(iters), b.solve(iters)
     for k in ("iters", "total_iters", "r", "s", "beta", "alpha", "converged"):
         assert ra[k] == rb[k], (k, ra[k], rb[k])
@@ -176,6 +177,7 @@ def test_wide_instance_fixed_schedule_parity(te, wide_11k, alpha):
     assert wide_11k.n_edges > 10770
     kw = dict(alpha_target=alpha, alpha_start=alpha, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
     t = te.TE(wide_11k, **kw)
+    assert t.layout()["edges_global"] == 1 and t.layout()["id_bytes"] == 2
     assert t.solve(40)["iters"] == 40
     s = O.OracleSolver(wide_11k, **kw)
     s.run(40)
@@ -228,7 +230,7 @@ def test_32bit_ids_layout_and_walks(te, torus_67k):
     assert torus_67k.n_edges == 67600
     t = te.TE(torus_67k)
     info = t.layout()
-    assert info["id_bytes"] == 4
+    assert info["id_bytes"] == 4 and info["edges_global"] == 1
     t.close()
 
 

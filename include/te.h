@@ -185,7 +185,9 @@ void te_default_options(te_options* opt);
  * per-edge arrays of the iteration kernel no longer fit a CTA's shared
  * memory and it keeps them in global memory (edge_mode; such instances need
  * deterministic = 1); above 65,534 edges the device layout stores 32-bit
- * edge ids instead of 16-bit ones.  On success *out
+ * edge ids instead of 16-bit ones, up to about 490,000 edges (each CTA's
+ * slice of the prices must fit shared memory beside the staging buffers;
+ * more return TE_EUNSUPPORTED).  On success *out
  * receives a new handle.  Errors: TE_EINVAL (bad input; message names the
  * first offending index), TE_EUNSUPPORTED, TE_ENOMEM, TE_ECUDA. */
 te_status te_create(const te_topology* topo, const te_paths* paths, const double* demands,

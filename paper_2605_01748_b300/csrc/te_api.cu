@@ -347,6 +347,12 @@ extern "C" te_status te_create(const te_topology* topo, const te_paths* P, const
                      "edge_mode asks for global memory, which needs deterministic = 1", E);
         return bail(TE_EUNSUPPORTED);
     }
+    if (h->wide && te::iter_smem_bytes_wide(E, nsm, id_bytes) > 227 * 1024 - 1024) {
+        // the staging buffers and each CTA's slice of the prices must fit
+        h->err = fmt("n_edges = %lld: the iteration kernel's price slices exceed shared memory (at most "
+                     "about 490,000 edges)", E);
+        return bail(TE_EUNSUPPORTED);
+    }
     if (h->wide) {
         if ((st = h->cuda(te::iter_occupancy_wide(G, id_bytes, E, nsm, &bps), "occupancy query"))) return bail(st);
     } else if ((st = h->cuda(te::iter_occupancy(G, opt.deterministic != 0, E, nsm, &bps), "occupancy query"))) {

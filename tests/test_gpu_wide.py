@@ -321,3 +321,35 @@ def test_wide_mode_streaming_and_warm_start(te, wide_11k):
     assert runs[0][0] == runs[1][0]
     assert np.array_equal(runs[0][1], runs[1][1]) and np.array_equal(runs[0][2], runs[1][2])
     assert rb2["iters"] > 0
+
+
+def _parallel_links(E, K, seed=1):
+    # E parallel one-hop links from node 0 to node 1; K demands with 1-4
+    # one-hop paths on random links, a few on the highest ids
+    from paper_2605_01748_b300.instances import Instance
+    rng = np.random.default_rng(seed)
+    npaths = rng.integers(1, 5, K)
+    dpo = np.concatenate([[0], np.cumsum(npaths)]).astype(np.int64)
+    P = int(dpo[-1])
+    pe = rng.integers(0, E, P).astype(np.int32)
+    pe[:20] = E - 1 - np.arange(20)
+    return Instance(f"parallel-{E}", 2, np.zeros(E, np.int32), np.ones(E, np.int32), rng.uniform(1.0, 2.0, E),
+                    np.zeros(K, np.int32), np.ones(K, np.int32), rng.uniform(0.5, 3.0, K), dpo,
+                    np.arange(P + 1, dtype=np.int64), pe, {})
+
+
+def test_edge_count_limit_of_the_global_mode(te):
+    # each CTA's slice of the prices sits in shared memory beside the
+    # staging buffers: 450,000 edges run (oracle parity), 600,000 are refused
+    ok = _parallel_links(450000, 400)
+    kw = dict(alpha_target=1.0, alpha_start=1.0, beta0=1.0, adapt_beta=0, continuation=0, gamma=-1.0)
+    t = te.TE(ok, **kw)
+    assert t.layout()["id_bytes"] == 4 and t.layout()["edges_global"] == 1
+    t.solve(20)
+    s = O.OracleSolver(ok, **kw)
+    s.run(20)
+    assert _rel_inf(t.allocation(project=te.PROJECT_NONE), s.allocation()) <= TOL
+    t.close()
+    with pytest.raises(te.TEError) as ei:
+        te.TE(_parallel_links(600000, 400), **kw)
+    assert ei.value.status == te.TE_EUNSUPPORTED and "edges" in str(ei.value)

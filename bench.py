@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--alpha-fair", default="", metavar="ALPHAS",
                     help="time to a duality-gap certificate of --cert-eps at each fixed alpha (e.g. 1,2)")
     ap.add_argument("--cert-eps", type=float, default=1e-3)
+    ap.add_argument("--no-alpha-fair-check", action="store_true",
+                    help="leave the certified alpha = 1 measurement out of the default line")
     ap.add_argument("--iters", type=int, default=0,
                     help="profiling runs only: use this K and skip the reference run and the probe")
     return ap.parse_args()
@@ -548,6 +550,15 @@ def run_ours(a, ws, rank, local, dist):
     # timed for real beside the same solve on the GPU
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         out.update(cpu_legs(a, inst, t, K, te, dev, stream))
+    # the alpha-fair objective at alpha = 1 (proportional fairness) against
+    # its exact optimum on the same workload, by the duality-gap certificate
+    # (outside the timed region; the full mode is --alpha-fair)
+    if rank == 0 and a.iters <= 0 and not a.no_alpha_fair_check:
+        row = alpha_fair_row(a, te, inst, 1.0, stream, xdev, False)
+        out["alpha_fair_certified"] = {"alpha": 1.0, "target": a.cert_eps, "certificate": CERT_DESC,
+                                       "iters": row["iters"], "ms": row["value"],
+                                       "certified_eps": row.get("certified_eps"),
+                                       "paper_stop_rule": row["paper_stop_rule"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
     t.close()
@@ -985,6 +996,88 @@ def certified_eps(gap: float, primal: float, dual: float, alpha: float, n_demand
     return gap / min(abs(lo), abs(hi))
 
 
+CERT_DESC = ("alpha = 1: gap / n_demands (mean log-ratio to the optimum); else gap / min(|primal_h|, |dual_h|), "
+             "_h: without U_alpha's constant -1/(1-alpha) per demand (relative objective)")
+
+
+def alpha_fair_row(a, te, inst, alpha, st, x, with_oracle):
+    """One alpha of the certified measurement (see run_alpha_fair): what the
+    paper's stop rule leaves, then the iterations and device time to a
+    certificate of --cert-eps, and (with_oracle) the FP64 oracle run for the
+    same number of iterations."""
+    import numpy as np
+    import torch
+
+    fixed = dict(alpha_target=alpha, alpha_start=alpha, continuation=0)
+
+    def cert(t):
+        g, pr, du = t.gap(project=te.PROJECT_SCALE)
+        return certified_eps(g, pr, du, alpha, inst.n_demands), (g, pr, du)
+
+    row = {}
+    t = te.TE(inst, cuda_stream=st.cuda_stream, **fixed)
+    r = t.solve(a.ref_iters)
+    e_stop, _ = cert(t)
+    row["paper_stop_rule"] = {"iters": r["iters"], "converged": bool(r["converged"]), "certified_eps": e_stop}
+    t.close()
+    t = te.TE(inst, cuda_stream=st.cuda_stream, gamma=-1.0, **fixed)
+    first, lo, trace = None, 0, []
+    while True:
+        n = int(t.solve(a.probe_every)["total_iters"])
+        e, _ = cert(t)
+        trace.append((n, e))
+        if e <= a.cert_eps:
+            first = n
+            break
+        lo = n
+        if n >= a.ref_iters:
+            break
+    row["probe_tail"] = trace[-3:]
+    if first is not None:
+        t.reset()
+        t.solve(lo)
+        n = lo
+        while n < first:
+            n += a.refine_every
+            t.solve(a.refine_every)
+            if cert(t)[0] <= a.cert_eps:
+                first = n
+                break
+        ms = []
+        for i in range(a.warmup + a.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            t.reset()
+            rr = t.solve(first)
+            t.allocation(project=te.PROJECT_SCALE, out=x)
+            e, bracket = cert(t)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if i >= a.warmup:
+                ms.append(e0.elapsed_time(e1))
+        v = statistics.mean(ms)
+        row.update({"iters": first, "value": round(v, 3), "certified_eps": e,
+                    "gap_primal_dual": bracket, "iters_per_s": round(first / (v / 1e3), 1)})
+        if with_oracle:
+            from oracle import oracle as O
+            s = O.OracleSolver(inst, gamma=-1.0, threads=os.cpu_count() or 0, **fixed)
+            s.run(first)
+            xo = O.project_scale(inst, s.allocation())
+            go, pro, duo = O.gap(inst, xo, s.prices(), alpha)
+            xg = x.cpu().numpy().astype(np.float64)
+            Sg, So = O.demand_totals(inst, xg), O.demand_totals(inst, xo)
+            row["oracle_same_iters"] = {
+                "certified_eps": certified_eps(go, pro, duo, alpha, inst.n_demands),
+                "max_rel_err_rates": float(np.max(np.abs(xg - xo)) / max(np.max(np.abs(xo)), 1e-300)),
+                "max_rel_err_demand_totals": float(np.max(np.abs(Sg - So)) / max(np.max(So), 1e-300)),
+                "beta_gpu_oracle": [rr["beta"], s.beta]}
+    else:
+        row.update({"iters": None, "value": None})
+    t.close()
+    return row
+
+
 def run_alpha_fair(a):
     """alpha-fair objectives at fixed alpha (Eq. 4; no continuation) against
     their exact optimum, certified by the duality gap: the Lagrangian dual at
@@ -999,7 +1092,6 @@ def run_alpha_fair(a):
     beside it what the paper's stop rule (gamma 1e-3) leaves.  On the 200-node
     and smaller workloads the FP64 oracle runs the same K iterations and its
     certificate and allocation are compared.  One JSON line."""
-    import numpy as np
     import torch
     from paper_2605_01748_b300 import instances, te
 
@@ -1010,78 +1102,9 @@ def run_alpha_fair(a):
     x = torch.empty(inst.n_paths, dtype=torch.float32, device=dev)
     line = {"mode": "alpha-fair", "workload": workload_desc(inst),
             "metric": f"ms to a duality-gap certificate within {a.cert_eps:g} of the exact alpha-fair optimum",
-            "unit": "ms", "certificate": "alpha = 1: gap / n_demands (mean log-ratio to the optimum); "
-                                         "else gap / min(|primal_h|, |dual_h|), _h: without U_alpha's "
-                                         "constant -1/(1-alpha) per demand (relative objective)"}
+            "unit": "ms", "certificate": CERT_DESC}
     for alpha in [float(v) for v in a.alpha_fair.split(",")]:
-        fixed = dict(alpha_target=alpha, alpha_start=alpha, continuation=0)
-
-        def cert(t):
-            g, pr, du = t.gap(project=te.PROJECT_SCALE)
-            return certified_eps(g, pr, du, alpha, inst.n_demands), (g, pr, du)
-
-        row = {}
-        t = te.TE(inst, cuda_stream=st.cuda_stream, **fixed)
-        r = t.solve(a.ref_iters)
-        e_stop, _ = cert(t)
-        row["paper_stop_rule"] = {"iters": r["iters"], "converged": bool(r["converged"]), "certified_eps": e_stop}
-        t.close()
-        t = te.TE(inst, cuda_stream=st.cuda_stream, gamma=-1.0, **fixed)
-        first, lo, trace = None, 0, []
-        while True:
-            n = int(t.solve(a.probe_every)["total_iters"])
-            e, _ = cert(t)
-            trace.append((n, e))
-            if e <= a.cert_eps:
-                first = n
-                break
-            lo = n
-            if n >= a.ref_iters:
-                break
-        row["probe_tail"] = trace[-3:]
-        if first is not None:
-            t.reset()
-            t.solve(lo)
-            n = lo
-            while n < first:
-                n += a.refine_every
-                t.solve(a.refine_every)
-                if cert(t)[0] <= a.cert_eps:
-                    first = n
-                    break
-            ms = []
-            for i in range(a.warmup + a.steps):
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(st)
-                t.reset()
-                rr = t.solve(first)
-                t.allocation(project=te.PROJECT_SCALE, out=x)
-                e, bracket = cert(t)
-                e1.record(st)
-                torch.cuda.synchronize()
-                if i >= a.warmup:
-                    ms.append(e0.elapsed_time(e1))
-            v = statistics.mean(ms)
-            row.update({"iters": first, "value": round(v, 3), "certified_eps": e,
-                        "gap_primal_dual": bracket, "iters_per_s": round(first / (v / 1e3), 1)})
-            if inst.n_paths <= 1_000_000:
-                from oracle import oracle as O
-                s = O.OracleSolver(inst, gamma=-1.0, threads=os.cpu_count() or 0, **fixed)
-                s.run(first)
-                xo = O.project_scale(inst, s.allocation())
-                go, pro, duo = O.gap(inst, xo, s.prices(), alpha)
-                xg = x.cpu().numpy().astype(np.float64)
-                Sg, So = O.demand_totals(inst, xg), O.demand_totals(inst, xo)
-                row["oracle_same_iters"] = {
-                    "certified_eps": certified_eps(go, pro, duo, alpha, inst.n_demands),
-                    "max_rel_err_rates": float(np.max(np.abs(xg - xo)) / max(np.max(np.abs(xo)), 1e-300)),
-                    "max_rel_err_demand_totals": float(np.max(np.abs(Sg - So)) / max(np.max(So), 1e-300)),
-                    "beta_gpu_oracle": [rr["beta"], s.beta]}
-        else:
-            row.update({"iters": None, "value": None})
-        t.close()
-        line[f"alpha={alpha:g}"] = row
+        line[f"alpha={alpha:g}"] = alpha_fair_row(a, te, inst, alpha, st, x, inst.n_paths <= 1_000_000)
     print(json.dumps(line), flush=True)
 
 

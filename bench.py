@@ -98,6 +98,9 @@ def parse():
     ap.add_argument("--feasibility", type=int, default=0, metavar="K",
                     help="time the two feasibility steps (Algorithm 2 and proportional scaling, device output) "
                          "on the iterate after K iterations of the default solver, one JSON line")
+    ap.add_argument("--literal", type=int, default=0, metavar="ITERS",
+                    help="time the printed multi-block iteration (te_literal_run) and report the "
+                         "capacity overload it leaves")
     ap.add_argument("--edge-mode", choices=["auto", "global"], default="auto",
                     help="the timed handle's (and --steady's) per-edge arrays of the iteration kernel: in "
                          "shared memory when they fit (auto) or always in global memory")
@@ -1108,6 +1111,49 @@ def run_alpha_fair(a):
     print(json.dumps(line), flush=True)
 
 
+def run_literal(a):
+    """The printed multi-block update equations on the device (te_literal_run,
+    an ablation): device time per iteration from two runs of different
+    length (the difference removes the per-call set-up), and what the
+    iterate looks like after --literal iterations at alpha = 1, beta = 1
+    (normalised units): the largest relative capacity overload and the share
+    of edges over capacity, against the two-block iteration of te_solve run
+    to its stop rule and made feasible by proportional scaling.  One JSON
+    line."""
+    import numpy as np
+    import torch
+    from paper_2605_01748_b300 import instances, te
+
+    torch.cuda.set_device(0)
+    inst = instances.make(a.workload, threads=os.cpu_count() or 0)
+    n2 = a.literal
+    n1 = max(1, n2 // 5)
+    times = {}
+    for n in (n1, n2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = te.te_literal_run(inst, 1.0, 1.0, n)
+        times[n] = time.perf_counter() - t0
+    plen = np.diff(inst.path_edge_off)
+    L = np.bincount(inst.path_edges, weights=np.repeat(np.maximum(x, 0.0), plen), minlength=inst.n_edges)
+    over = (L - inst.capacity) / inst.capacity
+    t = te.TE(inst, alpha_target=1.0, alpha_start=1.0, continuation=0)
+    r = t.solve(a.ref_iters)
+    xs = t.allocation(project=te.PROJECT_SCALE).astype(np.float64)
+    Ls = np.bincount(inst.path_edges, weights=np.repeat(xs, plen), minlength=inst.n_edges)
+    t.close()
+    per_iter_ms = (times[n2] - times[n1]) / (n2 - n1) * 1e3
+    print(json.dumps({"mode": "literal", "workload": workload_desc(inst), "alpha": 1.0, "beta": 1.0,
+                      "iters": n2, "ms_per_iter": round(per_iter_ms, 3),
+                      "call_s": {str(n1): round(times[n1], 3), str(n2): round(times[n2], 3)},
+                      "literal": {"max_overload": float(over.max()),
+                                  "edges_over_capacity": float((over > 1e-6).mean()),
+                                  "min_rate": float(x.min())},
+                      "two_block": {"iters": r["iters"], "converged": bool(r["converged"]),
+                                    "max_overload_after_scaling": float(((Ls - inst.capacity) / inst.capacity).max())}}),
+          flush=True)
+
+
 def run_steady(a):
     """Steady-state time per iteration of the iteration kernel at fixed
     alphas (no continuation, no stop, adaptive beta): CUDA events around
@@ -1183,6 +1229,8 @@ def main():
         run_exact_k1(a)
     elif a.alpha_fair:
         run_alpha_fair(a)
+    elif a.literal > 0:
+        run_literal(a)
     elif a.batch > 0:
         run_batch(a, ws, rank, dist)
     elif a.ablation:

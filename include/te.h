@@ -383,6 +383,31 @@ void te_batch_destroy(te_batch* b);
 /* Message of the batch's last error (b NULL: of the last failed te_batch_create). */
 const char* te_batch_last_error(const te_batch* b);
 
+/* The update equations of Section 3.3 as printed, run on the device as a
+ * multi-block iteration: an ablation beside the two-block iteration of
+ * te_solve, not a solver.  From Algorithm 1's start (x = D_c/|P_c|, every
+ * rate suggestion y_{e,r} = x_r, all duals zero), iters iterations of, in
+ * Algorithm 1's order: the dual updates of the demand cap, the capacity,
+ * the consensus (one dual per path-edge incidence) and non-negativity
+ * (dual-updates-dem/cap/con/neg), the per-incidence cost of penalty-b and
+ * the rate suggestion y_{e,r} = [(mean_e cost - cost_{e,r}) / beta]_+, and
+ * the rate formula x_r = (Q_r + U'(S)/beta - (S - D_c + dual_dem_c) +
+ * dual_neg_r) / (1 + n_r) of eq. rate-computation with the previous y and
+ * duals, S solved from its sum over the demand's paths (closed form at
+ * alpha = 0, bisection otherwise).  As printed, the capacity and its dual
+ * are common to all paths of an edge and cancel in the rate suggestion, so
+ * the rates do not see C_e.  Values are normalised by the geometric mean of
+ * the demands; FP64 throughout; per-edge sums in a fixed order.  Inputs
+ * are host arrays as for te_create (checked the same way); alpha >= 0 the
+ * fairness level, beta > 0 the penalty in normalised units; x_out: host
+ * [n_paths], the rates in caller units (FP64).  Device memory is allocated
+ * for the call and released before it returns; the call synchronises
+ * cuda_stream (NULL: default stream).  Errors (message via
+ * te_last_error(NULL)): TE_EINVAL, TE_ENOMEM, TE_ECUDA. */
+te_status te_literal_run(const te_topology* topo, const te_paths* paths, const double* demands,
+                         const double* capacities, double alpha, double beta, int64_t iters, double* x_out,
+                         void* cuda_stream);
+
 /* The duality gap of te_gap for a caller-supplied allocation, computed
  * without allocating any memory (the paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc where they need the

@@ -23,6 +23,7 @@ LIBTE = os.path.join(PKG_DIR, "libte.so")
 LIBTEGEN = os.path.join(PKG_DIR, "libtegen.so")
 
 TE_SOURCES = ["te_api.cu", "te_layout.cu", "te_iter.cu", "te_batch.cu", "te_adjoint.cu", "te_proj.cu", "te_gap.cu",
+              "te_literal.cu",
               "te_noalloc.cu"]
 GEN_SOURCES = [os.path.join("gen", "kpaths.cpp")]
 

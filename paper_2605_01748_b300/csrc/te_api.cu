@@ -12,6 +12,7 @@
 
 #include "te.h"
 #include "te_layout.h"
+#include "te_literal.h"
 #include "te_internal.cuh"
 #include "te_proj.h"
 #include "te_adjoint.h"
@@ -510,6 +511,26 @@ extern "C" te_status te_reset(te_handle* h) {
     A(cudaMemcpyAsync(h->sc, &h->hsc, sizeof(sc), cudaMemcpyHostToDevice, s));
     A(cudaStreamSynchronize(s));
     return h->cuda(ce, "te_reset");
+}
+
+extern "C" te_status te_literal_run(const te_topology* topo, const te_paths* paths, const double* demands,
+                                   const double* capacities, double alpha, double beta, int64_t iters,
+                                   double* x_out, void* cuda_stream) {
+    g_create_error.clear();
+    if (!x_out || !(alpha >= 0.0) || !isfinite(alpha) || !(beta > 0.0) || !isfinite(beta) || iters < 0) {
+        g_create_error = "te_literal_run: null output, alpha < 0, beta <= 0 or iters < 0";
+        return TE_EINVAL;
+    }
+    const std::string v = validate(topo, paths, demands, capacities);
+    if (!v.empty()) {
+        g_create_error = v;
+        return TE_EINVAL;
+    }
+    std::string err;
+    const te_status st = te::literal_run(paths, topo->n_edges, demands, capacities, alpha, beta, iters, x_out,
+                                         static_cast<cudaStream_t>(cuda_stream), err);
+    if (st != TE_OK) g_create_error = err;
+    return st;
 }
 
 extern "C" te_status te_solve(te_handle* h, int64_t max_iters, double tol, te_solve_result* out) {

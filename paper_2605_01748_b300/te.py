@@ -38,7 +38,7 @@ EXPORTED = ("te_default_options", "te_create", "te_solve", "te_allocation", "te_
             "te_prices", "te_set_warm_start", "te_set_demands", "te_set_capacities", "te_reset", "te_trace", "te_layout",
             "te_destroy", "te_last_error", "te_gap_noalloc", "te_batch_create", "te_batch_solve",
             "te_batch_allocation", "te_batch_reset", "te_batch_info", "te_batch_destroy", "te_batch_last_error",
-            "te_gradient")
+            "te_gradient", "te_literal_run")
 
 
 class TEError(RuntimeError):
@@ -156,6 +156,9 @@ def _load() -> ctypes.CDLL:
     lib.te_batch_destroy.argtypes = [H]
     lib.te_batch_last_error.restype = ctypes.c_char_p
     lib.te_batch_last_error.argtypes = [H]
+    lib.te_literal_run.restype = ctypes.c_int
+    lib.te_literal_run.argtypes = [ctypes.POINTER(te_topology), ctypes.POINTER(te_paths), P, P, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int64, P, ctypes.c_void_p]
     lib.te_gap_noalloc.restype = ctypes.c_int
     lib.te_gap_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                    P, P, P, P, P, P, P, ctypes.c_double, P, P]
@@ -234,6 +237,23 @@ def te_create(inst, options: Optional[te_options] = None, check_walks: bool = Tr
     if st != TE_OK:
         raise TEError(st, te_last_error(None))
     return h
+
+
+def te_literal_run(inst, alpha: float, beta: float, iters: int, cuda_stream=None) -> np.ndarray:
+    """The printed multi-block update equations run on the device for iters
+    iterations from Algorithm 1's start (an ablation, see include/te.h);
+    returns the path rates in caller units (FP64, caller path order)."""
+    k = _Keep(inst)
+    topo = te_topology(int(inst.n_nodes), k.capacity.shape[0], _ptr(k.edge_src), _ptr(k.edge_dst))
+    paths = te_paths(k.demand.shape[0], 0, k.peo.shape[0] - 1, k.pe.shape[0], _ptr(k.demand_src),
+                     _ptr(k.demand_dst), _ptr(k.dpo), _ptr(k.peo), _ptr(k.pe))
+    x = np.empty(k.peo.shape[0] - 1, dtype=np.float64)
+    stream = int(getattr(cuda_stream, "cuda_stream", cuda_stream) or 0)
+    st = _lib.te_literal_run(ctypes.byref(topo), ctypes.byref(paths), _ptr(k.demand), _ptr(k.capacity),
+                             float(alpha), float(beta), int(iters), _ptr(x), stream)
+    if st != TE_OK:
+        raise TEError(st, te_last_error(None))
+    return x
 
 
 def te_solve(h, max_iters: int, tol: float = -1.0) -> te_solve_result:

@@ -139,6 +139,19 @@ def test_edge_mode_default_and_checked(te, tiny):
     assert ei.value.status == te.TE_EINVAL
 
 
+def test_literal_run_checks_arguments_on_the_host(te, tiny):
+    # argument and instance checks come before any device work
+    for alpha, beta, iters in ((-1.0, 1.0, 10), (1.0, 0.0, 10), (1.0, 1.0, -1)):
+        with pytest.raises(te.TEError) as ei:
+            te.te_literal_run(tiny, alpha, beta, iters)
+        assert ei.value.status == te.TE_EINVAL
+    import dataclasses
+    bad = dataclasses.replace(tiny, demand=-tiny.demand)
+    with pytest.raises(te.TEError) as ei:
+        te.te_literal_run(bad, 1.0, 1.0, 10)
+    assert ei.value.status == te.TE_EINVAL and "demand" in str(ei.value)
+
+
 def test_solve_rejects_null_handle(te):
     res = te.te_solve_result()
     assert te.lib().te_solve(None, 10, -1.0, ctypes.byref(res)) == te.TE_EINVAL

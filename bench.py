@@ -831,7 +831,13 @@ def run_batch(a, ws=1, rank=0, dist=None):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     n = len(W_all)
-    achieved = info["bytes_per_iter"] * ws * K / (batch_ms * 1e-3) / 1e9
+    # the method's bytes (the headline's per-unit rule, summed over the
+    # instances; per-CTA partial loads for the CTAs an instance runs on) and
+    # the bytes this layout moves
+    cpi = max(1, int(info.get("ctas_per_instance", 1) or 1))
+    method = sum(method_bytes(w, cpi) for w in W_all)
+    achieved = method * K / (batch_ms * 1e-3) / 1e9
+    layout_achieved = info["bytes_per_iter"] * ws * K / (batch_ms * 1e-3) / 1e9
     out = {"mode": "batch", "workload": f"what-if batch: {a.batch} failure scenarios x 4 demand matrices = {n} "
                                          f"instances of the 500-node WAN ({base.n_edges} directed edges, "
                                          f"{base.n_demands} demands, k=8, {info['n_paths']} paths in all)",
@@ -840,7 +846,12 @@ def run_batch(a, ws=1, rank=0, dist=None):
            "instance_iters_per_s": {"batch": round(n * K / (batch_ms * 1e-3), 1),
                                     "loop": round(n * K / (loop_ms * 1e-3), 1)},
            "batch_roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                              "frac": round(achieved / hbm, 4), "bytes_per_iter": info["bytes_per_iter"]},
+                              "frac": round(achieved / hbm, 4), "algorithmic_bytes_per_iter": method,
+                              "algorithmic_bytes_rule": "4 B per incidence (int32 id) + 12 B per path + 8 B per "
+                                                        "demand + 8 B per edge per CTA, summed over the instances",
+                              "layout_bytes_per_iter": info["bytes_per_iter"] * ws,
+                              "layout_achieved": round(layout_achieved, 1),
+                              "layout_frac": round(layout_achieved / hbm, 4)},
            "batch_shape": {"warps_per_cta": info["warps_per_cta"], "ctas_per_sm": info["ctas_per_sm"],
                            "lanes_per_demand": info["lanes_per_demand"]},
            "host_s": {"generate": round(gen_s, 1), "batch_create": round(create_s, 1)},

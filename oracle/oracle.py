@@ -22,6 +22,8 @@ Functions (all FP64; paper references are to GATE, Section 3 and Appendix B):
   iterations and its gradient in capacities and demands (reverse mode,
   checkpointed; not in the paper).
 * :func:`optimality` -- the optimality metric of Section 4.1.
+* :func:`literal_run` -- the update equations of Section 3.3 as printed, run
+  as a multi-block iteration (an ablation; numpy).
 """
 from __future__ import annotations
 
@@ -304,3 +306,67 @@ def optimality(S: np.ndarray, opt: np.ndarray, theta: float) -> float:
     S = np.asarray(S, dtype=np.float64)
     opt = np.asarray(opt, dtype=np.float64)
     return float(np.mean(np.minimum(S / np.maximum(opt, theta), 1.0)))
+
+
+def literal_run(inst, alpha: float, beta: float, iters: int) -> np.ndarray:
+    """The update equations of Section 3.3 as printed, run as a multi-block
+    iteration in Algorithm 1's order from its start (x = D_c/|P_c|, y = x on
+    every incidence, all duals zero), normalised by the geometric mean of the
+    demands; returns the path rates in caller units.  Per iteration, from the
+    previous x, y and duals: dual-updates-dem/cap/con/neg, the per-incidence
+    cost of penalty-b and the rate suggestion y = [(mean_e cost - cost) /
+    beta]_+, and eq. rate-computation x_r = (Q_r + U'(S)/beta - (S - D +
+    dual_dem) + dual_neg_r) / (1 + n_r) with Q_r = sum_{e in r} (y - dual_con)
+    and S the demand's total solved from the sum of that formula (closed form
+    at alpha = 0, bisection otherwise).  An ablation: as printed the capacity
+    cancels in the rate suggestion.  numpy, FP64; sums in index order."""
+    scale = float(np.exp(np.mean(np.log(inst.demand))))
+    C = inst.capacity / scale
+    D = inst.demand / scale
+    P, K = inst.n_paths, inst.n_demands
+    plen = np.diff(inst.path_edge_off)
+    inc_path = np.repeat(np.arange(P), plen)          # path of each incidence
+    inc_edge = inst.path_edges.astype(np.int64)       # edge of each incidence
+    path_dem = np.repeat(np.arange(K), np.diff(inst.demand_path_off))
+    n_e = np.bincount(inc_edge, minlength=inst.n_edges).astype(np.float64)
+    x = np.repeat(D / np.diff(inst.demand_path_off), np.diff(inst.demand_path_off))
+    y = x[inc_path].copy()
+    d_dem = np.zeros(K)
+    d_cap = np.zeros(inst.n_edges)
+    d_con = np.zeros(inc_edge.shape[0])
+    d_neg = np.zeros(P)
+    w = 1.0 / (1.0 + plen)
+    for _ in range(iters):
+        S = np.bincount(path_dem, weights=x, minlength=K)
+        # dual updates from x^k, y^k
+        d_dem_n = np.maximum(d_dem + (S - D), 0.0)
+        d_cap_n = np.maximum(d_cap + (np.bincount(inc_edge, weights=y, minlength=inst.n_edges) - C), 0.0)
+        d_con_n = np.maximum(d_con + (x[inc_path] - y), 0.0)
+        d_neg_n = np.maximum(d_neg - x, 0.0)
+        # rate suggestions
+        cost = beta * (-C[inc_edge] - x[inc_path]) - d_cap_n[inc_edge] - d_con_n
+        mean_e = np.bincount(inc_edge, weights=cost, minlength=inst.n_edges) / np.maximum(n_e, 1.0)
+        y_n = np.maximum((mean_e[inc_edge] - cost) / beta, 0.0)
+        # rate computation from the previous y and duals
+        Q = np.bincount(inc_path, weights=y - d_con, minlength=P)
+        a = np.bincount(path_dem, weights=w * (Q + d_neg), minlength=K)
+        W = np.bincount(path_dem, weights=w, minlength=K)
+        # S (1 + W) = a + W (D - d_dem) + W S^-alpha / beta, solved by bisection (the
+        # right side falls as S grows for alpha > 0; alpha = 0 is linear)
+        rhs0 = a + W * (D - d_dem)
+        if alpha == 0.0:
+            S_new = (rhs0 + W / beta) / (1.0 + W)
+        else:
+            lo = np.full(K, 1e-12)
+            hi = np.maximum(1.0, np.abs(rhs0) + W / beta) * 10.0 + 1.0
+            for _ in range(200):
+                mid = 0.5 * (lo + hi)
+                f = mid * (1.0 + W) - rhs0 - W * mid ** (-alpha) / beta
+                lo = np.where(f < 0, mid, lo)
+                hi = np.where(f < 0, hi, mid)
+            S_new = 0.5 * (lo + hi)
+        Sp = S_new[path_dem]
+        x = w * (Q + Sp ** (-alpha) / beta - (Sp - D[path_dem] + d_dem[path_dem]) + d_neg) if alpha > 0.0 else \
+            w * (Q + 1.0 / beta - (Sp - D[path_dem] + d_dem[path_dem]) + d_neg)
+        y, d_dem, d_cap, d_con, d_neg = y_n, d_dem_n, d_cap_n, d_con_n, d_neg_n
+    return x * scale

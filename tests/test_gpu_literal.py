@@ -1,6 +1,6 @@
 """The printed multi-block update equations of Section 3.3 on the device
 (te_literal_run, an ablation beside the two-block iteration), against their
-FP64 restatement in tests/test_paper_literal_variant.py on the same input.
+FP64 restatement in the oracle (oracle.literal_run) on the same input.
 
 Both run FP64 with the per-edge, per-path and per-demand sums in the same
 index order; the bisection for the demand total and pow() may differ in the
@@ -16,7 +16,6 @@ import numpy as np
 import pytest
 
 from oracle import oracle as O
-from test_paper_literal_variant import _literal_run
 
 pytestmark = pytest.mark.gpu
 
@@ -36,19 +35,19 @@ def _rel(a, b):
 @pytest.mark.parametrize("alpha", [0.0, 1.0, 2.0])
 def test_literal_iteration_matches_host_restatement_tiny(te, tiny, alpha):
     for iters, tol in ((50, 1e-9), (500, 1e-6)):
-        xg = te.te_literal_run(tiny, alpha, 1.0, iters)
-        xh = _literal_run(tiny, alpha=alpha, beta=1.0, iters=iters)
+        xg = te.teO.literal_run(tiny, alpha, 1.0, iters)
+        xh = O.literal_run(tiny, alpha=alpha, beta=1.0, iters=iters)
         assert _rel(xg, xh) <= tol, (iters, _rel(xg, xh))
 
 
 def test_literal_iteration_matches_host_restatement_medium(te, medium):
-    xg = te.te_literal_run(medium, 1.0, 1.0, 50)
-    xh = _literal_run(medium, alpha=1.0, beta=1.0, iters=50)
+    xg = te.teO.literal_run(medium, 1.0, 1.0, 50)
+    xh = O.literal_run(medium, alpha=1.0, beta=1.0, iters=50)
     assert _rel(xg, xh) <= 1e-9, _rel(xg, xh)
 
 
 def test_literal_iteration_ignores_capacity_on_gpu(te, tiny):
-    x = te.te_literal_run(tiny, 1.0, 1.0, 2000)
+    x = te.teO.literal_run(tiny, 1.0, 1.0, 2000)
     L = O.edge_loads(tiny, np.maximum(x, 0.0))
     assert float(np.max((L - tiny.capacity) / tiny.capacity)) > 0.5
     # the capacity and its dual cancel in mean_e(cost) - cost exactly in
@@ -56,6 +55,6 @@ def test_literal_iteration_ignores_capacity_on_gpu(te, tiny):
     # products fuse into FMAs, so the leftover differs from the host's);
     # the printed iteration does not contract, so after 300 iterations the
     # two runs agree to about 1e-9 of the largest rate instead of bit for bit
-    x2 = te.te_literal_run(dataclasses.replace(tiny, capacity=2.0 * tiny.capacity), 1.0, 1.0, 300)
-    x1 = te.te_literal_run(tiny, 1.0, 1.0, 300)
+    x2 = te.teO.literal_run(dataclasses.replace(tiny, capacity=2.0 * tiny.capacity), 1.0, 1.0, 300)
+    x1 = te.teO.literal_run(tiny, 1.0, 1.0, 300)
     assert _rel(x1, x2) <= 1e-7, _rel(x1, x2)

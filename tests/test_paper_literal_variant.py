@@ -18,65 +18,31 @@ where the rate formula takes the previous y and duals (the rate equation's
 superscripts).  The capacity and its dual are the same for every path of an
 edge, so they cancel in the rate suggestion: nothing in the iteration sees
 C_e, and the loads settle where the demands and the utility put them.  This
-file measures that on the tiny instance and records the numbers; it needs
-no GPU.  Test infrastructure only."""
+file pins the oracle's restatement (oracle.literal_run) on two iterations
+worked by hand, and measures the capacity effect on the tiny instance; it
+needs no GPU."""
 import numpy as np
 
 from oracle import oracle as O
 
 
-def _literal_run(inst, alpha, beta, iters):
-    """The printed multi-block iteration; returns the path rates (caller units)."""
-    scale = float(np.exp(np.mean(np.log(inst.demand))))
-    C = inst.capacity / scale
-    D = inst.demand / scale
-    P, K = inst.n_paths, inst.n_demands
-    plen = np.diff(inst.path_edge_off)
-    inc_path = np.repeat(np.arange(P), plen)          # path of each incidence
-    inc_edge = inst.path_edges.astype(np.int64)       # edge of each incidence
-    path_dem = np.repeat(np.arange(K), np.diff(inst.demand_path_off))
-    n_e = np.bincount(inc_edge, minlength=inst.n_edges).astype(np.float64)
-    x = np.repeat(D / np.diff(inst.demand_path_off), np.diff(inst.demand_path_off))
-    y = x[inc_path].copy()
-    d_dem = np.zeros(K)
-    d_cap = np.zeros(inst.n_edges)
-    d_con = np.zeros(inc_edge.shape[0])
-    d_neg = np.zeros(P)
-    w = 1.0 / (1.0 + plen)
-    for _ in range(iters):
-        S = np.bincount(path_dem, weights=x, minlength=K)
-        # dual updates from x^k, y^k
-        d_dem_n = np.maximum(d_dem + (S - D), 0.0)
-        d_cap_n = np.maximum(d_cap + (np.bincount(inc_edge, weights=y, minlength=inst.n_edges) - C), 0.0)
-        d_con_n = np.maximum(d_con + (x[inc_path] - y), 0.0)
-        d_neg_n = np.maximum(d_neg - x, 0.0)
-        # rate suggestions
-        cost = beta * (-C[inc_edge] - x[inc_path]) - d_cap_n[inc_edge] - d_con_n
-        mean_e = np.bincount(inc_edge, weights=cost, minlength=inst.n_edges) / np.maximum(n_e, 1.0)
-        y_n = np.maximum((mean_e[inc_edge] - cost) / beta, 0.0)
-        # rate computation from the previous y and duals
-        Q = np.bincount(inc_path, weights=y - d_con, minlength=P)
-        a = np.bincount(path_dem, weights=w * (Q + d_neg), minlength=K)
-        W = np.bincount(path_dem, weights=w, minlength=K)
-        # S (1 + W) = a + W (D - d_dem) + W S^-alpha / beta, solved by bisection (the
-        # right side falls as S grows for alpha > 0; alpha = 0 is linear)
-        rhs0 = a + W * (D - d_dem)
-        if alpha == 0.0:
-            S_new = (rhs0 + W / beta) / (1.0 + W)
-        else:
-            lo = np.full(K, 1e-12)
-            hi = np.maximum(1.0, np.abs(rhs0) + W / beta) * 10.0 + 1.0
-            for _ in range(200):
-                mid = 0.5 * (lo + hi)
-                f = mid * (1.0 + W) - rhs0 - W * mid ** (-alpha) / beta
-                lo = np.where(f < 0, mid, lo)
-                hi = np.where(f < 0, hi, mid)
-            S_new = 0.5 * (lo + hi)
-        Sp = S_new[path_dem]
-        x = w * (Q + Sp ** (-alpha) / beta - (Sp - D[path_dem] + d_dem[path_dem]) + d_neg) if alpha > 0.0 else \
-            w * (Q + 1.0 / beta - (Sp - D[path_dem] + d_dem[path_dem]) + d_neg)
-        y, d_dem, d_cap, d_con, d_neg = y_n, d_dem_n, d_cap_n, d_con_n, d_neg_n
-    return x * scale
+def test_two_iterations_worked_by_hand():
+    """One demand D = 2 on one one-hop path over a link of capacity C = 1,
+    alpha = 0, beta = 1.  Normalised by the geometric mean of the demands
+    (2): D = 1, C = 0.5, x0 = y0 = 1, duals 0.
+    Iteration 1: S = 1, dual_dem = 0, dual_cap = [1 - 0.5]_+ = 0.5,
+    dual_con = [1 - 1]_+ = 0, dual_neg = 0; the only incidence's cost is its
+    edge's mean, so y = 0.  Rate from the previous y and duals: Q = 1,
+    w = 1/2, a = w Q = 1/2, W = 1/2, rhs0 = a + W (D - 0) = 1, S = (rhs0 +
+    W / beta) / (1 + W) = 1, x = w (Q + 1 - (S - D) + 0) = 1.
+    Iteration 2: S = 1, dual_dem = 0, dual_cap = [0.5 + 0 - 0.5]_+ = 0,
+    dual_con = [0 + 1 - 0]_+ = 1, dual_neg = 0, y = 0.  Rate: Q = y - dual_con
+    (both previous) = 0, a = 0, rhs0 = 1/2, S = (1/2 + 1/2) / (3/2) = 2/3,
+    x = (1/2)(0 + 1 - (2/3 - 1) + 0) = 2/3, i.e. 4/3 in caller units."""
+    import refsolvers as R
+    inst = R.single_link(np.array([2.0]), 1.0)
+    assert np.allclose(O.literal_run(inst, alpha=0.0, beta=1.0, iters=1), [2.0], rtol=0, atol=1e-15)
+    assert np.allclose(O.literal_run(inst, alpha=0.0, beta=1.0, iters=2), [4.0 / 3.0], rtol=0, atol=1e-15)
 
 
 def _violation(inst, x):
@@ -88,7 +54,7 @@ def test_printed_multiblock_iteration_does_not_enforce_capacity(tiny):
     """After 2000 iterations at alpha = 1 the printed iteration leaves edges
     far over capacity, while the two-block reading (the oracle) meets the
     capacities to within its stop tolerance."""
-    x_lit = _literal_run(tiny, alpha=1.0, beta=1.0, iters=2000)
+    x_lit = O.literal_run(tiny, alpha=1.0, beta=1.0, iters=2000)
     v_lit = _violation(tiny, x_lit)
     s = O.OracleSolver(tiny, alpha_target=1.0, alpha_start=1.0, gamma=1e-6)
     s.run(20000)
@@ -103,6 +69,6 @@ def test_printed_iteration_ignores_capacity_values(tiny):
     """The same run with every capacity doubled gives the same rates: the
     capacities never enter the printed iteration's rates."""
     import dataclasses
-    x1 = _literal_run(tiny, alpha=1.0, beta=1.0, iters=300)
-    x2 = _literal_run(dataclasses.replace(tiny, capacity=2.0 * tiny.capacity), alpha=1.0, beta=1.0, iters=300)
+    x1 = O.literal_run(tiny, alpha=1.0, beta=1.0, iters=300)
+    x2 = O.literal_run(dataclasses.replace(tiny, capacity=2.0 * tiny.capacity), alpha=1.0, beta=1.0, iters=300)
     assert np.allclose(x1, x2, rtol=1e-12, atol=1e-12)

@@ -403,7 +403,8 @@ const char* te_batch_last_error(const te_batch* b);
  * [n_paths], the rates in caller units (FP64).  Device memory is allocated
  * for the call and released before it returns; the call synchronises
  * cuda_stream (NULL: default stream).  Errors (message via
- * te_last_error(NULL)): TE_EINVAL, TE_ENOMEM, TE_ECUDA. */
+ * te_last_error(NULL)): TE_EINVAL, TE_EUNSUPPORTED (more than 2^31 - 1
+ * incidences), TE_ENOMEM, TE_ECUDA. */
 te_status te_literal_run(const te_topology* topo, const te_paths* paths, const double* demands,
                          const double* capacities, double alpha, double beta, int64_t iters, double* x_out,
                          void* cuda_stream);

@@ -526,6 +526,10 @@ extern "C" te_status te_literal_run(const te_topology* topo, const te_paths* pat
         g_create_error = v;
         return TE_EINVAL;
     }
+    if (paths->nnz > 0x7fffffffLL) {  // the incidence lists hold 32-bit indices
+        g_create_error = "te_literal_run: more than 2^31 - 1 path-edge incidences";
+        return TE_EUNSUPPORTED;
+    }
     std::string err;
     const te_status st = te::literal_run(paths, topo->n_edges, demands, capacities, alpha, beta, iters, x_out,
                                          static_cast<cudaStream_t>(cuda_stream), err);

@@ -60,6 +60,7 @@ struct BatchArgs {
     int dpb;
     const uint16_t* ids;
     const BlockMeta* blkmeta;
+    const unsigned* hops;  // [blocks*32] hop counts of a lane's paths, slot j in bits 8j..8j+7
     const float* Dn;
     float* lam;
     float* blkres;
@@ -152,7 +153,8 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
         sc.converged = 0;
         sc.stop_reason = 0;
         long long done = 0;
-        const BlockCtx bc{a.Dn + I.dslot0, a.lam + I.dslot0, a.blkres + (size_t)I.res0 * 3, nullptr, a.dpb, (uint16_t)E};
+        const BlockCtx bc{a.Dn + I.dslot0, a.lam + I.dslot0, a.blkres + (size_t)I.res0 * 3,
+                          a.hops + (size_t)I.meta0 * kLanes, a.dpb, (uint16_t)E};
         const BlockMeta* bm = a.blkmeta + I.meta0;
         const uint16_t* ids = a.ids + (size_t)I.row0 * kLanes;
         const float* cap = a.cap_n + eo;
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(W * 32) k_batch(BatchArgs a) {
 
             // phase A: the instance's blocks, shared among the warps
             LaneRes unused;
-            run_blocks<G, kStageRows, false, false, true>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
+            run_blocks<G, kStageRows, false, true, true>(0, 1, I.nblocks, bm, ids, xin, xout, bc, ws, w_s, h_hi, h_lo, inv_beta,
                                              logbeta, beta_f, alpha, inv_alpha, unused);
             __syncthreads();
             if (*(volatile int*)a.status != 0) failed = true;
@@ -353,7 +355,7 @@ struct te_batch {
     // them all in one cooperative launch, `group` CTAs per instance (0: the
     // batch kernel, one instance per CTA)
     int group = 0;
-    unsigned* hops = nullptr;           // [blocks*32] per layout, for the iteration kernel
+    unsigned* hops = nullptr;           // [blocks*32] per layout
     float *u_next = nullptr, *w_next = nullptr;  // [n][E]
     uint2* gloads = nullptr;            // [n][group][E] per-CTA partial loads
     double* gpart = nullptr;            // [n][2][group][kPartWidth]
@@ -769,7 +771,7 @@ extern "C" te_status te_batch_create(const te_topology* topo, int32_t n, const t
         V.rowoff = b->rowoff + lro[j];
         V.slotbase = b->slotbase + lso[j];
         V.blkmeta = b->blkmeta + lmeta0[j];
-        V.hops = b->hops + (size_t)lmeta0[j] * kLanes;  // for the iteration kernel (the batch kernel counts hops)
+        V.hops = b->hops + (size_t)lmeta0[j] * kLanes;
         V.Dn = b->Dn + I.dslot0;
         V.np = b->np + (size_t)lmeta0[j] * b->dpb;
         V.demand_of = b->demand_of + (size_t)lmeta0[j] * b->dpb;
@@ -802,6 +804,7 @@ te::BatchArgs batch_args(te_batch* b, long long iters) {
     a.dpb = b->dpb;
     a.ids = b->ids;
     a.blkmeta = b->blkmeta;
+    a.hops = b->hops;
     a.Dn = b->Dn;
     a.lam = b->lam;
     a.blkres = b->blkres;

@@ -35,19 +35,19 @@ def _rel(a, b):
 @pytest.mark.parametrize("alpha", [0.0, 1.0, 2.0])
 def test_literal_iteration_matches_host_restatement_tiny(te, tiny, alpha):
     for iters, tol in ((50, 1e-9), (500, 1e-6)):
-        xg = te.teO.literal_run(tiny, alpha, 1.0, iters)
+        xg = te.te_literal_run(tiny, alpha, 1.0, iters)
         xh = O.literal_run(tiny, alpha=alpha, beta=1.0, iters=iters)
         assert _rel(xg, xh) <= tol, (iters, _rel(xg, xh))
 
 
 def test_literal_iteration_matches_host_restatement_medium(te, medium):
-    xg = te.teO.literal_run(medium, 1.0, 1.0, 50)
+    xg = te.te_literal_run(medium, 1.0, 1.0, 50)
     xh = O.literal_run(medium, alpha=1.0, beta=1.0, iters=50)
     assert _rel(xg, xh) <= 1e-9, _rel(xg, xh)
 
 
 def test_literal_iteration_ignores_capacity_on_gpu(te, tiny):
-    x = te.teO.literal_run(tiny, 1.0, 1.0, 2000)
+    x = te.te_literal_run(tiny, 1.0, 1.0, 2000)
     L = O.edge_loads(tiny, np.maximum(x, 0.0))
     assert float(np.max((L - tiny.capacity) / tiny.capacity)) > 0.5
     # the capacity and its dual cancel in mean_e(cost) - cost exactly in
@@ -55,6 +55,6 @@ def test_literal_iteration_ignores_capacity_on_gpu(te, tiny):
     # products fuse into FMAs, so the leftover differs from the host's);
     # the printed iteration does not contract, so after 300 iterations the
     # two runs agree to about 1e-9 of the largest rate instead of bit for bit
-    x2 = te.teO.literal_run(dataclasses.replace(tiny, capacity=2.0 * tiny.capacity), 1.0, 1.0, 300)
-    x1 = te.teO.literal_run(tiny, 1.0, 1.0, 300)
+    x2 = te.te_literal_run(dataclasses.replace(tiny, capacity=2.0 * tiny.capacity), 1.0, 1.0, 300)
+    x1 = te.te_literal_run(tiny, 1.0, 1.0, 300)
     assert _rel(x1, x2) <= 1e-7, _rel(x1, x2)

@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="large", choices=["tiny", "medium", "large"])
+    ap.add_argument("--workload", default="large", choices=["tiny", "medium", "large", "wan3000"])
     ap.add_argument("--ref-iters", type=int, default=40000)
     ap.add_argument("--ref-alpha-max", type=float, default=32.0,
                     help="alpha cap of the OPT reference run")
@@ -1181,6 +1181,8 @@ def run_steady(a):
     for alpha in [float(v) for v in a.steady.split(",")]:
         t = te.TE(inst, alpha_target=alpha, alpha_start=alpha, gamma=-1.0, cuda_stream=st.cuda_stream,
                   edge_mode=te.EDGES_GLOBAL if a.edge_mode == "global" else te.EDGES_AUTO)
+        lay = t.layout()
+        grid, edges_global = lay["grid"], lay["edges_global"]
         t.solve(60)
         best = math.inf
         for _ in range(3):
@@ -1193,8 +1195,17 @@ def run_steady(a):
             best = min(best, e0.elapsed_time(e1) * 1e3 / r["iters"])
         row[f"{alpha:g}"] = round(best, 1)
         t.close()
+    # the method's bytes per iteration (the headline's per-unit rule) over the
+    # best time per iteration, against the measured peak
+    peaks = {}
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    mb = method_bytes(inst, grid)
+    frac = {k: round(mb / (v * 1e-6) / 1e9 / hbm, 4) for k, v in row.items()}
     print(json.dumps({"mode": "steady", "workload": workload_desc(inst), "edge_mode": a.edge_mode,
-                      "us_per_iter": row}), flush=True)
+                      "edges_global": bool(edges_global), "us_per_iter": row, "method_bytes_per_iter": mb,
+                      "frac_of_measured_hbm": frac}), flush=True)
 
 
 def run_feasibility(a):

@@ -350,6 +350,11 @@ def make(name: str, seed: int = 0, threads: int = 0) -> Instance:
         return make_medium(seed, threads=threads)
     if name == "large":
         return make_large(seed, threads=threads)
+    if name == "wan3000":
+        # beyond the shared-memory edge limit of the iteration kernel: 3000
+        # nodes, 15,111 links (30,222 directed edges), all 8,997,000 ordered
+        # pairs with their shortest path (k = 1)
+        return make_waxman("wan3000", 3000, 15000, 1, seed=seed + 1, locality=LARGE_LOCALITY, threads=threads)
     raise ValueError(f"unknown instance {name!r}")
 
 

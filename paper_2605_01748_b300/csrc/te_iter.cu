@@ -58,7 +58,9 @@ namespace {
 // IdT: the layout's edge id type; 32-bit ids (above 65,534 edges) only in
 // the wide-edge mode, where the staging buffers take the room of the
 // per-edge arrays.
-template <int G, bool DET, bool GROUPED, bool WIDE = false, typename IdT = uint16_t>
+// KL: path slots per lane (kMaxPathsPerLane, or 1 for layouts with one path
+// per lane: the single-path demands of k = 1 instances).
+template <int G, bool DET, bool GROUPED, bool WIDE = false, typename IdT = uint16_t, int KL = kMaxPathsPerLane>
 __global__ void __launch_bounds__(kIterThreads, 1)
     k_iter(IterArgs a_param, const IterArgs* __restrict__ group_args, int group) {
     static_assert(!WIDE || (DET && !GROUPED), "the wide-edge mode has deterministic loads and one instance");
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(kIterThreads, 1)
         LaneRes acc;
         if (!failed) {
             const BlockCtx bc{a.L.Dn, a.lam, nullptr, a.L.hops, a.L.dpb, (uint16_t)a.L.E};
-            run_blocks<G, kIterStageRows, true, true, DET, WIDE, IdT>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws,
+            run_blocks<G, kIterStageRows, true, true, DET, WIDE, IdT, KL>(cta, NG, nbc, a.L.blkmeta, ids, xin, xout, bc, ws,
                                                 w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         {
@@ -470,31 +472,31 @@ __global__ void k_init_x(Layout L, float* x) {
     for (int j = 0; j < KB; ++j) x[(size_t)(s0 + j) * kLanes + lane] = j * L.G + hh < np ? v : 0.f;
 }
 
-template <int G, bool DET>
+template <int G, bool DET, int KL = kMaxPathsPerLane>
 cudaError_t launch_iter_t(const IterArgs& a, int grid, cudaStream_t st) {
     const size_t smem = iter_smem_bytes(a.L.E, grid, DET);
-    cudaError_t err =
-        cudaFuncSetAttribute(k_iter<G, DET, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err != cudaSuccess) return err;
-    IterArgs args = a;
-    const IterArgs* none = nullptr;
-    int group = 0;
-    void* params[] = {&args, &none, &group};
-    return cudaLaunchCooperativeKernel((const void*)k_iter<G, DET, false>, dim3(grid), dim3(kIterThreads), params,
-                                       smem, st);
-}
-
-template <int G, typename IdT>
-cudaError_t launch_iter_wide_t(const IterArgs& a, int grid, cudaStream_t st) {
-    const size_t smem = iter_smem_bytes_wide(a.L.E, grid, (int)sizeof(IdT));
-    cudaError_t err = cudaFuncSetAttribute(k_iter<G, true, false, true, IdT>,
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G, DET, false, false, uint16_t, KL>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     IterArgs args = a;
     const IterArgs* none = nullptr;
     int group = 0;
     void* params[] = {&args, &none, &group};
-    return cudaLaunchCooperativeKernel((const void*)k_iter<G, true, false, true, IdT>, dim3(grid),
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G, DET, false, false, uint16_t, KL>, dim3(grid),
+                                       dim3(kIterThreads), params, smem, st);
+}
+
+template <int G, typename IdT, int KL = kMaxPathsPerLane>
+cudaError_t launch_iter_wide_t(const IterArgs& a, int grid, cudaStream_t st) {
+    const size_t smem = iter_smem_bytes_wide(a.L.E, grid, (int)sizeof(IdT));
+    cudaError_t err = cudaFuncSetAttribute(k_iter<G, true, false, true, IdT, KL>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    IterArgs args = a;
+    const IterArgs* none = nullptr;
+    int group = 0;
+    void* params[] = {&args, &none, &group};
+    return cudaLaunchCooperativeKernel((const void*)k_iter<G, true, false, true, IdT, KL>, dim3(grid),
                                        dim3(kIterThreads), params, smem, st);
 }
 
@@ -588,7 +590,9 @@ cudaError_t iter_occupancy(int G, bool det, int E, int grid_hint, int* blocks_pe
 cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
     if (a.hist64 && a.L.id_bytes == 4) {
         switch (a.L.G) {
-            case 1: return launch_iter_wide_t<1, uint32_t>(a, grid, st);
+            case 1:
+                return a.L.kl == 1 ? launch_iter_wide_t<1, uint32_t, 1>(a, grid, st)
+                                   : launch_iter_wide_t<1, uint32_t>(a, grid, st);
             case 2: return launch_iter_wide_t<2, uint32_t>(a, grid, st);
             case 4: return launch_iter_wide_t<4, uint32_t>(a, grid, st);
             default: return launch_iter_wide_t<8, uint32_t>(a, grid, st);
@@ -596,7 +600,9 @@ cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
     }
     if (a.hist64) {
         switch (a.L.G) {
-            case 1: return launch_iter_wide_t<1, uint16_t>(a, grid, st);
+            case 1:
+                return a.L.kl == 1 ? launch_iter_wide_t<1, uint16_t, 1>(a, grid, st)
+                                   : launch_iter_wide_t<1, uint16_t>(a, grid, st);
             case 2: return launch_iter_wide_t<2, uint16_t>(a, grid, st);
             case 4: return launch_iter_wide_t<4, uint16_t>(a, grid, st);
             default: return launch_iter_wide_t<8, uint16_t>(a, grid, st);
@@ -605,7 +611,9 @@ cudaError_t launch_iter(const IterArgs& a, int grid, cudaStream_t st) {
     if (a.L.id_bytes != 2) return cudaErrorInvalidValue;
     if (a.o.deterministic) {
         switch (a.L.G) {
-            case 1: return launch_iter_t<1, true>(a, grid, st);
+            case 1:
+                // one path per lane (single-path demands): the one-slot block code
+                return a.L.kl == 1 ? launch_iter_t<1, true, 1>(a, grid, st) : launch_iter_t<1, true>(a, grid, st);
             case 2: return launch_iter_t<2, true>(a, grid, st);
             case 4: return launch_iter_t<4, true>(a, grid, st);
             default: return launch_iter_t<8, true>(a, grid, st);

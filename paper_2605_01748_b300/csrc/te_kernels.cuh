@@ -292,23 +292,24 @@ struct BlockCtx {
 // Per-lane inputs of one block read from global memory: the lane's rates,
 // its demand, the demand's multiplier and (HOPS) the hop counts of the
 // lane's paths, slot j in bits 8j..8j+7.  Loaded one block ahead of use.
+template <int KL = kMaxPathsPerLane>
 struct BlockIn {
-    float x[kMaxPathsPerLane];
+    float x[KL];
     float D, lam;
     unsigned nb;
 };
 
-template <int G, bool HOPS>
-__device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int lane, int s0, int KB,
+template <int G, bool HOPS, int KL = kMaxPathsPerLane>
+__device__ __forceinline__ BlockIn<KL> load_block_in(const BlockCtx& a, int b, int lane, int s0, int KB,
                                                  const float* __restrict__ xin) {
-    BlockIn in;
+    BlockIn<KL> in;
     const size_t di = (size_t)b * a.dpb + lane / G;
     in.D = __ldg(&a.Dn[di]);
     in.lam = __ldcg(&a.lam[di]);
     in.nb = HOPS ? __ldg(&a.hops[(size_t)b * kLanes + lane]) : 0u;
     const float* xp = xin + (size_t)s0 * kLanes + lane;
     #pragma unroll
-    for (int j = 0; j < kMaxPathsPerLane; ++j) {
+    for (int j = 0; j < KL; ++j) {
         in.x[j] = 0.f;
         if (j < KB) in.x[j] = __ldcg(xp + j * kLanes);
     }
@@ -328,14 +329,17 @@ __device__ __forceinline__ BlockIn load_block_in(const BlockCtx& a, int b, int l
 // value hi * 2^12 + lo (units of 2^-24) by one 64-bit L2 reduction (red:
 // no value returned, so the warp does not wait for it); h_lo unused.
 // IdT: the layout's edge id type (uint16_t, or uint32_t above 65,534 edges,
-// where the hop counts come with the block: HOPS).
-template <int G, bool STAGED, bool ACC, bool HOPS, bool DET, bool GH = false, typename IdT = uint16_t>
+// where the hop counts come with the block: HOPS).  KL: the path slots a lane
+// can hold (kMaxPathsPerLane; 1 for layouts of one path per lane, where the
+// absent slots' loops and registers go away; the arithmetic is the same).
+template <int G, bool STAGED, bool ACC, bool HOPS, bool DET, bool GH = false, typename IdT = uint16_t,
+          int KL = kMaxPathsPerLane>
 __device__ __forceinline__ void process_block(const BlockCtx& a, int b, int lane, const IdT* bids, int s0,
-                                              unsigned counts, int KB, const BlockIn& in,
+                                              unsigned counts, int KB, const BlockIn<KL>& in,
                                               float* __restrict__ xout, const float* w_s, unsigned* h_hi,
                                               unsigned* h_lo, float inv_beta, float logbeta,
                                               float beta_f, float alpha, float inv_alpha, LaneRes& acc) {
-    constexpr int KL = kMaxPathsPerLane;
+    static_assert(KL >= 1 && KL <= kMaxPathsPerLane, "path slots per lane");
     static_assert(sizeof(IdT) == 2 || (sizeof(IdT) == 4 && HOPS), "32-bit ids come with stored hop counts");
     const IdT sentinel = (IdT)a.sentinel;
     const unsigned gm = G == 1 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
@@ -496,7 +500,8 @@ __device__ __forceinline__ IdT* stage_buf(const WarpStage& ws, int k) {
 // per lane into acc (compensated), in the fixed order of the interleave.  HOPS
 // and DET: see process_block.  GH, IdT: see process_block (with 32-bit ids a
 // warp's two staging buffers take twice the bytes: ws.base must have room).
-template <int G, int ROWS, bool ACC, bool HOPS, bool DET, bool GH = false, typename IdT = uint16_t>
+template <int G, int ROWS, bool ACC, bool HOPS, bool DET, bool GH = false, typename IdT = uint16_t,
+          int KL = kMaxPathsPerLane>
 __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __restrict__ blkmeta,
                            const IdT* __restrict__ ids, const float* __restrict__ xin,
                            float* __restrict__ xout, const BlockCtx& bc, WarpStage& ws, const float* w_s,
@@ -540,11 +545,11 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
         }
         return true;
     };
-    auto prefetch = [&](int b, const BlockMeta& m) -> BlockIn {
+    auto prefetch = [&](int b, const BlockMeta& m) -> BlockIn<KL> {
         const int s0 = (int)__shfl_sync(0xffffffffu, m.s0, 0);
         const int KB = (int)__shfl_sync(0xffffffffu, m.kb, 0);
-        BlockIn in{};
-        if (b < none) in = load_block_in<G, HOPS>(bc, b, lane, s0, KB, xin);
+        BlockIn<KL> in{};
+        if (b < none) in = load_block_in<G, HOPS, KL>(bc, b, lane, s0, KB, xin);
         return in;
     };
     int b0 = grab();
@@ -554,13 +559,13 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
     int cur = 0;
     bool st0 = b0 < none ? issue(m0, cur) : false;
     cp_async_commit();  // one group per block, empty when nothing was copied
-    BlockIn in0 = prefetch(b0, m0);
+    BlockIn<KL> in0 = prefetch(b0, m0);
     while (b0 < none) {
         const int b2 = grab();
         const BlockMeta m2 = load_meta(b2);
         const bool st1 = b1 < none ? issue(m1, cur ^ 1) : false;
         cp_async_commit();
-        const BlockIn in1 = prefetch(b1, m1);
+        const BlockIn<KL> in1 = prefetch(b1, m1);
         const int s0 = (int)__shfl_sync(0xffffffffu, m0.s0, 0);
         const unsigned counts = __shfl_sync(0xffffffffu, m0.counts, 0);
         const int KB = (int)__shfl_sync(0xffffffffu, m0.kb, 0);
@@ -569,11 +574,11 @@ __device__ void run_blocks(int start, int stride, int count, const BlockMeta* __
             // lane; the __syncwarp makes each lane's copies visible to all
             cp_async_wait_prev();
             __syncwarp();
-            process_block<G, true, ACC, HOPS, DET, GH, IdT>(bc, b0, lane, stage_buf<ROWS, IdT>(ws, cur), s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
+            process_block<G, true, ACC, HOPS, DET, GH, IdT, KL>(bc, b0, lane, stage_buf<ROWS, IdT>(ws, cur), s0, counts, KB, in0, xout, w_s, h_hi, h_lo,
                                         inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         } else {
             const unsigned row0 = __shfl_sync(0xffffffffu, m0.row0, 0);
-            process_block<G, false, ACC, HOPS, DET, GH, IdT>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
+            process_block<G, false, ACC, HOPS, DET, GH, IdT, KL>(bc, b0, lane, ids + (size_t)row0 * kLanes, s0, counts, KB, in0, xout,
                                          w_s, h_hi, h_lo, inv_beta, logbeta, beta_f, alpha, inv_alpha, acc);
         }
         b0 = b1;
